@@ -1,0 +1,135 @@
+/*
+ * ns.h -- C ABI of libns: one GB300 (sm_103a) time-stepper for the triply periodic
+ * incompressible Navier-Stokes equations with phase-shift dealiasing.
+ *
+ * Method (Lambert, Reneuve & Augier, "Aliasing and phase shifting in pseudo-spectral
+ * simulations of the incompressible Navier-Stokes equations"):
+ *   d_t S = sigma S + N(S) (+ O(S)),  sigma = -nu |k|^2          (Sec. 4.1, Eq. base-eq)
+ *   N~_D(S) = T P exp(-ik.D) FFT[u_D x w_D]                       (Sec. 4.1-4.2, Eq. shift_operator_3d)
+ *   schemes: RK2, RK4 (+ 2/3 truncation baseline), RK2 phase-shift exact
+ *   (Patterson-Orszag), approx and random (Rogallo), and the forced "split" variant
+ *   (Sec. 4.1, Eq. Rogallo1981; Sec. 4.2; Sec. 6.1, Eq. forcing-eq).
+ *
+ * Conventions shared by every call:
+ *   - domain [0, 2*pi)^3 (L must be 2*pi), grid N^3, N = 2^a 3^b even, 8 <= N <= 1024;
+ *   - physical fields: double u[3][N][N][N], C order [component][z][y][x], x fastest;
+ *   - spectral fields: double re_im[3][N][N][N/2][2]: index [component][kz][ky][kx][re,im],
+ *     kz, ky in FFT order (0..N/2-1, -N/2..-1), kx = 0..N/2-1 (real-to-complex half
+ *     spectrum; the kx = N/2 plane is always zero because kmax <= N/2 truncates it);
+ *     uh(k) = N^-3 sum_x u(x) exp(-i k.x) (supplementary Eq. dft_def);
+ *   - every host buffer is owned by the caller and only read or written during the call;
+ *   - every function returns an ns_status; on failure a message is kept in the context
+ *     (ns_last_error) until the next failing call replaces it.
+ *   - one context is used from one host thread at a time; it owns all its device memory.
+ */
+#ifndef NS_H_
+#define NS_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  NS_OK = 0,
+  NS_ERR_INVALID_ARG = 1,  /* NULL pointer, bad enum, L != 2*pi, nu < 0, dt <= 0 ...   */
+  NS_ERR_UNSUPPORTED_N = 2,/* N not 2^a 3^b, odd, < 8 or > 1024                        */
+  NS_ERR_KMAX = 3,         /* kmax <= 0 or kmax > N/2 (C_t = kmax / k_N > 1)           */
+  NS_ERR_CUDA = 4,         /* a CUDA runtime call failed (message has the CUDA error)   */
+  NS_ERR_OOM = 5,          /* device allocation failed                                  */
+  NS_ERR_NONFINITE = 6,    /* energy or dissipation is NaN/Inf                          */
+  NS_ERR_TIMEOUT = 7,      /* a bounded device-side wait gave up                        */
+  NS_ERR_STATE = 8,        /* call out of order (e.g. step before a velocity was set)   */
+  NS_ERR_INTERNAL = 9      /* a device-side consistency check failed (bad launch shape) */
+} ns_status;
+
+enum { NS_TRUNC_SPHERICAL = 0, NS_TRUNC_CUBIC = 1 };
+enum { NS_RK2 = 0, NS_RK4 = 1, NS_RK2_PS_EXACT = 2, NS_RK2_PS_APPROX = 3, NS_RK2_PS_RANDOM = 4 };
+enum { NS_FP32 = 0, NS_FP64 = 1 };
+enum { NS_FORCE_NONE = 0, NS_FORCE_TCRANDOM_CONST_EPS = 1 };
+enum { NS_SPEC_SHELL = 0, NS_SPEC_X = 1, NS_SPEC_Y = 2, NS_SPEC_Z = 3 };
+
+typedef struct ns_ctx ns_ctx;
+
+typedef struct {
+  int N;             /* grid points per direction                                       */
+  double L;          /* domain size, must be 2*pi                                       */
+  double nu;         /* kinematic viscosity >= 0                                        */
+  double kmax;       /* truncation wavenumber, 0 < kmax <= N/2 (Sec. 3.2: kmax = C_t k_N) */
+  int truncation;    /* NS_TRUNC_SPHERICAL (keep |k| < kmax) or NS_TRUNC_CUBIC (all |k_i| < kmax) */
+  int scheme;        /* NS_RK2 ... NS_RK2_PS_RANDOM                                     */
+  int precision;     /* NS_FP32 (FP32 butterflies and products, FP64 tables/reductions) or NS_FP64 */
+  int device;        /* CUDA device ordinal                                             */
+  void* stream;      /* cudaStream_t to launch on (NULL: the context creates its own)   */
+  uint64_t seed;     /* seed of the random shifts delta_alpha (splitmix64 counter)       */
+} ns_params;
+
+/* Creates a context (FP32, device 0, own stream, seed 0).  Sec. 3.2 (truncation), Sec. 4
+ * (schemes).  *ctx is set to NULL on failure; the message is then in ns_init_error(). */
+int ns_init(ns_ctx** ctx, int N, double L, double nu, double kmax, int truncation, int scheme);
+/* Same with every option; params is read during the call only. */
+int ns_init_ex(ns_ctx** ctx, const ns_params* params);
+/* Message of the last failed ns_init / ns_init_ex in this thread. */
+const char* ns_init_error(void);
+/* Frees every device and host resource of the context. NULL is accepted. */
+int ns_destroy(ns_ctx* ctx);
+/* Message of the last failure on this context ("" if none). Valid until the next call. */
+const char* ns_last_error(ns_ctx* ctx);
+
+/* Physical velocity u (host, [3][N][N][N]) -> state: forward FFT, truncation T, Leray
+ * projection P, mean mode zeroed (Sec. 3.2; Sec. 4.1 below Eq. base-eq).  A
+ * non-solenoidal input is projected.  Resets time and step counter to 0. */
+int ns_set_velocity(ns_ctx* ctx, const double* u);
+/* State -> physical velocity u_out (host, [3][N][N][N]). */
+int ns_get_velocity(ns_ctx* ctx, double* u_out);
+/* Copies the spectral state to/from host re_im[3][N][N][N/2][2] (no truncation or
+ * projection applied on set: resuming from ns_get_state output is bitwise exact). */
+int ns_get_state(ns_ctx* ctx, double* re_im_out);
+int ns_set_state(ns_ctx* ctx, const double* re_im);
+
+/* Large-scale forcing O(S) (Sec. 2; Sec. 6.1, Eq. forcing-eq).  kind NS_FORCE_TCRANDOM_CONST_EPS:
+ * modes kf_min <= |k| <= kf_max (kf_max <= 8), random projected pattern redrawn every
+ * t_corr and linearly interpolated in time, amplitude chosen so that an Euler step dt of
+ * the forcing alone injects exactly eps*dt of energy.  With forcing set, NS_RK2_PS_RANDOM
+ * runs the "split" scheme; RK2 / RK4 / PS exact add O at every stage.  kind NS_FORCE_NONE
+ * switches forcing off. */
+int ns_set_forcing(ns_ctx* ctx, int kind, double kf_min, double kf_max, double eps,
+                   double t_corr, uint64_t seed);
+
+/* Advances nsteps time steps of size dt with the context's scheme (Sec. 4.1-4.2, 6.1).
+ * The random scheme draws delta_alpha of step s from splitmix64(seed, 3s+i) unless
+ * ns_set_shifts supplied them.  Synchronises the context's stream before returning. */
+int ns_step(ns_ctx* ctx, double dt, int nsteps);
+/* Test hook: delta_alpha for the next nsteps steps (host [nsteps][3], radians), consumed
+ * by the following ns_step calls in order; delta_beta = delta_alpha + (pi/N)(1,1,1). */
+int ns_set_shifts(ns_ctx* ctx, const double* delta_alpha, int nsteps);
+
+/* Shifted-and-de-shifted nonlinear term of Sec. 4.1-4.2 for the state re_im_in (host,
+ * NULL = the context's state) with shift delta[3] (radians): N~ = T P exp(-ik.D)
+ * FFT[u_D x w_D], mean mode zero.  Writes host re_im_out[3][N][N][N/2][2]. */
+int ns_nonlinear(ns_ctx* ctx, const double* re_im_in, const double* delta, double* re_im_out);
+
+/* Kinetic energy E = (1/2) sum_k |uh|^2 and dissipation eps = nu sum_k k^2 |uh|^2 (full
+ * spectrum sums, FP64 accumulation; Sec. 3.4).  NS_ERR_NONFINITE if either is not finite. */
+int ns_energy(ns_ctx* ctx, double* E, double* eps);
+/* Energy spectrum, FP64 bins k = 0..nbins-1: NS_SPEC_SHELL bins floor(|k| + 1/2),
+ * NS_SPEC_X/Y/Z fold +-k_i onto |k_i| (Sec. 3.4, Eq. quality uses the 1D spectra). */
+int ns_energy_spectrum(ns_ctx* ctx, int kind, double* out, int nbins);
+/* Simulated time and number of steps done since the last ns_set_velocity. */
+int ns_time(ns_ctx* ctx, double* t, int64_t* step);
+/* Overrides time and step counter (checkpoint resume). */
+int ns_set_time(ns_ctx* ctx, double t, int64_t step);
+
+/* Device pointers of the context (for callers that keep data on the GPU): the state
+ * ([3][N][N][N/2] complex of the context's precision) and the stream. */
+int ns_device_state(ns_ctx* ctx, void** state, void** stream, int* precision);
+
+/* Bytes moved to/from HBM per time step by the algorithmic two-pass model (one slab and
+ * one pencil pass per evaluation), for roofline reporting. */
+double ns_model_bytes_per_step(ns_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NS_H_ */

@@ -1,0 +1,201 @@
+"""Thin ctypes binding over libns.so (include/ns.h); argument marshalling only.
+
+Every numerical step runs in the library's CUDA kernels.  Importing this module loads the
+library and raises ImportError when it is missing: there is no CPU fallback.
+
+Arrays follow ns.h: physical velocity float64 [3, N, N, N] (x fastest); spectral state
+complex128 [3, N, N, N//2] (index [c, kz, ky, kx], kz and ky in FFT order).
+"""
+import ctypes
+import math
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libns.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(
+        "libns.so is not built (run `python -m paper_2603_08892_gb300.build` or "
+        "`python -c 'import __graft_entry__ as g; g.build()'`); there is no CPU fallback")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+NS_OK = 0
+ERRORS = {1: "NS_ERR_INVALID_ARG", 2: "NS_ERR_UNSUPPORTED_N", 3: "NS_ERR_KMAX", 4: "NS_ERR_CUDA",
+          5: "NS_ERR_OOM", 6: "NS_ERR_NONFINITE", 7: "NS_ERR_TIMEOUT", 8: "NS_ERR_STATE",
+          9: "NS_ERR_INTERNAL"}
+TRUNC_SPHERICAL, TRUNC_CUBIC = 0, 1
+RK2, RK4, RK2_PS_EXACT, RK2_PS_APPROX, RK2_PS_RANDOM = 0, 1, 2, 3, 4
+FP32, FP64 = 0, 1
+FORCE_NONE, FORCE_TCRANDOM_CONST_EPS = 0, 1
+SPEC_SHELL, SPEC_X, SPEC_Y, SPEC_Z = 0, 1, 2, 3
+
+_dp = ctypes.POINTER(ctypes.c_double)
+_vp = ctypes.c_void_p
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int), ("L", ctypes.c_double), ("nu", ctypes.c_double),
+                ("kmax", ctypes.c_double), ("truncation", ctypes.c_int), ("scheme", ctypes.c_int),
+                ("precision", ctypes.c_int), ("device", ctypes.c_int), ("stream", _vp),
+                ("seed", ctypes.c_uint64)]
+
+
+def _sig(name, res, args):
+    f = getattr(_lib, name)
+    f.restype = res
+    f.argtypes = args
+    return f
+
+
+_init_ex = _sig("ns_init_ex", ctypes.c_int, [ctypes.POINTER(_vp), ctypes.POINTER(Params)])
+_init_error = _sig("ns_init_error", ctypes.c_char_p, [])
+_destroy = _sig("ns_destroy", ctypes.c_int, [_vp])
+_last_error = _sig("ns_last_error", ctypes.c_char_p, [_vp])
+_set_velocity = _sig("ns_set_velocity", ctypes.c_int, [_vp, _dp])
+_get_velocity = _sig("ns_get_velocity", ctypes.c_int, [_vp, _dp])
+_get_state = _sig("ns_get_state", ctypes.c_int, [_vp, _dp])
+_set_state = _sig("ns_set_state", ctypes.c_int, [_vp, _dp])
+_set_forcing = _sig("ns_set_forcing", ctypes.c_int,
+                    [_vp, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                     ctypes.c_double, ctypes.c_uint64])
+_step = _sig("ns_step", ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_int])
+_set_shifts = _sig("ns_set_shifts", ctypes.c_int, [_vp, _dp, ctypes.c_int])
+_nonlinear = _sig("ns_nonlinear", ctypes.c_int, [_vp, _dp, _dp, _dp])
+_energy = _sig("ns_energy", ctypes.c_int, [_vp, _dp, _dp])
+_spectrum = _sig("ns_energy_spectrum", ctypes.c_int, [_vp, ctypes.c_int, _dp, ctypes.c_int])
+_time = _sig("ns_time", ctypes.c_int, [_vp, _dp, ctypes.POINTER(ctypes.c_int64)])
+_set_time = _sig("ns_set_time", ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_int64])
+_device_state = _sig("ns_device_state", ctypes.c_int,
+                     [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(ctypes.c_int)])
+_model_bytes = _sig("ns_model_bytes_per_step", ctypes.c_double, [_vp])
+
+EXPORTED = ["ns_init", "ns_init_ex", "ns_init_error", "ns_destroy", "ns_last_error",
+            "ns_set_velocity", "ns_get_velocity", "ns_get_state", "ns_set_state",
+            "ns_set_forcing", "ns_step", "ns_set_shifts", "ns_nonlinear", "ns_energy",
+            "ns_energy_spectrum", "ns_time", "ns_set_time", "ns_device_state",
+            "ns_model_bytes_per_step"]
+
+
+class NSError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s (%d): %s" % (ERRORS.get(code, "?"), code, msg))
+        self.code = code
+
+
+def _ptr(a):
+    return a.ctypes.data_as(_dp)
+
+
+class Solver:
+    """One libns context (owns its device memory; one GB300 stream)."""
+
+    def __init__(self, N, nu, kmax, scheme=RK2_PS_RANDOM, truncation=TRUNC_SPHERICAL,
+                 precision=FP32, device=0, stream=None, seed=0, L=2 * math.pi):
+        p = Params(N, L, nu, kmax, truncation, scheme, precision, device,
+                   _vp(stream) if stream else None, seed)
+        h = _vp()
+        rc = _init_ex(ctypes.byref(h), ctypes.byref(p))
+        if rc != NS_OK:
+            raise NSError(rc, _init_error().decode())
+        self._h = h
+        self.N, self.nu, self.kmax, self.scheme, self.precision = N, nu, kmax, scheme, precision
+
+    def _check(self, rc):
+        if rc != NS_OK:
+            raise NSError(rc, _last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # --- state ---------------------------------------------------------------------
+    def set_velocity(self, u):
+        u = np.ascontiguousarray(u, dtype=np.float64)
+        assert u.shape == (3, self.N, self.N, self.N)
+        self._check(_set_velocity(self._h, _ptr(u)))
+
+    def get_velocity(self):
+        u = np.empty((3, self.N, self.N, self.N))
+        self._check(_get_velocity(self._h, _ptr(u)))
+        return u
+
+    def get_state(self):
+        N = self.N
+        s = np.empty((3, N, N, N // 2), dtype=np.complex128)
+        self._check(_get_state(self._h, s.ctypes.data_as(_dp)))
+        return s
+
+    def set_state(self, S):
+        S = np.ascontiguousarray(S, dtype=np.complex128)
+        assert S.shape == (3, self.N, self.N, self.N // 2)
+        self._check(_set_state(self._h, S.ctypes.data_as(_dp)))
+
+    def set_forcing(self, kf_min=2.0, kf_max=3.0, eps=1.0, t_corr=0.5, seed=0,
+                    kind=FORCE_TCRANDOM_CONST_EPS):
+        self._check(_set_forcing(self._h, kind, kf_min, kf_max, eps, t_corr, seed))
+
+    def step(self, dt, nsteps=1):
+        self._check(_step(self._h, dt, nsteps))
+
+    def set_shifts(self, delta_alpha):
+        d = np.ascontiguousarray(delta_alpha, dtype=np.float64).reshape(-1, 3)
+        self._check(_set_shifts(self._h, _ptr(d), d.shape[0]))
+
+    def nonlinear(self, delta, S=None):
+        N = self.N
+        out = np.empty((3, N, N, N // 2), dtype=np.complex128)
+        d = np.ascontiguousarray(delta, dtype=np.float64)
+        if S is not None:
+            S = np.ascontiguousarray(S, dtype=np.complex128)
+            sp = S.ctypes.data_as(_dp)
+        else:
+            sp = None
+        self._check(_nonlinear(self._h, sp, _ptr(d), out.ctypes.data_as(_dp)))
+        return out
+
+    def energy(self):
+        e = ctypes.c_double()
+        d = ctypes.c_double()
+        self._check(_energy(self._h, ctypes.byref(e), ctypes.byref(d)))
+        return e.value, d.value
+
+    def spectrum(self, kind=SPEC_SHELL, nbins=None):
+        nbins = self.N // 2 + 1 if nbins is None else nbins
+        out = np.empty(nbins)
+        self._check(_spectrum(self._h, kind, _ptr(out), nbins))
+        return out
+
+    def time(self):
+        t = ctypes.c_double()
+        s = ctypes.c_int64()
+        self._check(_time(self._h, ctypes.byref(t), ctypes.byref(s)))
+        return t.value, s.value
+
+    def set_time(self, t, step):
+        self._check(_set_time(self._h, t, step))
+
+    def device_state(self):
+        s = _vp()
+        st = _vp()
+        p = ctypes.c_int()
+        self._check(_device_state(self._h, ctypes.byref(s), ctypes.byref(st), ctypes.byref(p)))
+        return s.value, st.value, p.value
+
+    def model_bytes_per_step(self):
+        return _model_bytes(self._h)

@@ -1,0 +1,919 @@
+// ns_api.cu -- host runtime and C ABI of libns (declared in include/ns.h).
+//
+// The host side owns the device buffers, factorises the transform lengths, sizes the
+// tiles, draws the random shifts and forcing patterns (counter-based, reproducible) and
+// sequences the kernels of ns_kernels.cuh into the schemes of Sec. 4 and 6.1 of the paper:
+//   RK2            INIT | X P(RK2_1) X P(RK2_2)                       41 C bytes / step
+//   RK4 (Lawson)   INIT | X P(RK4_1) X P(RK4_2) X P(RK4_3) X P(RK4_4)  94 C
+//   PS exact       INIT(2 shifts) | 2X P(RK2_1, avg) 2X P(RK2_2, avg)  73 C
+//   PS approx/rand INIT(alpha_0) | X P(ROG_1, beta_n) X P(ROG_2, alpha_{n+1})  44 C
+// where X is the slab pass and P the pencil pass of one evaluation, and C = N^3 * sizeof(T)
+// is the size of one half-spectrum complex field.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/ns.h"
+#include "ns_kernels.cuh"
+
+using namespace ns;
+
+namespace {
+
+thread_local std::string g_init_error;
+
+struct NsError {
+  int code;
+  std::string msg;
+};
+
+#define CUDA_TRY(call)                                                                   \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess) {                                                             \
+      throw NsError{e_ == cudaErrorMemoryAllocation ? NS_ERR_OOM : NS_ERR_CUDA,          \
+                    std::string(#call) + ": " + cudaGetErrorString(e_)};                 \
+    }                                                                                    \
+  } while (0)
+
+#define LAUNCH_CHECK() CUDA_TRY(cudaGetLastError())
+
+bool is_2a3b(int n) {
+  if (n <= 0) return false;
+  while (n % 2 == 0) n /= 2;
+  while (n % 3 == 0) n /= 3;
+  return n == 1;
+}
+
+FFTPlan make_plan(int n, int Ntab) {
+  FFTPlan p;
+  memset(&p, 0, sizeof(p));
+  p.n = n;
+  p.tw_stride = Ntab / n;
+  int m = n, a2 = 0, a3 = 0;
+  while (m % 2 == 0) { m /= 2; ++a2; }
+  while (m % 3 == 0) { m /= 3; ++a3; }
+  while (a2 >= 3) { p.radix[p.nst++] = 8; a2 -= 3; }
+  if (a2 == 2) p.radix[p.nst++] = 4;
+  if (a2 == 1) p.radix[p.nst++] = 2;
+  for (int i = 0; i < a3; ++i) p.radix[p.nst++] = 3;
+  return p;
+}
+
+int largest_divisor_le(int m, int cap) {
+  for (int d = cap < m ? cap : m; d >= 1; --d)
+    if (m % d == 0) return d;
+  return 1;
+}
+
+// block size for a batch of nl lines of length n (every stage holds <= 15 values / thread)
+int fft_block(int nl, int n) {
+  const int need = (nl * n + 14) / 15;
+  int bd = 128;
+  while (bd < need) bd *= 2;
+  return bd;
+}
+
+// splitmix64 (Steele, Lea & Flood 2014): n-th output of the generator seeded with s
+uint64_t splitmix64(uint64_t s, uint64_t n) {
+  uint64_t z = s + (n + 1) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+double uniform01(uint64_t s, uint64_t n) {
+  return (double)(splitmix64(s, n) >> 11) * (1.0 / 9007199254740992.0);
+}
+
+struct SolverBase {
+  virtual ~SolverBase() {}
+  virtual void set_velocity(const double* u) = 0;
+  virtual void get_velocity(double* u) = 0;
+  virtual void get_state(double* s) = 0;
+  virtual void set_state(const double* s) = 0;
+  virtual void step(double dt, int nsteps) = 0;
+  virtual void nonlinear(const double* in, const double* delta, double* out) = 0;
+  virtual void energy(double* E, double* eps) = 0;
+  virtual void spectrum(int kind, double* out, int nbins) = 0;
+  virtual void set_forcing(int kind, double kfmin, double kfmax, double eps, double tcorr,
+                           uint64_t seed) = 0;
+  virtual void* state_ptr() = 0;
+};
+
+}  // namespace
+
+struct ns_ctx {
+  ns_params p;
+  double K2maxd;
+  int K2max, Kimax;
+  double t = 0.0;
+  int64_t step = 0;
+  bool have_state = false;
+  std::vector<double> override_shifts;  // [n][3], consumed from the front
+  size_t override_pos = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  SolverBase* solver = nullptr;
+  std::string err;
+};
+
+namespace {
+
+template <typename T>
+struct Solver : SolverBase {
+  ns_ctx* c;
+  int N, M;
+  size_t F1;  // complex elements of one half-spectrum field: N*N*M
+  cudaStream_t st;
+  // device buffers
+  cpx<T>* state = nullptr;
+  cpx<T>* acc = nullptr;
+  cpx<T>* mixed[2] = {nullptr, nullptr};
+  cpx<T>* Ft[2] = {nullptr, nullptr};
+  cpx<T>* scr = nullptr;
+  cpx<T>* tw = nullptr;
+  T* ifac = nullptr;
+  cpx<T>* shtab = nullptr;
+  size_t shtab_cap = 0;  // number of shift vectors
+  double* d_shifts = nullptr;
+  double* red = nullptr;
+  int red_blocks = 0;
+  int* d_err = nullptr;
+  double cur_dt = -1.0;
+  // forcing
+  int fkind = NS_FORCE_NONE, fK = 0;
+  double fkmin = 0, fkmax = 0, feps = 0, ftcorr = 1, fD = 0;
+  uint64_t fseed = 0;
+  cpx<double>* fpat = nullptr;
+  int fpat_cap = 0;
+  cpx<T>* force = nullptr;
+  cpx<T>* shell = nullptr;
+  // plans and launch shapes
+  FFTPlan pz, py, px;
+  int TX, bdP;
+  size_t smP;
+  int TY, bdYi, bdYf;
+  size_t smYi, smYf;
+  int RX, bdX;
+  size_t smX;
+  int G;
+  int nsm = 148;
+
+  explicit Solver(ns_ctx* ctx) : c(ctx) {
+    N = c->p.N;
+    M = N / 2;
+    F1 = (size_t)N * N * M;
+    st = c->stream;
+    int dev = c->p.device;
+    CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    pz = make_plan(N, N);
+    py = pz;
+    px = make_plan(M, N);
+    const size_t cs = sizeof(cpx<T>);
+    const size_t smax = 200 * 1024;
+    // pencil: 4 tiles of N x TX
+    TX = largest_divisor_le(M, 16);
+    while (TX > 1 && (4 * N * TX * cs > smax || fft_block(TX, N) > 512)) TX = largest_divisor_le(M, TX - 1);
+    bdP = fft_block(TX, N);
+    if (bdP < 256) bdP = 256;
+    smP = 4 * (size_t)N * TX * cs;
+    // y passes: 6 (inverse) or 3 (forward) tiles of N x TY
+    TY = largest_divisor_le(M, 16);
+    while (TY > 1 && (6 * N * TY * cs > smax || fft_block(TY, N) > 512)) TY = largest_divisor_le(M, TY - 1);
+    bdYi = bdYf = fft_block(TY, N) < 256 ? 256 : fft_block(TY, N);
+    smYi = 6 * (size_t)N * TY * cs;
+    smYf = 3 * (size_t)N * TY * cs;
+    // x rows: 6 fields x RX rows of M
+    RX = 16;
+    while (RX > 1 && (6 * (size_t)RX * M * cs > 100 * 1024 || fft_block(RX, M) > 512)) RX /= 2;
+    bdX = fft_block(RX, M) < 256 ? 256 : fft_block(RX, M);
+    smX = 6 * (size_t)RX * M * cs;
+    // plane group sized to keep the scratch (6 fields) in L2
+    const size_t plane6 = 6 * (size_t)N * M * cs;
+    G = (int)((48ull << 20) / plane6);
+    if (G < 1) G = 1;
+    if (G > N) G = N;
+
+    CUDA_TRY(cudaFuncSetAttribute(k_pencil<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smP));
+    CUDA_TRY(cudaFuncSetAttribute(k_yinv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smYi));
+    CUDA_TRY(cudaFuncSetAttribute(k_yfwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smYf));
+    CUDA_TRY(cudaFuncSetAttribute(k_xrow<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smX));
+
+    const int sch = c->p.scheme;
+    const bool two = sch == NS_RK2_PS_EXACT;
+    CUDA_TRY(cudaMalloc(&state, 3 * F1 * cs));
+    CUDA_TRY(cudaMalloc(&acc, 3 * F1 * cs));
+    CUDA_TRY(cudaMalloc(&mixed[0], 5 * F1 * cs));
+    CUDA_TRY(cudaMalloc(&Ft[0], 3 * F1 * cs));
+    if (two) {
+      CUDA_TRY(cudaMalloc(&mixed[1], 5 * F1 * cs));
+      CUDA_TRY(cudaMalloc(&Ft[1], 3 * F1 * cs));
+    }
+    CUDA_TRY(cudaMalloc(&scr, 6 * (size_t)G * N * M * cs));
+    CUDA_TRY(cudaMalloc(&tw, N * cs));
+    CUDA_TRY(cudaMalloc(&ifac, 2 * N * sizeof(T)));
+    red_blocks = 2 * nsm;
+    CUDA_TRY(cudaMalloc(&red, (size_t)red_blocks * 1024 * sizeof(double)));
+    CUDA_TRY(cudaMalloc(&d_err, sizeof(int)));
+    CUDA_TRY(cudaMemsetAsync(d_err, 0, sizeof(int), st));
+    CUDA_TRY(cudaMemsetAsync(state, 0, 3 * F1 * cs, st));
+    k_twiddle<T><<<(N + 255) / 256, 256, 0, st>>>(tw, N);
+    LAUNCH_CHECK();
+    CUDA_TRY(cudaStreamSynchronize(st));
+  }
+
+  ~Solver() override {
+    cudaFree(state); cudaFree(acc); cudaFree(mixed[0]); cudaFree(mixed[1]);
+    cudaFree(Ft[0]); cudaFree(Ft[1]); cudaFree(scr); cudaFree(tw); cudaFree(ifac);
+    cudaFree(shtab); cudaFree(d_shifts); cudaFree(red); cudaFree(d_err);
+    cudaFree(fpat); cudaFree(force); cudaFree(shell);
+  }
+
+  void* state_ptr() override { return state; }
+
+  // ---- device error flag ------------------------------------------------------------
+  void sync_check() {
+    CUDA_TRY(cudaStreamSynchronize(st));
+    int h = 0;
+    CUDA_TRY(cudaMemcpy(&h, d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (h) {
+      CUDA_TRY(cudaMemset(d_err, 0, sizeof(int)));
+      throw NsError{NS_ERR_INTERNAL, "device-side launch-shape check failed (flag " + std::to_string(h) + ")"};
+    }
+  }
+
+  // ---- passes -----------------------------------------------------------------------
+  SlabArgs<T> slab_args() {
+    SlabArgs<T> a;
+    memset(&a, 0, sizeof(a));
+    a.N = N; a.M = M; a.py = py; a.px = px; a.tw = tw; a.scr = scr;
+    a.TY = TY; a.RX = RX; a.err = d_err;
+    return a;
+  }
+
+  // slab pass over every plane group: mixed (5 fields) -> Ft (3 fields)
+  void slab(const cpx<T>* mix, cpx<T>* out) {
+    SlabArgs<T> a = slab_args();
+    a.mixed = mix;
+    a.Ft = out;
+    a.xmode = XMODE_NONLINEAR;
+    for (int z0 = 0; z0 < N; z0 += G) {
+      a.z0 = z0;
+      a.G = (z0 + G <= N) ? G : N - z0;
+      k_yinv<T><<<dim3(M / TY, a.G), bdYi, smYi, st>>>(a);
+      k_xrow<T><<<(a.G * N + RX - 1) / RX, bdX, smX, st>>>(a);
+      k_yfwd<T><<<dim3(M / TY, a.G), bdYf, smYf, st>>>(a);
+    }
+    LAUNCH_CHECK();
+  }
+
+  PencilArgs<T> pencil_args(int mode) {
+    PencilArgs<T> a;
+    memset(&a, 0, sizeof(a));
+    a.N = N; a.M = M; a.TX = TX; a.pz = pz; a.tw = tw; a.mode = mode;
+    a.dt = (T)cur_dt; a.ifac = ifac; a.state = state; a.acc = acc;
+    a.trunc = c->p.truncation; a.K2max = c->K2max; a.Kimax = c->Kimax;
+    a.err = d_err;
+    if (fkind != NS_FORCE_NONE) {
+      a.shell = shell;
+      a.fK = fK;
+    }
+    return a;
+  }
+
+  void pencil(const PencilArgs<T>& a) {
+    k_pencil<T><<<(M / TX) * N, bdP, smP, st>>>(a);
+    LAUNCH_CHECK();
+  }
+
+  const cpx<T>* shift_tab(int idx) const { return idx < 0 ? nullptr : shtab + (size_t)idx * 3 * N; }
+
+  void upload_shifts(const std::vector<double>& sh) {
+    const size_t n = sh.size() / 3;
+    if (n == 0) return;
+    if (n > shtab_cap) {
+      cudaFree(shtab);
+      cudaFree(d_shifts);
+      shtab = nullptr;
+      d_shifts = nullptr;
+      CUDA_TRY(cudaMalloc(&shtab, n * 3 * N * sizeof(cpx<T>)));
+      CUDA_TRY(cudaMalloc(&d_shifts, n * 3 * sizeof(double)));
+      shtab_cap = n;
+    }
+    CUDA_TRY(cudaMemcpyAsync(d_shifts, sh.data(), n * 3 * sizeof(double), cudaMemcpyHostToDevice, st));
+    const int tot = (int)(n * 3 * N);
+    k_shift_tables<T><<<(tot + 255) / 256, 256, 0, st>>>(shtab, N, d_shifts, (int)n);
+    LAUNCH_CHECK();
+  }
+
+  void set_dt(double dt) {
+    if (dt == cur_dt) return;
+    k_ifac<T><<<(N + 255) / 256, 256, 0, st>>>(ifac, N, c->p.nu, dt, 0.5 * dt);
+    LAUNCH_CHECK();
+    cur_dt = dt;
+  }
+
+  // ---- forcing ------------------------------------------------------------------------
+  int fD1() const { return 2 * fK + 1; }
+  int fDn() const { return fD1() * fD1() * (fK + 1); }
+
+  // projected random pattern j on the dense table [3][D] (reading documented in ns.h)
+  void make_pattern(int64_t j, std::vector<cpx<double>>& out) {
+    const int K = fK, D1 = fD1(), D = fDn();
+    out.assign(3 * (size_t)D, mk<double>(0, 0));
+    // canonical modes in counter order
+    std::vector<int> modes;
+    for (int kz = -K; kz <= K; ++kz)
+      for (int ky = -K; ky <= K; ++ky)
+        for (int kx = 0; kx <= K; ++kx) {
+          const double k2 = kx * kx + ky * ky + kz * kz;
+          if (k2 < fkmin * fkmin || k2 > fkmax * fkmax) continue;
+          const bool canon = kx > 0 || kz > 0 || (kz == 0 && ky > 0);
+          if (canon && kx < M) {
+            modes.push_back(kx);
+            modes.push_back(ky);
+            modes.push_back(kz);
+          }
+        }
+    const int64_t Mm = (int64_t)modes.size() / 3;
+    auto idx = [&](int kx, int ky, int kz) { return ((kz + K) * D1 + (ky + K)) * (K + 1) + kx; };
+    for (int64_t m = 0; m < Mm; ++m) {
+      const int kx = modes[3 * m], ky = modes[3 * m + 1], kz = modes[3 * m + 2];
+      double g[3][2];
+      for (int comp = 0; comp < 3; ++comp) {
+        const uint64_t n = (uint64_t)((j * Mm + m) * 3 + comp);
+        const double u1 = uniform01(fseed, 2 * n), u2 = uniform01(fseed, 2 * n + 1);
+        const double r = std::sqrt(-2.0 * std::log(1.0 - u1));
+        const double th = 2.0 * M_PI * u2;
+        g[comp][0] = r * std::cos(th);
+        g[comp][1] = r * std::sin(th);
+      }
+      // Leray projection P(k) = I - k k / |k|^2
+      const double k[3] = {(double)kx, (double)ky, (double)kz};
+      const double k2 = k[0] * k[0] + k[1] * k[1] + k[2] * k[2];
+      double kd[2] = {0, 0};
+      for (int q = 0; q < 3; ++q) {
+        kd[0] += k[q] * g[q][0];
+        kd[1] += k[q] * g[q][1];
+      }
+      for (int q = 0; q < 3; ++q) {
+        const double re = g[q][0] - k[q] * kd[0] / k2, im = g[q][1] - k[q] * kd[1] / k2;
+        out[(size_t)q * D + idx(kx, ky, kz)] = mk<double>(re, im);
+        if (kx == 0) out[(size_t)q * D + idx(0, -ky, -kz)] = mk<double>(re, -im);
+      }
+    }
+  }
+
+  int64_t fj0 = 0;  // redraw index of fpat[0]
+
+  void prepare_forcing(double t0, double t1) {
+    const int64_t j0 = (int64_t)std::floor(t0 / ftcorr);
+    const int64_t j1 = (int64_t)std::floor(t1 / ftcorr) + 2;  // margin for rounding of stage times
+    const int n = (int)(j1 - j0 + 1);
+    const int D = fDn();
+    if (n > fpat_cap) {
+      cudaFree(fpat);
+      fpat = nullptr;
+      CUDA_TRY(cudaMalloc(&fpat, (size_t)n * 3 * D * sizeof(cpx<double>)));
+      fpat_cap = n;
+    }
+    std::vector<cpx<double>> all((size_t)n * 3 * D), one;
+    for (int i = 0; i < n; ++i) {
+      make_pattern(j0 + i, one);
+      std::copy(one.begin(), one.end(), all.begin() + (size_t)i * 3 * D);
+    }
+    CUDA_TRY(cudaMemcpy(fpat, all.data(), all.size() * sizeof(cpx<double>), cudaMemcpyHostToDevice));
+    fj0 = j0;
+  }
+
+  // forcing term of the coming pencil pass at time ts, from the state stored in `shell`
+  void force_coef(double ts, PencilArgs<T>& a) {
+    if (fkind == NS_FORCE_NONE) return;
+    const double x = ts / ftcorr;
+    const int64_t j = (int64_t)std::floor(x);
+    const double th = x - (double)j;
+    const int D = fDn();
+    if (j < fj0 || j - fj0 + 1 >= fpat_cap)
+      throw NsError{NS_ERR_INTERNAL, "forcing pattern index out of the prepared range"};
+    const cpx<double>* pj = fpat + (size_t)(j - fj0) * 3 * D;
+    k_force_coef<T><<<1, 256, 0, st>>>(pj, pj + 3 * D, th, shell, fK, cur_dt, feps, force, nullptr);
+    LAUNCH_CHECK();
+    a.force = force;
+  }
+
+  void set_forcing(int kind, double kfmin, double kfmax, double eps, double tcorr,
+                   uint64_t seed) override {
+    fkind = kind;
+    if (kind == NS_FORCE_NONE) return;
+    fkmin = kfmin; fkmax = kfmax; feps = eps; ftcorr = tcorr; fseed = seed;
+    fK = (int)std::floor(kfmax);
+    cudaFree(force);
+    cudaFree(shell);
+    force = shell = nullptr;
+    CUDA_TRY(cudaMalloc(&force, 3 * (size_t)fDn() * sizeof(cpx<T>)));
+    CUDA_TRY(cudaMalloc(&shell, 3 * (size_t)fDn() * sizeof(cpx<T>)));
+    CUDA_TRY(cudaMemsetAsync(shell, 0, 3 * (size_t)fDn() * sizeof(cpx<T>), st));
+  }
+
+  // ---- schemes ------------------------------------------------------------------------
+  void step(double dt, int nsteps) override {
+    set_dt(dt);
+    const int sch = c->p.scheme;
+    const double dx = 2.0 * M_PI / N;
+    const int CH = 256;  // steps per chunk of shift tables
+    for (int s0 = 0; s0 < nsteps; s0 += CH) {
+      const int ns = (s0 + CH <= nsteps) ? CH : nsteps - s0;
+      const bool last_chunk = s0 + ns == nsteps;
+      if (fkind != NS_FORCE_NONE) prepare_forcing(c->t, c->t + ns * dt);
+      if (sch == NS_RK2_PS_RANDOM || sch == NS_RK2_PS_APPROX) {
+        // shift vectors: [2n] alpha_n, [2n+1] beta_n
+        std::vector<double> sh(6 * (size_t)ns);
+        for (int n = 0; n < ns; ++n) {
+          double da[3] = {0, 0, 0};
+          if (sch == NS_RK2_PS_RANDOM) {
+            if (c->override_pos < c->override_shifts.size()) {
+              for (int i = 0; i < 3; ++i) da[i] = c->override_shifts[c->override_pos + i];
+              c->override_pos += 3;
+            } else {
+              for (int i = 0; i < 3; ++i)
+                da[i] = dx * uniform01(c->p.seed, (uint64_t)(3 * (c->step + n) + i));
+            }
+          }
+          for (int i = 0; i < 3; ++i) {
+            sh[6 * n + i] = da[i];
+            sh[6 * n + 3 + i] = da[i] + 0.5 * dx;
+          }
+        }
+        upload_shifts(sh);
+        run_rogallo(dt, ns, sch == NS_RK2_PS_APPROX);
+      } else if (sch == NS_RK2_PS_EXACT) {
+        std::vector<double> sh = {0.5 * dx, 0.5 * dx, 0.5 * dx};
+        upload_shifts(sh);
+        run_rk2(dt, ns, true);
+      } else if (sch == NS_RK2) {
+        run_rk2(dt, ns, false);
+      } else {
+        run_rk4(dt, ns);
+      }
+      (void)last_chunk;
+    }
+    sync_check();
+  }
+
+  void init_pass(int nOut, const cpx<T>* o0, const cpx<T>* o1) {
+    PencilArgs<T> a = pencil_args(MODE_INIT);
+    a.src = state;
+    a.nOut = nOut;
+    a.osh[0] = o0; a.out[0] = mixed[0];
+    a.osh[1] = o1; a.out[1] = mixed[1];
+    pencil(a);
+  }
+
+  void run_rogallo(double dt, int ns, bool approx) {
+    const T w = (T)(1.0 / ((double)N * N * N));
+    auto alpha = [&](int n) -> const cpx<T>* { return approx ? nullptr : shift_tab(2 * n); };
+    auto beta = [&](int n) -> const cpx<T>* { return shift_tab(2 * n + 1); };
+    init_pass(1, alpha(0), nullptr);
+    for (int n = 0; n < ns; ++n) {
+      const double t = c->t;
+      slab(mixed[0], Ft[0]);
+      PencilArgs<T> a = pencil_args(MODE_ROG_1);
+      force_coef(t, a);
+      a.nF = 1; a.F[0] = Ft[0]; a.dsh[0] = alpha(n); a.wF[0] = w;
+      a.nOut = 1; a.osh[0] = beta(n); a.out[0] = mixed[0];
+      pencil(a);
+      slab(mixed[0], Ft[0]);
+      PencilArgs<T> b = pencil_args(MODE_ROG_2);
+      force_coef(t + dt, b);
+      b.nF = 1; b.F[0] = Ft[0]; b.dsh[0] = beta(n); b.wF[0] = w;
+      b.nOut = (n + 1 < ns) ? 1 : 0;
+      b.osh[0] = (n + 1 < ns) ? alpha(n + 1) : nullptr;
+      b.out[0] = mixed[0];
+      if (fkind != NS_FORCE_NONE && b.nOut == 0) b.nOut = 0;
+      pencil(b);
+      c->t = t + dt;
+      c->step += 1;
+    }
+  }
+
+  void run_rk2(double dt, int ns, bool exact) {
+    const T w = (T)(1.0 / ((double)N * N * N));
+    const cpx<T>* iso = exact ? shift_tab(0) : nullptr;
+    init_pass(exact ? 2 : 1, nullptr, iso);
+    for (int n = 0; n < ns; ++n) {
+      const double t = c->t;
+      for (int stg = 0; stg < 2; ++stg) {
+        slab(mixed[0], Ft[0]);
+        if (exact) slab(mixed[1], Ft[1]);
+        PencilArgs<T> a = pencil_args(stg == 0 ? MODE_RK2_1 : MODE_RK2_2);
+        force_coef(stg == 0 ? t : t + 0.5 * dt, a);
+        a.nF = exact ? 2 : 1;
+        a.F[0] = Ft[0]; a.dsh[0] = nullptr; a.wF[0] = exact ? (T)0.5 * w : w;
+        a.F[1] = Ft[1]; a.dsh[1] = iso; a.wF[1] = (T)0.5 * w;
+        const bool out = stg == 0 || n + 1 < ns;
+        a.nOut = out ? (exact ? 2 : 1) : 0;
+        a.osh[0] = nullptr; a.out[0] = mixed[0];
+        a.osh[1] = iso; a.out[1] = mixed[1];
+        pencil(a);
+      }
+      c->t = t + dt;
+      c->step += 1;
+    }
+  }
+
+  void run_rk4(double dt, int ns) {
+    const T w = (T)(1.0 / ((double)N * N * N));
+    init_pass(1, nullptr, nullptr);
+    const int modes[4] = {MODE_RK4_1, MODE_RK4_2, MODE_RK4_3, MODE_RK4_4};
+    const double ts[4] = {0.0, 0.5, 0.5, 1.0};
+    for (int n = 0; n < ns; ++n) {
+      const double t = c->t;
+      for (int stg = 0; stg < 4; ++stg) {
+        slab(mixed[0], Ft[0]);
+        PencilArgs<T> a = pencil_args(modes[stg]);
+        force_coef(t + ts[stg] * dt, a);
+        a.nF = 1; a.F[0] = Ft[0]; a.wF[0] = w;
+        a.nOut = (stg < 3 || n + 1 < ns) ? 1 : 0;
+        a.out[0] = mixed[0];
+        pencil(a);
+      }
+      c->t = t + dt;
+      c->step += 1;
+    }
+  }
+
+  // ---- transfers ----------------------------------------------------------------------
+  void set_velocity(const double* u) override {
+    const size_t n = 3 * (size_t)N * N * N;
+    std::vector<T> h(n);
+    for (size_t i = 0; i < n; ++i) h[i] = (T)u[i];
+    T* rin = reinterpret_cast<T*>(mixed[0]);  // 5 N^3 reals >= 3 N^3
+    CUDA_TRY(cudaMemcpyAsync(rin, h.data(), n * sizeof(T), cudaMemcpyHostToDevice, st));
+    SlabArgs<T> a = slab_args();
+    a.rio = rin;
+    a.Ft = Ft[0];
+    a.xmode = XMODE_R2C;
+    for (int z0 = 0; z0 < N; z0 += G) {
+      a.z0 = z0;
+      a.G = (z0 + G <= N) ? G : N - z0;
+      k_xrow<T><<<(a.G * N + RX - 1) / RX, bdX, smX, st>>>(a);
+      k_yfwd<T><<<dim3(M / TY, a.G), bdYf, smYf, st>>>(a);
+    }
+    LAUNCH_CHECK();
+    PencilArgs<T> p = pencil_args(MODE_PROJECT);
+    p.shell = nullptr;
+    p.nF = 1; p.F[0] = Ft[0]; p.wF[0] = (T)(1.0 / ((double)N * N * N));
+    pencil(p);
+    sync_check();
+  }
+
+  void get_velocity(double* u) override {
+    PencilArgs<T> p = pencil_args(MODE_INIT);
+    p.shell = nullptr;
+    p.src = state;
+    p.nOut = 1; p.out[0] = mixed[0];
+    pencil(p);
+    T* rout = reinterpret_cast<T*>(Ft[0]);  // 3 N^3 reals
+    SlabArgs<T> a = slab_args();
+    a.mixed = mixed[0];
+    a.rio = rout;
+    a.xmode = XMODE_C2R;
+    for (int z0 = 0; z0 < N; z0 += G) {
+      a.z0 = z0;
+      a.G = (z0 + G <= N) ? G : N - z0;
+      k_yinv<T><<<dim3(M / TY, a.G), bdYi, smYi, st>>>(a);
+      k_xrow<T><<<(a.G * N + RX - 1) / RX, bdX, smX, st>>>(a);
+    }
+    LAUNCH_CHECK();
+    const size_t n = 3 * (size_t)N * N * N;
+    std::vector<T> h(n);
+    CUDA_TRY(cudaMemcpyAsync(h.data(), rout, n * sizeof(T), cudaMemcpyDeviceToHost, st));
+    sync_check();
+    for (size_t i = 0; i < n; ++i) u[i] = (double)h[i];
+  }
+
+  void download(const cpx<T>* src, double* out) {
+    const size_t n = 3 * F1;
+    std::vector<cpx<T>> h(n);
+    CUDA_TRY(cudaMemcpyAsync(h.data(), src, n * sizeof(cpx<T>), cudaMemcpyDeviceToHost, st));
+    sync_check();
+    for (size_t i = 0; i < n; ++i) {
+      out[2 * i] = (double)h[i].x;
+      out[2 * i + 1] = (double)h[i].y;
+    }
+  }
+
+  void upload(const double* in, cpx<T>* dst) {
+    const size_t n = 3 * F1;
+    std::vector<cpx<T>> h(n);
+    for (size_t i = 0; i < n; ++i) h[i] = mk<T>((T)in[2 * i], (T)in[2 * i + 1]);
+    CUDA_TRY(cudaMemcpyAsync(dst, h.data(), n * sizeof(cpx<T>), cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+  }
+
+  void get_state(double* s) override { download(state, s); }
+  void set_state(const double* s) override { upload(s, state); }
+
+  void nonlinear(const double* in, const double* delta, double* out) override {
+    const cpx<T>* src = state;
+    if (in) {
+      upload(in, acc);
+      src = acc;
+    }
+    std::vector<double> sh(delta, delta + 3);
+    upload_shifts(sh);
+    PencilArgs<T> p = pencil_args(MODE_INIT);
+    p.shell = nullptr;
+    p.src = src;
+    p.nOut = 1; p.osh[0] = shift_tab(0); p.out[0] = mixed[0];
+    pencil(p);
+    slab(mixed[0], Ft[0]);
+    PencilArgs<T> q = pencil_args(MODE_NL);
+    q.shell = nullptr;
+    q.nF = 1; q.F[0] = Ft[0]; q.dsh[0] = shift_tab(0); q.wF[0] = (T)(1.0 / ((double)N * N * N));
+    pencil(q);
+    download(acc, out);
+  }
+
+  void energy(double* E, double* eps) override {
+    const int nb = red_blocks;
+    k_energy<T><<<nb, 256, 0, st>>>(state, N, c->p.nu, red);
+    k_sum_pairs<<<1, 256, 0, st>>>(red, nb, red + 2 * nb);
+    LAUNCH_CHECK();
+    double h[2];
+    CUDA_TRY(cudaMemcpyAsync(h, red + 2 * nb, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    sync_check();
+    *E = h[0];
+    *eps = h[1];
+  }
+
+  void spectrum(int kind, double* out, int nbins) override {
+    // partial bins [nb][nbins] followed by the final [nbins] in the reduction buffer
+    const size_t cap = (size_t)red_blocks * 1024;
+    int nb = (int)(cap / (size_t)nbins) - 1;
+    if (nb > red_blocks) nb = red_blocks;
+    if (nb < 1) throw NsError{NS_ERR_INVALID_ARG, "nbins too large"};
+    k_spectrum<T><<<nb, 256, nbins * sizeof(double), st>>>(state, N, kind, nbins, red);
+    double* fin = red + (size_t)nb * nbins;
+    k_spectrum_final<<<(nbins + 127) / 128, 128, 0, st>>>(red, nb, nbins, fin);
+    LAUNCH_CHECK();
+    CUDA_TRY(cudaMemcpyAsync(out, fin, nbins * sizeof(double), cudaMemcpyDeviceToHost, st));
+    sync_check();
+  }
+};
+
+int fail(ns_ctx* c, int code, const std::string& msg) {
+  if (c) c->err = msg;
+  return code;
+}
+
+template <typename F>
+int guarded(ns_ctx* c, F&& f) {
+  if (!c) return NS_ERR_INVALID_ARG;
+  try {
+    if (c->p.device >= 0) {
+      cudaError_t e = cudaSetDevice(c->p.device);
+      if (e != cudaSuccess) return fail(c, NS_ERR_CUDA, std::string("cudaSetDevice: ") + cudaGetErrorString(e));
+    }
+    return f();
+  } catch (const NsError& e) {
+    return fail(c, e.code, e.msg);
+  } catch (const std::bad_alloc&) {
+    return fail(c, NS_ERR_OOM, "host allocation failed");
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* ns_init_error(void) { return g_init_error.c_str(); }
+
+int ns_init_ex(ns_ctx** out, const ns_params* prm) {
+  if (!out || !prm) {
+    g_init_error = "NULL argument";
+    return NS_ERR_INVALID_ARG;
+  }
+  *out = nullptr;
+  const ns_params& p = *prm;
+  if (p.N < 8 || p.N > 1024 || p.N % 2 != 0 || !is_2a3b(p.N)) {
+    g_init_error = "N must be even, of the form 2^a 3^b, with 8 <= N <= 1024";
+    return NS_ERR_UNSUPPORTED_N;
+  }
+  if (!(std::fabs(p.L - 2.0 * M_PI) <= 1e-12)) {
+    g_init_error = "L must be 2*pi";
+    return NS_ERR_INVALID_ARG;
+  }
+  if (!(p.nu >= 0.0) || !std::isfinite(p.nu)) {
+    g_init_error = "nu must be finite and >= 0";
+    return NS_ERR_INVALID_ARG;
+  }
+  if (!(p.kmax > 0.0) || p.kmax > 0.5 * p.N) {
+    g_init_error = "kmax must satisfy 0 < kmax <= N/2";
+    return NS_ERR_KMAX;
+  }
+  if (p.truncation != NS_TRUNC_SPHERICAL && p.truncation != NS_TRUNC_CUBIC) {
+    g_init_error = "unknown truncation";
+    return NS_ERR_INVALID_ARG;
+  }
+  if (p.scheme < NS_RK2 || p.scheme > NS_RK2_PS_RANDOM) {
+    g_init_error = "unknown scheme";
+    return NS_ERR_INVALID_ARG;
+  }
+  if (p.precision != NS_FP32 && p.precision != NS_FP64) {
+    g_init_error = "unknown precision";
+    return NS_ERR_INVALID_ARG;
+  }
+  ns_ctx* c = new ns_ctx();
+  c->p = p;
+  {
+    const double q = p.kmax * p.kmax;
+    double m = std::floor(q);
+    if (m == q) m -= 1;
+    c->K2max = (int)m;
+    double r = std::floor(p.kmax);
+    if (r == p.kmax) r -= 1;
+    c->Kimax = (int)r;
+  }
+  try {
+    CUDA_TRY(cudaSetDevice(p.device));
+    if (p.stream) {
+      c->stream = (cudaStream_t)p.stream;
+    } else {
+      CUDA_TRY(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+      c->own_stream = true;
+    }
+    if (p.precision == NS_FP32)
+      c->solver = new Solver<float>(c);
+    else
+      c->solver = new Solver<double>(c);
+  } catch (const NsError& e) {
+    g_init_error = e.msg;
+    delete c->solver;
+    if (c->own_stream) cudaStreamDestroy(c->stream);
+    delete c;
+    return e.code;
+  }
+  *out = c;
+  return NS_OK;
+}
+
+int ns_init(ns_ctx** ctx, int N, double L, double nu, double kmax, int truncation, int scheme) {
+  ns_params p;
+  memset(&p, 0, sizeof(p));
+  p.N = N; p.L = L; p.nu = nu; p.kmax = kmax; p.truncation = truncation; p.scheme = scheme;
+  p.precision = NS_FP32; p.device = 0; p.stream = nullptr; p.seed = 0;
+  return ns_init_ex(ctx, &p);
+}
+
+int ns_destroy(ns_ctx* c) {
+  if (!c) return NS_OK;
+  cudaSetDevice(c->p.device);
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  delete c->solver;
+  if (c->own_stream) cudaStreamDestroy(c->stream);
+  delete c;
+  return NS_OK;
+}
+
+const char* ns_last_error(ns_ctx* c) { return c ? c->err.c_str() : "NULL context"; }
+
+int ns_set_velocity(ns_ctx* c, const double* u) {
+  return guarded(c, [&]() {
+    if (!u) return fail(c, NS_ERR_INVALID_ARG, "u is NULL");
+    c->solver->set_velocity(u);
+    c->t = 0.0;
+    c->step = 0;
+    c->have_state = true;
+    return (int)NS_OK;
+  });
+}
+
+int ns_get_velocity(ns_ctx* c, double* u) {
+  return guarded(c, [&]() {
+    if (!u) return fail(c, NS_ERR_INVALID_ARG, "u_out is NULL");
+    c->solver->get_velocity(u);
+    return (int)NS_OK;
+  });
+}
+
+int ns_get_state(ns_ctx* c, double* s) {
+  return guarded(c, [&]() {
+    if (!s) return fail(c, NS_ERR_INVALID_ARG, "re_im_out is NULL");
+    c->solver->get_state(s);
+    return (int)NS_OK;
+  });
+}
+
+int ns_set_state(ns_ctx* c, const double* s) {
+  return guarded(c, [&]() {
+    if (!s) return fail(c, NS_ERR_INVALID_ARG, "re_im is NULL");
+    c->solver->set_state(s);
+    c->have_state = true;
+    return (int)NS_OK;
+  });
+}
+
+int ns_set_forcing(ns_ctx* c, int kind, double kf_min, double kf_max, double eps, double t_corr,
+                   uint64_t seed) {
+  return guarded(c, [&]() {
+    if (kind == NS_FORCE_NONE) {
+      c->solver->set_forcing(kind, 0, 0, 0, 1, 0);
+      return (int)NS_OK;
+    }
+    if (kind != NS_FORCE_TCRANDOM_CONST_EPS) return fail(c, NS_ERR_INVALID_ARG, "unknown forcing kind");
+    if (!(kf_min >= 1.0) || !(kf_max >= kf_min) || kf_max > 8.0 || kf_max >= 0.5 * c->p.N ||
+        kf_max >= c->p.kmax)
+      return fail(c, NS_ERR_INVALID_ARG, "need 1 <= kf_min <= kf_max <= 8, kf_max < min(N/2, kmax)");
+    if (!(t_corr > 0.0) || !(eps >= 0.0) || !std::isfinite(eps))
+      return fail(c, NS_ERR_INVALID_ARG, "need t_corr > 0 and finite eps >= 0");
+    c->solver->set_forcing(kind, kf_min, kf_max, eps, t_corr, seed);
+    return (int)NS_OK;
+  });
+}
+
+int ns_step(ns_ctx* c, double dt, int nsteps) {
+  return guarded(c, [&]() {
+    if (!c->have_state) return fail(c, NS_ERR_STATE, "no velocity or state set");
+    if (!(dt > 0.0) || !std::isfinite(dt) || nsteps < 0) return fail(c, NS_ERR_INVALID_ARG, "need dt > 0, nsteps >= 0");
+    if (nsteps == 0) return (int)NS_OK;
+    c->solver->step(dt, nsteps);
+    return (int)NS_OK;
+  });
+}
+
+int ns_set_shifts(ns_ctx* c, const double* da, int nsteps) {
+  return guarded(c, [&]() {
+    if (nsteps < 0 || (nsteps > 0 && !da)) return fail(c, NS_ERR_INVALID_ARG, "bad shifts");
+    c->override_shifts.assign(da, da + 3 * (size_t)nsteps);
+    c->override_pos = 0;
+    return (int)NS_OK;
+  });
+}
+
+int ns_nonlinear(ns_ctx* c, const double* in, const double* delta, double* out) {
+  return guarded(c, [&]() {
+    if (!delta || !out) return fail(c, NS_ERR_INVALID_ARG, "NULL delta or output");
+    if (!in && !c->have_state) return fail(c, NS_ERR_STATE, "no state");
+    c->solver->nonlinear(in, delta, out);
+    return (int)NS_OK;
+  });
+}
+
+int ns_energy(ns_ctx* c, double* E, double* eps) {
+  return guarded(c, [&]() {
+    if (!E || !eps) return fail(c, NS_ERR_INVALID_ARG, "NULL output");
+    c->solver->energy(E, eps);
+    if (!std::isfinite(*E) || !std::isfinite(*eps)) return fail(c, NS_ERR_NONFINITE, "energy is not finite");
+    return (int)NS_OK;
+  });
+}
+
+int ns_energy_spectrum(ns_ctx* c, int kind, double* out, int nbins) {
+  return guarded(c, [&]() {
+    if (!out || nbins <= 0 || nbins > 4096) return fail(c, NS_ERR_INVALID_ARG, "need out != NULL, 0 < nbins <= 4096");
+    if (kind < NS_SPEC_SHELL || kind > NS_SPEC_Z) return fail(c, NS_ERR_INVALID_ARG, "unknown spectrum kind");
+    c->solver->spectrum(kind, out, nbins);
+    return (int)NS_OK;
+  });
+}
+
+int ns_time(ns_ctx* c, double* t, int64_t* step) {
+  if (!c) return NS_ERR_INVALID_ARG;
+  if (t) *t = c->t;
+  if (step) *step = c->step;
+  return NS_OK;
+}
+
+int ns_set_time(ns_ctx* c, double t, int64_t step) {
+  if (!c) return NS_ERR_INVALID_ARG;
+  c->t = t;
+  c->step = step;
+  return NS_OK;
+}
+
+int ns_device_state(ns_ctx* c, void** state, void** stream, int* precision) {
+  if (!c) return NS_ERR_INVALID_ARG;
+  if (state) *state = c->solver->state_ptr();
+  if (stream) *stream = (void*)c->stream;
+  if (precision) *precision = c->p.precision;
+  return NS_OK;
+}
+
+double ns_model_bytes_per_step(ns_ctx* c) {
+  if (!c) return 0.0;
+  const double C = (double)c->p.N * c->p.N * c->p.N * (c->p.precision == NS_FP64 ? 8.0 : 4.0);
+  switch (c->p.scheme) {
+    case NS_RK2: return 41.0 * C;
+    case NS_RK4: return 94.0 * C;
+    case NS_RK2_PS_EXACT: return 73.0 * C;
+    default: return 44.0 * C;
+  }
+}
+
+}  // extern "C"
