@@ -1,0 +1,357 @@
+#!/usr/bin/env python
+"""Benchmark: phase-shift RK2 steps/s and Gcells/s vs RK4 + 2/3 truncation at the same kmax.
+
+Workload (timed `--steps` steps, one JSON line on rank 0):
+  Taylor-Green vortex (Sec. 3.4, Eq. T-G-init), Re = 1/nu = 1600, 256^3, L = 2 pi,
+  RK2 phase-shift random (Rogallo) with spherical truncation C_t = 1 (kmax = 128),
+  FP32 butterflies and products, FP64 tables and reductions, dt from CFL 0.5 with the
+  CFL frequency summed over directions (dt = 0.5 dx / 2 for this field) and rounded so
+  that t = 9 lands on a step, shifts from splitmix64 seed 12345.
+  Comparison leg: RK4 + 2/3 spherical truncation at 384^3 (kmax = 128, same dt rule).
+
+Per step the state (201 MB) and the moved data (2.95 GB by the two-pass byte model) are
+larger than the 129 MB L2, so no L2 flush is needed between steps.
+
+--impl reference times the FP64 CPU oracle on the host cores on the same workload (a
+bounded number of whole steps).  Under torchrun (N > 1) every rank runs an independent
+replica (weak scaling, no collective on the data path) and value = all ranks' steps / the
+slowest rank's time.
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "phase-shift RK2 steps/s & Gcells/s vs RK4+2/3 at same kmax; % HBM roofline"
+N_PS, N_RK4, KMAX, NU, SEED, CFL, T_END = 256, 384, 128.0, 1.0 / 1600.0, 12345, 0.5, 9.0
+WORKLOAD = ("Taylor-Green Re=1600, 256^3, RK2 phase-shift random (Rogallo), spherical C_t=1 "
+            "(kmax=128), FP32 bulk / FP64 reductions, dt = 0.5 / sum_i(max|u_i|/dx) (t=9 on a step)")
+
+
+def dt_for(N):
+    """dt = CFL / sum_i(max|u_i| / dx), rounded down so that t = 9 lands on a step.
+
+    For the Taylor-Green field max|u_x| = max|u_y| = 1 and u_z = 0, so dt = CFL dx / 2.
+    """
+    dt = CFL / (2.0 / (2 * math.pi / N))
+    return T_END / math.ceil(T_END / dt)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--rk4-steps", type=int, default=30)
+    ap.add_argument("--e2e-steps", type=int, default=50)
+    ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
+    ap.add_argument("--no-rk4", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("ns_fft.cuh", "ns_kernels.cuh"):
+        with open(os.path.join(ROOT, "paper_2603_08892_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel):
+    """DRAM bytes per launch from the committed ncu summary, if it matches the kernels."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "ncu_traffic.json")) as f:
+            d = json.load(f)
+        if d.get("kernel_source_hash") != kernel_source_hash():
+            return None
+        return d["kernels"][kernel]["dram_bytes_per_launch_full_size"]
+    except Exception:
+        return None
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, local_rank):
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+        ids = [v for v in vis.split(",") if v.strip()]
+        self.idx = ids[local_rank] if local_rank < len(ids) else str(local_rank)
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(
+                ["nvidia-smi", "-i", self.idx, "--query-gpu=" + self.Q, "--format=csv,noheader",
+                 "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if self.p is None:
+            return out
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1].split()[0]))
+                smax.append(float(parts[2].split()[0]))
+            except Exception:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.f.name)
+        if sm:
+            out = {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                   "reasons": sorted(reasons), "samples": len(sm)}
+        return out
+
+
+def reduce_max(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def cpu_oracle_rate(budget_s=60.0, max_steps=3, warmup=0):
+    """Oracle steps/s on the workload (whole 256^3 steps, bounded by a wall-time budget)."""
+    from oracle import rng as orng
+    from oracle import schemes as sc
+    from oracle import spectral as osp
+    from paper_2603_08892_gb300 import inputs
+
+    N = N_PS
+    dt = dt_for(N)
+    prob = sc.Problem(N, NU, KMAX)
+    S = osp.set_velocity(inputs.taylor_green(N), KMAX)
+    for n in range(warmup):
+        S = sc.step_ps_random(S, dt, prob, orng.shift_alpha(SEED, n, N))
+    t0 = time.perf_counter()
+    n = 0
+    while n < max_steps:
+        S = sc.step_ps_random(S, dt, prob, orng.shift_alpha(SEED, warmup + n, N))
+        n += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    el = time.perf_counter() - t0
+    return n / el, n, el
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    steps = max(1, args.steps)
+    rate, n, el = cpu_oracle_rate(budget_s=150.0, max_steps=steps, warmup=min(args.warmup, 1))
+    cores = 1  # numpy.fft (pocketfft) and numpy elementwise run on one thread
+    line = {
+        "impl": "reference", "metric": METRIC, "value": rate, "unit": "steps/s",
+        "n_gpus": args.gpus, "steps": n, "warmup": min(args.warmup, 1),
+        "ms_per_step": 1000.0 * el / n, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic (Taylor-Green field, Eq. T-G-init)",
+        "config": {"workload": WORKLOAD + " -- FP64 CPU oracle", "N": N_PS, "dt": dt_for(N_PS)},
+        "gcells_per_s": rate * N_PS ** 3 / 1e9,
+        "cpu_baseline": {"value": rate, "unit": "steps/s", "cores": cores, "kind": "oracle",
+                         "sample": "%d whole 256^3 steps after %d warm-up step(s), %.1f s"
+                                   % (n, min(args.warmup, 1), el)},
+        "e2e": {"value": rate, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def timed_steps(ns, s, dt, K, stream):
+    import torch
+
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    s.step(dt, K)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    import numpy as np
+    import torch
+
+    from paper_2603_08892_gb300 import binding as ns
+    from paper_2603_08892_gb300 import inputs
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    stream = torch.cuda.Stream()
+    W = max(3, args.warmup)
+    K = max(1, args.steps)
+    dt = dt_for(N_PS)
+    u0 = inputs.taylor_green(N_PS)
+
+    s = ns.Solver(N_PS, NU, KMAX, scheme=ns.RK2_PS_RANDOM, precision=ns.FP32, device=local,
+                  stream=stream.cuda_stream, seed=SEED + rank)
+    s.set_velocity(u0)
+    s.step(dt, W)
+    clocks = Clocks(local)
+    s.profile(True)
+    barrier(world)
+    clocks.start()
+    ms = timed_steps(ns, s, dt, K, stream)
+    clk = clocks.stop()
+    prof = s.profile_read()
+    s.profile(False)
+    E, eps = s.energy()
+    ms_max = reduce_max(ms, world)
+    barrier(world)
+
+    C = N_PS ** 3 * 4.0
+    model_bytes = s.model_bytes_per_step()
+    value = world * K / (ms_max / 1000.0)
+    ms_step = ms_max / K
+    hbm, peak_kind = peaks()
+
+    # dominant kernel and its algorithmic bytes per launch
+    nchunks = (K + 255) // 256
+    pencil_bytes = (8.0 + 28.0 * K - 5.0) * C  # INIT + 2 pencil passes/step, last has no output
+    G_planes = max(1, min(N_PS, int((48 << 20) // (6 * N_PS * (N_PS // 2) * 8))))
+    kinds = {"k_pencil": pencil_bytes / prof["k_pencil"][2],
+             "k_yinv": 5.0 * C * G_planes / N_PS,
+             "k_yfwd": 3.0 * C * G_planes / N_PS,
+             "k_xrow": 0.0}
+    tot = {k: prof[k][0] for k in kinds}
+    dom = max(tot, key=tot.get)
+    avg_ms = prof[dom][0] / max(1, prof[dom][1])
+    achieved = kinds[dom] / (avg_ms / 1000.0) / 1e9
+    shares = {k: round(tot[k] / max(1e-9, sum(tot.values())), 4) for k in tot}
+    launches = sum(prof[k][2] for k in ("k_pencil", "k_yinv", "k_xrow", "k_yfwd")) + nchunks
+    roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
+            "frac": achieved / hbm, "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)",
+            "algorithmic_bytes_per_launch": kinds[dom], "avg_launch_ms": avg_ms,
+            "traffic": ncu_traffic(dom), "kernel_time_shares": shares,
+            "step_model_bytes": model_bytes,
+            "step_frac": (model_bytes / (ms_step / 1000.0) / 1e9) / hbm}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": K,
+        "warmup": W, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (Taylor-Green initial field, Eq. T-G-init; no dataset)",
+        "config": {"workload": WORKLOAD, "N": N_PS, "kmax": KMAX, "nu": NU, "dt": dt,
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "l2": "no flush: state 201 MB and 2.95 GB moved per step exceed the 129 MB L2"},
+        "gcells_per_s": value * N_PS ** 3 / 1e9,
+        "sim_time_per_s": value * dt / world,
+        "energy_at_end": E, "dissipation_at_end": eps,
+        "roofline": roof, "gpu_launches": launches, "clocks": clk,
+    }
+
+    # RK4 + 2/3 truncation at 384^3, same kmax (comparison leg)
+    if not args.no_rk4:
+        dt4 = dt_for(N_RK4)
+        r = ns.Solver(N_RK4, NU, KMAX, scheme=ns.RK4, precision=ns.FP32, device=local,
+                      stream=stream.cuda_stream)
+        r.set_velocity(inputs.taylor_green(N_RK4))
+        r.step(dt4, 2)
+        Kr = max(3, args.rk4_steps)
+        ms4 = reduce_max(timed_steps(ns, r, dt4, Kr, stream), world)
+        rate4 = world * Kr / (ms4 / 1000.0)
+        mb4 = r.model_bytes_per_step()
+        line["rk4_two_thirds"] = {
+            "N": N_RK4, "kmax": KMAX, "dt": dt4, "steps": Kr, "steps_per_s": rate4,
+            "gcells_per_s": rate4 * N_RK4 ** 3 / 1e9, "sim_time_per_s": rate4 * dt4 / world,
+            "ms_per_step": ms4 / Kr, "step_frac_hbm": (mb4 / (ms4 / Kr / 1000.0) / 1e9) / hbm}
+        line["sim_time_speedup_vs_rk4"] = line["sim_time_per_s"] / line["rk4_two_thirds"]["sim_time_per_s"]
+        r.close()
+
+    # end to end through the C ABI with host buffers: host velocity in, E/eps out every step
+    Ke = max(3, min(args.e2e_steps, K))
+    s.step(dt, 1)
+    barrier(world)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    s.set_velocity(u0)
+    for _ in range(Ke):
+        s.step(dt, 1)
+        s.energy()
+    torch.cuda.synchronize()
+    el = reduce_max(time.perf_counter() - t0, world)
+    h2d = (3 * N_PS ** 3 * 4 + Ke * 48) / Ke
+    line["e2e"] = {"value": world * Ke / el, "unit": "steps/s", "h2d_bytes_per_step": h2d,
+                   "d2h_bytes_per_step": 16,
+                   "what": "ns_set_velocity(host 3x256^3 f64) once + per step ns_step(dt,1) and "
+                           "ns_energy (E, eps to host); %d steps" % Ke}
+    s.close()
+
+    if rank == 0 and world == 1 and not args.no_cpu:
+        rate, n, el = cpu_oracle_rate(budget_s=40.0, max_steps=2)
+        line["cpu_baseline"] = {"value": rate, "unit": "steps/s", "cores": 1, "kind": "oracle",
+                                "sample": "%d whole 256^3 Rogallo steps of the FP64 NumPy oracle "
+                                          "(single-threaded pocketfft), %.1f s" % (n, el)}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -125,6 +125,16 @@ int ns_set_time(ns_ctx* ctx, double t, int64_t step);
  * ([3][N][N][N/2] complex of the context's precision) and the stream. */
 int ns_device_state(ns_ctx* ctx, void** state, void** stream, int* precision);
 
+/* Per-kernel timing with CUDA events recorded on the context's stream around every launch
+ * (at most 65536 launches are timed; all are counted).  ns_profile(ctx, 1) resets the
+ * counters and starts timing, ns_profile(ctx, 0) stops.  ns_profile_read synchronises the
+ * stream and returns, for one kind, the summed event time in ms, the number of timed
+ * launches and the number of launches since the reset.  Kinds: */
+enum { NS_PROF_PENCIL = 0, NS_PROF_YINV = 1, NS_PROF_XROW = 2, NS_PROF_YFWD = 3,
+       NS_PROF_SLAB_PASS = 4, NS_PROF_KINDS = 5 };
+int ns_profile(ns_ctx* ctx, int enable);
+int ns_profile_read(ns_ctx* ctx, int kind, double* total_ms, int64_t* timed, int64_t* launches);
+
 /* Bytes moved to/from HBM per time step by the algorithmic two-pass model (one slab and
  * one pencil pass per evaluation), for roofline reporting. */
 double ns_model_bytes_per_step(ns_ctx* ctx);

@@ -71,12 +71,17 @@ _set_time = _sig("ns_set_time", ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_in
 _device_state = _sig("ns_device_state", ctypes.c_int,
                      [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(ctypes.c_int)])
 _model_bytes = _sig("ns_model_bytes_per_step", ctypes.c_double, [_vp])
+_profile = _sig("ns_profile", ctypes.c_int, [_vp, ctypes.c_int])
+_profile_read = _sig("ns_profile_read", ctypes.c_int,
+                     [_vp, ctypes.c_int, _dp, ctypes.POINTER(ctypes.c_int64),
+                      ctypes.POINTER(ctypes.c_int64)])
+PROF_KINDS = {"k_pencil": 0, "k_yinv": 1, "k_xrow": 2, "k_yfwd": 3, "slab_pass": 4}
 
 EXPORTED = ["ns_init", "ns_init_ex", "ns_init_error", "ns_destroy", "ns_last_error",
             "ns_set_velocity", "ns_get_velocity", "ns_get_state", "ns_set_state",
             "ns_set_forcing", "ns_step", "ns_set_shifts", "ns_nonlinear", "ns_energy",
             "ns_energy_spectrum", "ns_time", "ns_set_time", "ns_device_state",
-            "ns_model_bytes_per_step"]
+            "ns_model_bytes_per_step", "ns_profile", "ns_profile_read"]
 
 
 class NSError(RuntimeError):
@@ -199,3 +204,17 @@ class Solver:
 
     def model_bytes_per_step(self):
         return _model_bytes(self._h)
+
+    def profile(self, enable=True):
+        self._check(_profile(self._h, 1 if enable else 0))
+
+    def profile_read(self):
+        """{kind: (total_ms, timed_launches, launches)} since the last profile() call."""
+        out = {}
+        for name, k in PROF_KINDS.items():
+            ms = ctypes.c_double()
+            n = ctypes.c_int64()
+            nl = ctypes.c_int64()
+            self._check(_profile_read(self._h, k, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(nl)))
+            out[name] = (ms.value, n.value, nl.value)
+        return out

@@ -103,6 +103,8 @@ struct SolverBase {
   virtual void set_forcing(int kind, double kfmin, double kfmax, double eps, double tcorr,
                            uint64_t seed) = 0;
   virtual void* state_ptr() = 0;
+  virtual void profile(int on) = 0;
+  virtual void profile_read(int k, double* ms, int64_t* n, int64_t* launches) = 0;
 };
 
 }  // namespace
@@ -163,6 +165,61 @@ struct Solver : SolverBase {
   size_t smX;
   int G;
   int nsm = 148;
+  // optional per-kernel timing with CUDA events on the context's stream
+  struct Prof {
+    bool on = false;
+    std::vector<cudaEvent_t> pool;
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> rec;
+    double ms[NS_PROF_KINDS] = {0};
+    int64_t n[NS_PROF_KINDS] = {0};
+    int64_t launches[NS_PROF_KINDS] = {0};
+  } prof;
+
+  cudaEvent_t prof_event() {
+    if (!prof.pool.empty()) {
+      cudaEvent_t e = prof.pool.back();
+      prof.pool.pop_back();
+      return e;
+    }
+    cudaEvent_t e;
+    CUDA_TRY(cudaEventCreate(&e));
+    return e;
+  }
+  // brackets one launch (or a pass) of kind k; returns the stop event to record after it
+  cudaEvent_t prof_begin(int k) {
+    prof.launches[k] += 1;
+    if (!prof.on || prof.rec.size() >= 65536) return nullptr;
+    cudaEvent_t a = prof_event(), b = prof_event();
+    CUDA_TRY(cudaEventRecord(a, st));
+    prof.rec.push_back({k, {a, b}});
+    return b;
+  }
+  void prof_end(cudaEvent_t b) {
+    if (b) CUDA_TRY(cudaEventRecord(b, st));
+  }
+  void prof_collect() {
+    CUDA_TRY(cudaStreamSynchronize(st));
+    for (auto& r : prof.rec) {
+      float ms = 0;
+      CUDA_TRY(cudaEventElapsedTime(&ms, r.second.first, r.second.second));
+      prof.ms[r.first] += ms;
+      prof.n[r.first] += 1;
+      prof.pool.push_back(r.second.first);
+      prof.pool.push_back(r.second.second);
+    }
+    prof.rec.clear();
+  }
+  void profile(int on) override {
+    prof_collect();
+    prof.on = on != 0;
+    for (int k = 0; k < NS_PROF_KINDS; ++k) prof.ms[k] = 0, prof.n[k] = 0, prof.launches[k] = 0;
+  }
+  void profile_read(int k, double* ms, int64_t* n, int64_t* launches) override {
+    prof_collect();
+    if (ms) *ms = prof.ms[k];
+    if (n) *n = prof.n[k];
+    if (launches) *launches = prof.launches[k];
+  }
 
   explicit Solver(ns_ctx* ctx) : c(ctx) {
     N = c->p.N;
@@ -199,10 +256,16 @@ struct Solver : SolverBase {
     if (G < 1) G = 1;
     if (G > N) G = N;
 
-    CUDA_TRY(cudaFuncSetAttribute(k_pencil<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smP));
-    CUDA_TRY(cudaFuncSetAttribute(k_yinv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smYi));
-    CUDA_TRY(cudaFuncSetAttribute(k_yfwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smYf));
-    CUDA_TRY(cudaFuncSetAttribute(k_xrow<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smX));
+    // The attribute belongs to the kernel, not to this context: allow the device maximum so
+    // that contexts of different sizes in one process never lower each other's limit.
+    int optin = 0;
+    CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    if ((int)smP > optin || (int)smYi > optin || (int)smX > optin)
+      throw NsError{NS_ERR_INTERNAL, "tile shapes exceed the shared memory of the device"};
+    CUDA_TRY(cudaFuncSetAttribute(k_pencil<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+    CUDA_TRY(cudaFuncSetAttribute(k_yinv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+    CUDA_TRY(cudaFuncSetAttribute(k_yfwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+    CUDA_TRY(cudaFuncSetAttribute(k_xrow<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
 
     const int sch = c->p.scheme;
     const bool two = sch == NS_RK2_PS_EXACT;
@@ -232,6 +295,11 @@ struct Solver : SolverBase {
     cudaFree(Ft[0]); cudaFree(Ft[1]); cudaFree(scr); cudaFree(tw); cudaFree(ifac);
     cudaFree(shtab); cudaFree(d_shifts); cudaFree(red); cudaFree(d_err);
     cudaFree(fpat); cudaFree(force); cudaFree(shell);
+    for (auto& r : prof.rec) {
+      cudaEventDestroy(r.second.first);
+      cudaEventDestroy(r.second.second);
+    }
+    for (auto e : prof.pool) cudaEventDestroy(e);
   }
 
   void* state_ptr() override { return state; }
@@ -262,13 +330,21 @@ struct Solver : SolverBase {
     a.mixed = mix;
     a.Ft = out;
     a.xmode = XMODE_NONLINEAR;
+    cudaEvent_t pass = prof_begin(NS_PROF_SLAB_PASS);
     for (int z0 = 0; z0 < N; z0 += G) {
       a.z0 = z0;
       a.G = (z0 + G <= N) ? G : N - z0;
+      cudaEvent_t e = prof_begin(NS_PROF_YINV);
       k_yinv<T><<<dim3(M / TY, a.G), bdYi, smYi, st>>>(a);
+      prof_end(e);
+      e = prof_begin(NS_PROF_XROW);
       k_xrow<T><<<(a.G * N + RX - 1) / RX, bdX, smX, st>>>(a);
+      prof_end(e);
+      e = prof_begin(NS_PROF_YFWD);
       k_yfwd<T><<<dim3(M / TY, a.G), bdYf, smYf, st>>>(a);
+      prof_end(e);
     }
+    prof_end(pass);
     LAUNCH_CHECK();
   }
 
@@ -287,7 +363,9 @@ struct Solver : SolverBase {
   }
 
   void pencil(const PencilArgs<T>& a) {
+    cudaEvent_t e = prof_begin(NS_PROF_PENCIL);
     k_pencil<T><<<(M / TX) * N, bdP, smP, st>>>(a);
+    prof_end(e);
     LAUNCH_CHECK();
   }
 
@@ -903,6 +981,21 @@ int ns_device_state(ns_ctx* c, void** state, void** stream, int* precision) {
   if (stream) *stream = (void*)c->stream;
   if (precision) *precision = c->p.precision;
   return NS_OK;
+}
+
+int ns_profile(ns_ctx* c, int enable) {
+  return guarded(c, [&]() {
+    c->solver->profile(enable);
+    return (int)NS_OK;
+  });
+}
+
+int ns_profile_read(ns_ctx* c, int kind, double* total_ms, int64_t* timed, int64_t* launches) {
+  return guarded(c, [&]() {
+    if (kind < 0 || kind >= NS_PROF_KINDS) return fail(c, NS_ERR_INVALID_ARG, "unknown kernel kind");
+    c->solver->profile_read(kind, total_ms, timed, launches);
+    return (int)NS_OK;
+  });
 }
 
 double ns_model_bytes_per_step(ns_ctx* c) {

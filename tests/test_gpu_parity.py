@@ -248,3 +248,17 @@ def test_full_size_bench_config_properties(ns):
     assert osp.divergence_ratio(S) < 1e-5
     keep = osp.truncation_mask(N, kmax)
     assert np.abs(S[:, ~keep]).max() == 0.0
+
+
+def test_contexts_of_different_sizes_coexist(ns):
+    # kernel attributes are per function: a second context must not break the first one
+    a = ns.Solver(32, 0.01, 16.0, scheme=4)
+    a.set_velocity(field(32, seed=1))
+    b = ns.Solver(96, 0.01, 32.0, scheme=1)
+    b.set_velocity(field(96, seed=2))
+    b.step(0.01, 1)
+    b.close()
+    a.step(0.01, 2)
+    e, _ = a.energy()
+    assert math.isfinite(e)
+    a.close()
