@@ -135,6 +135,26 @@ enum { NS_PROF_PENCIL = 0, NS_PROF_YINV = 1, NS_PROF_XROW = 2, NS_PROF_YFWD = 3,
 int ns_profile(ns_ctx* ctx, int enable);
 int ns_profile_read(ns_ctx* ctx, int kind, double* total_ms, int64_t* timed, int64_t* launches);
 
+/* Nonlinear term N~_D(S) like ns_nonlinear, on device buffers, without allocating any device
+ * memory.  No counterpart in the paper: it serves callers that cannot call cudaMalloc --
+ * host applications whose device memory is entirely reserved by their own allocator, and
+ * loops that must not pay an allocation's latency or risk its failure once running.
+ *   state, out: device pointers, complex FP32 [3][N][N][N/2] (layout of ns.h), caller owned;
+ *               out may not alias state.
+ *   N: 8 <= N <= 64 (NS_ERR_UNSUPPORTED_N beyond, or if N is not an even 2^a 3^b);
+ *   kmax, truncation: as in ns_params (NS_ERR_KMAX if kmax <= 0 or kmax > N/2);
+ *   delta: host double[3], the shift in radians; stream: cudaStream_t (NULL = default).
+ * Working memory is one fixed array inside the library (about 15 MB, sized for N = 64 in
+ * FP32), held by every GPU that loads the library until the process exits.  The first call
+ * on a device looks up that array's device address and sets kernel attributes (make it
+ * before any stream capture).  All calls share the array and it keeps the last call's
+ * contents, so calls that overlap on the GPU (other threads or streams) race.  The call is
+ * stream ordered and synchronises `stream` before returning; it calls no cudaMalloc,
+ * cudaFree or other allocating routine.  Returns NS_ERR_CUDA on a CUDA failure and
+ * NS_ERR_INTERNAL if a device-side shape check failed. */
+int ns_nonlinear_noalloc(const void* state, void* out, int N, double kmax, int truncation,
+                         const double* delta, void* stream);
+
 /* Bytes moved to/from HBM per time step by the algorithmic two-pass model (one slab and
  * one pencil pass per evaluation), for roofline reporting. */
 double ns_model_bytes_per_step(ns_ctx* ctx);

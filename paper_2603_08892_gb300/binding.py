@@ -75,13 +75,15 @@ _profile = _sig("ns_profile", ctypes.c_int, [_vp, ctypes.c_int])
 _profile_read = _sig("ns_profile_read", ctypes.c_int,
                      [_vp, ctypes.c_int, _dp, ctypes.POINTER(ctypes.c_int64),
                       ctypes.POINTER(ctypes.c_int64)])
+_nonlinear_noalloc = _sig("ns_nonlinear_noalloc", ctypes.c_int,
+                         [_vp, _vp, ctypes.c_int, ctypes.c_double, ctypes.c_int, _dp, _vp])
 PROF_KINDS = {"k_pencil": 0, "k_yinv": 1, "k_xrow": 2, "k_yfwd": 3, "slab_pass": 4}
 
 EXPORTED = ["ns_init", "ns_init_ex", "ns_init_error", "ns_destroy", "ns_last_error",
             "ns_set_velocity", "ns_get_velocity", "ns_get_state", "ns_set_state",
             "ns_set_forcing", "ns_step", "ns_set_shifts", "ns_nonlinear", "ns_energy",
             "ns_energy_spectrum", "ns_time", "ns_set_time", "ns_device_state",
-            "ns_model_bytes_per_step", "ns_profile", "ns_profile_read"]
+            "ns_model_bytes_per_step", "ns_profile", "ns_profile_read", "ns_nonlinear_noalloc"]
 
 
 class NSError(RuntimeError):
@@ -218,3 +220,16 @@ class Solver:
             self._check(_profile_read(self._h, k, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(nl)))
             out[name] = (ms.value, n.value, nl.value)
         return out
+
+
+def nonlinear_noalloc(state_ptr, out_ptr, N, kmax, delta, truncation=TRUNC_SPHERICAL, stream=None):
+    """ns_nonlinear_noalloc on caller-owned device buffers (complex64 [3, N, N, N//2]).
+
+    For callers that cannot allocate device memory: the library works in one fixed array of
+    its own (N <= 64), shared by every call, so calls that overlap on the GPU race.
+    """
+    d = np.ascontiguousarray(delta, dtype=np.float64)
+    rc = _nonlinear_noalloc(_vp(state_ptr), _vp(out_ptr), N, kmax, truncation, _ptr(d),
+                            _vp(stream) if stream else None)
+    if rc != NS_OK:
+        raise NSError(rc, "ns_nonlinear_noalloc failed")

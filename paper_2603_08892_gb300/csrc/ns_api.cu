@@ -15,6 +15,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -1010,3 +1011,144 @@ double ns_model_bytes_per_step(ns_ctx* c) {
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------------------------------
+// Nonlinear term without any device allocation (ns_nonlinear_noalloc).
+//
+// For callers that cannot allocate device memory themselves: host applications whose
+// device memory is fully reserved by their own allocator, and loops that must not pay an
+// allocation's latency or risk its failure once they run.  All working memory is the
+// file-scope array below, sized for N <= NS_NOALLOC_MAX_N in FP32; every GPU that loads
+// this library holds it until the process exits.  Calls share it and keep the last call's
+// contents, so calls that overlap on the GPU (other streams or threads) race.
+// ------------------------------------------------------------------------------------------
+namespace {
+
+constexpr int kNoallocMaxN = 64;
+constexpr size_t kNoallocF1 = (size_t)kNoallocMaxN * kNoallocMaxN * (kNoallocMaxN / 2);
+constexpr size_t align256(size_t b) { return (b + 255) / 256 * 256; }
+constexpr size_t kOffMixed = 0;
+constexpr size_t kOffFt = kOffMixed + align256(5 * kNoallocF1 * sizeof(cpx<float>));
+constexpr size_t kOffScr = kOffFt + align256(3 * kNoallocF1 * sizeof(cpx<float>));
+constexpr size_t kOffTw = kOffScr + align256(6 * kNoallocF1 * sizeof(cpx<float>));  // G = N planes
+constexpr size_t kOffSh = kOffTw + align256(kNoallocMaxN * sizeof(cpx<float>));
+constexpr size_t kOffErr = kOffSh + align256(3 * kNoallocMaxN * sizeof(cpx<float>));
+constexpr size_t kNoallocBytes = kOffErr + 256;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
+
+// exp(i k(i) delta_d) for one shift passed by value (no device-side argument buffer)
+__global__ void k_shift_table_value(cpx<float>* out, int N, double d0, double d1, double d2) {
+  int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= 3 * N) return;
+  const int i = idx % N, d = idx / N;
+  const double dl = d == 0 ? d0 : (d == 1 ? d1 : d2);
+  double s, c;
+  sincos((double)kof(i, N) * dl, &s, &c);
+  out[idx] = mk<float>((float)c, (float)s);
+}
+
+std::mutex g_noalloc_mu;
+void* g_noalloc_base[256] = {nullptr};
+
+}  // namespace
+
+extern "C" int ns_nonlinear_noalloc(const void* state, void* out, int N, double kmax,
+                                    int truncation, const double* delta, void* stream_p) {
+  if (!state || !out || !delta) return NS_ERR_INVALID_ARG;
+  if (N < 8 || N > kNoallocMaxN || N % 2 != 0 || !is_2a3b(N)) return NS_ERR_UNSUPPORTED_N;
+  if (!(kmax > 0.0) || kmax > 0.5 * N) return NS_ERR_KMAX;
+  if (truncation != NS_TRUNC_SPHERICAL && truncation != NS_TRUNC_CUBIC) return NS_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream_p;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return NS_ERR_CUDA;
+  unsigned char* base = nullptr;
+  {
+    // once per device, with that device current: the host-side name of the array is not a
+    // device address, so ask the runtime for the address the kernels must use
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_base[dev]) {
+      void* p = nullptr;
+      if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return NS_ERR_CUDA;
+      int optin = 0;
+      if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+        return NS_ERR_CUDA;
+      if (cudaFuncSetAttribute(k_pencil<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin) != cudaSuccess ||
+          cudaFuncSetAttribute(k_yinv<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin) != cudaSuccess ||
+          cudaFuncSetAttribute(k_yfwd<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin) != cudaSuccess ||
+          cudaFuncSetAttribute(k_xrow<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin) != cudaSuccess)
+        return NS_ERR_CUDA;
+      g_noalloc_base[dev] = p;
+    }
+    base = static_cast<unsigned char*>(g_noalloc_base[dev]);
+  }
+  const int M = N / 2;
+  cpx<float>* mixed = reinterpret_cast<cpx<float>*>(base + kOffMixed);
+  cpx<float>* Ft = reinterpret_cast<cpx<float>*>(base + kOffFt);
+  cpx<float>* scr = reinterpret_cast<cpx<float>*>(base + kOffScr);
+  cpx<float>* tw = reinterpret_cast<cpx<float>*>(base + kOffTw);
+  cpx<float>* sh = reinterpret_cast<cpx<float>*>(base + kOffSh);
+  int* err = reinterpret_cast<int*>(base + kOffErr);
+
+  // launch shapes (same rules as a context of this size)
+  const size_t cs = sizeof(cpx<float>), smax = 200 * 1024;
+  FFTPlan pz = make_plan(N, N), px = make_plan(M, N);
+  int TX = largest_divisor_le(M, 16);
+  while (TX > 1 && (4 * N * TX * cs > smax || fft_block(TX, N) > 512)) TX = largest_divisor_le(M, TX - 1);
+  const int bdP = fft_block(TX, N) < 256 ? 256 : fft_block(TX, N);
+  const size_t smP = 4 * (size_t)N * TX * cs;
+  int TY = largest_divisor_le(M, 16);
+  while (TY > 1 && (6 * N * TY * cs > smax || fft_block(TY, N) > 512)) TY = largest_divisor_le(M, TY - 1);
+  const int bdY = fft_block(TY, N) < 256 ? 256 : fft_block(TY, N);
+  const size_t smYi = 6 * (size_t)N * TY * cs, smYf = 3 * (size_t)N * TY * cs;
+  int RX = 16;
+  while (RX > 1 && (6 * (size_t)RX * M * cs > 100 * 1024 || fft_block(RX, M) > 512)) RX /= 2;
+  const int bdX = fft_block(RX, M) < 256 ? 256 : fft_block(RX, M);
+  const size_t smX = 6 * (size_t)RX * M * cs;
+
+  int K2max, Kimax;
+  {
+    const double q = kmax * kmax;
+    double m = std::floor(q);
+    if (m == q) m -= 1;
+    K2max = (int)m;
+    double r = std::floor(kmax);
+    if (r == kmax) r -= 1;
+    Kimax = (int)r;
+  }
+
+  // the error flag must start at zero; every other region is written before it is read
+  if (cudaMemsetAsync(err, 0, sizeof(int), st) != cudaSuccess) return NS_ERR_CUDA;
+  k_twiddle<float><<<(N + 255) / 256, 256, 0, st>>>(tw, N);
+  k_shift_table_value<<<(3 * N + 255) / 256, 256, 0, st>>>(sh, N, delta[0], delta[1], delta[2]);
+
+  PencilArgs<float> p;
+  memset(&p, 0, sizeof(p));
+  p.N = N; p.M = M; p.TX = TX; p.pz = pz; p.tw = tw; p.mode = MODE_INIT;
+  p.src = static_cast<const cpx<float>*>(state);
+  p.trunc = truncation; p.K2max = K2max; p.Kimax = Kimax; p.err = err;
+  p.nOut = 1; p.osh[0] = sh; p.out[0] = mixed;
+  k_pencil<float><<<(M / TX) * N, bdP, smP, st>>>(p);
+
+  SlabArgs<float> a;
+  memset(&a, 0, sizeof(a));
+  a.N = N; a.M = M; a.py = pz; a.px = px; a.tw = tw; a.scr = scr; a.TY = TY; a.RX = RX;
+  a.err = err; a.mixed = mixed; a.Ft = Ft; a.xmode = XMODE_NONLINEAR; a.z0 = 0; a.G = N;
+  k_yinv<float><<<dim3(M / TY, N), bdY, smYi, st>>>(a);
+  k_xrow<float><<<(N * N + RX - 1) / RX, bdX, smX, st>>>(a);
+  k_yfwd<float><<<dim3(M / TY, N), bdY, smYf, st>>>(a);
+
+  PencilArgs<float> q = p;
+  q.mode = MODE_NL;
+  q.src = nullptr;
+  q.nOut = 0;
+  q.nF = 1; q.F[0] = Ft; q.dsh[0] = sh; q.wF[0] = (float)(1.0 / ((double)N * N * N));
+  q.acc = static_cast<cpx<float>*>(out);
+  k_pencil<float><<<(M / TX) * N, bdP, smP, st>>>(q);
+  if (cudaGetLastError() != cudaSuccess) return NS_ERR_CUDA;
+
+  int h = 0;
+  if (cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess) return NS_ERR_CUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return NS_ERR_CUDA;
+  return h ? NS_ERR_INTERNAL : NS_OK;
+}
