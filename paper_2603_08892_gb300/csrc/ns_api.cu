@@ -21,8 +21,21 @@
 
 #include "../../include/ns.h"
 #include "ns_kernels.cuh"
+#include "ns_kernels2.cuh"
 
 using namespace ns;
+
+// size-specialised kernels (ns_k2_*.cu)
+namespace ns {
+bool k2_lookup_f32a(int N, K2Entry<float>* e);
+bool k2_lookup_f32b(int N, K2Entry<float>* e);
+bool k2_lookup_f32c(int N, K2Entry<float>* e);
+bool k2_lookup_f32d(int N, K2Entry<float>* e);
+bool k2_lookup_f64a(int N, K2Entry<double>* e);
+bool k2_lookup_f64b(int N, K2Entry<double>* e);
+bool k2_lookup_f64c(int N, K2Entry<double>* e);
+}  // namespace ns
+
 
 namespace {
 
@@ -89,6 +102,15 @@ uint64_t splitmix64(uint64_t s, uint64_t n) {
 }
 double uniform01(uint64_t s, uint64_t n) {
   return (double)(splitmix64(s, n) >> 11) * (1.0 / 9007199254740992.0);
+}
+
+bool k2_find(int N, K2Entry<float>* e) {
+  if (std::getenv("NS_GENERIC_KERNELS")) return false;
+  return k2_lookup_f32a(N, e) || k2_lookup_f32b(N, e) || k2_lookup_f32c(N, e) || k2_lookup_f32d(N, e);
+}
+bool k2_find(int N, K2Entry<double>* e) {
+  if (std::getenv("NS_GENERIC_KERNELS")) return false;
+  return k2_lookup_f64a(N, e) || k2_lookup_f64b(N, e) || k2_lookup_f64c(N, e);
 }
 
 struct SolverBase {
@@ -166,6 +188,8 @@ struct Solver : SolverBase {
   size_t smX;
   int G;
   int nsm = 148;
+  K2Entry<T> k2;     // size-specialised kernels, if this N has them
+  bool use2 = false;
   // optional per-kernel timing with CUDA events on the context's stream
   struct Prof {
     bool on = false;
@@ -267,6 +291,15 @@ struct Solver : SolverBase {
     CUDA_TRY(cudaFuncSetAttribute(k_yinv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
     CUDA_TRY(cudaFuncSetAttribute(k_yfwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
     CUDA_TRY(cudaFuncSetAttribute(k_xrow<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+    use2 = k2_find(N, &k2);
+    if (use2) {
+      if ((int)k2.smP5 > optin || (int)k2.smX > optin || (int)k2.smY > optin || (int)k2.smYI > optin)
+        throw NsError{NS_ERR_INTERNAL, "specialised tile shapes exceed the shared memory of the device"};
+      CUDA_TRY(cudaFuncSetAttribute(k2.pencil, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+      CUDA_TRY(cudaFuncSetAttribute(k2.yinv, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+      CUDA_TRY(cudaFuncSetAttribute(k2.yfwd, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+      CUDA_TRY(cudaFuncSetAttribute(k2.xrow, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+    }
 
     const int sch = c->p.scheme;
     const bool two = sch == NS_RK2_PS_EXACT;
@@ -336,13 +369,22 @@ struct Solver : SolverBase {
       a.z0 = z0;
       a.G = (z0 + G <= N) ? G : N - z0;
       cudaEvent_t e = prof_begin(NS_PROF_YINV);
-      k_yinv<T><<<dim3(M / TY, a.G), bdYi, smYi, st>>>(a);
+      if (use2)
+        k2.yinv<<<dim3(M / k2.TYI, a.G), k2.NTYI, k2.smYI, st>>>(a);
+      else
+        k_yinv<T><<<dim3(M / TY, a.G), bdYi, smYi, st>>>(a);
       prof_end(e);
       e = prof_begin(NS_PROF_XROW);
-      k_xrow<T><<<(a.G * N + RX - 1) / RX, bdX, smX, st>>>(a);
+      if (use2)
+        k2.xrow<<<(a.G * N + k2.RX - 1) / k2.RX, k2.NTX, k2.smX, st>>>(a);
+      else
+        k_xrow<T><<<(a.G * N + RX - 1) / RX, bdX, smX, st>>>(a);
       prof_end(e);
       e = prof_begin(NS_PROF_YFWD);
-      k_yfwd<T><<<dim3(M / TY, a.G), bdYf, smYf, st>>>(a);
+      if (use2)
+        k2.yfwd<<<dim3(M / k2.TY, a.G), k2.NTY, k2.smY, st>>>(a);
+      else
+        k_yfwd<T><<<dim3(M / TY, a.G), bdYf, smYf, st>>>(a);
       prof_end(e);
     }
     prof_end(pass);
@@ -365,7 +407,10 @@ struct Solver : SolverBase {
 
   void pencil(const PencilArgs<T>& a) {
     cudaEvent_t e = prof_begin(NS_PROF_PENCIL);
-    k_pencil<T><<<(M / TX) * N, bdP, smP, st>>>(a);
+    if (use2)
+      k2.pencil<<<(M / k2.TX) * N, k2.NTP, a.nF > 1 ? k2.smP5 : k2.smP4, st>>>(a);
+    else
+      k_pencil<T><<<(M / TX) * N, bdP, smP, st>>>(a);
     prof_end(e);
     LAUNCH_CHECK();
   }

@@ -1,0 +1,196 @@
+// ns_fft2.cuh -- compile-time mixed-radix FFT for the grid sizes the library specialises.
+//
+// Same transform as ns_fft.cuh (supplementary Eq. dft_def per direction, unnormalised), but
+// the length, the radix plan (16, 16, ..., then 8/4/2, then 3s), the batch width and the
+// thread count are template parameters, so every index is resolved at compile time.  A
+// length-n transform of NL lines is a chain of Stockham stages:
+//   stage 0        reads its inputs through an accessor (global memory or shared memory,
+//                  with any pointwise factor applied on the fly) and writes a shared work tile;
+//   middle stages  work tile -> work tile in place (all reads before a barrier, then writes);
+//   last stage     reads the work tile and writes through an output accessor (global rows,
+//                  or a shared tile).
+// For n = 16^2 = 256 that is the four-step algorithm with a single shared-memory transpose.
+#pragma once
+
+#include "ns_fft.cuh"
+
+namespace ns {
+
+struct CPlan {
+  int nst;
+  int r[8];
+};
+
+__host__ __device__ constexpr CPlan cplan(int n) {
+  CPlan p{0, {0, 0, 0, 0, 0, 0, 0, 0}};
+  int m = n, a2 = 0, a3 = 0;
+  while (m % 2 == 0) { m /= 2; ++a2; }
+  while (m % 3 == 0) { m /= 3; ++a3; }
+  while (a2 >= 4) { p.r[p.nst++] = 16; a2 -= 4; }
+  if (a2 == 3) p.r[p.nst++] = 8;
+  else if (a2 == 2) p.r[p.nst++] = 4;
+  else if (a2 == 1) p.r[p.nst++] = 2;
+  for (int i = 0; i < a3; ++i) p.r[p.nst++] = 3;
+  return p;
+}
+
+// 16-point DFT as 4 x 4 (n = n1 + 4 n2, k = 4 k1 + k2), internal twiddles W16^(n1 k2)
+template <typename T>
+struct DFT<T, 16> {
+  static __device__ __forceinline__ void run(cpx<T>* v, T s) {
+    const T c8 = T(0.92387953251128675613), s8 = T(0.38268343236508977173);
+    const T r2 = T(0.70710678118654752440);
+    cpx<T> a[4][4];
+#pragma unroll
+    for (int n1 = 0; n1 < 4; ++n1) {
+      cpx<T> q[4] = {v[n1], v[n1 + 4], v[n1 + 8], v[n1 + 12]};
+      DFT<T, 4>::run(q, s);
+#pragma unroll
+      for (int k2 = 0; k2 < 4; ++k2) a[n1][k2] = q[k2];
+    }
+    // twiddles W16^m = cos(2 pi m/16) + s i sin(2 pi m/16)
+    a[1][1] = a[1][1] * mk<T>(c8, s * s8);
+    a[1][2] = a[1][2] * mk<T>(r2, s * r2);
+    a[1][3] = a[1][3] * mk<T>(s8, s * c8);
+    a[2][1] = a[2][1] * mk<T>(r2, s * r2);
+    a[2][2] = mul_si(a[2][2], s);
+    a[2][3] = a[2][3] * mk<T>(-r2, s * r2);
+    a[3][1] = a[3][1] * mk<T>(s8, s * c8);
+    a[3][2] = a[3][2] * mk<T>(-r2, s * r2);
+    a[3][3] = a[3][3] * mk<T>(-c8, -s * s8);
+#pragma unroll
+    for (int k2 = 0; k2 < 4; ++k2) {
+      cpx<T> q[4] = {a[0][k2], a[1][k2], a[2][k2], a[3][k2]};
+      DFT<T, 4>::run(q, s);
+#pragma unroll
+      for (int k1 = 0; k1 < 4; ++k1) v[4 * k1 + k2] = q[k1];
+    }
+  }
+};
+
+// Shared work tile of NL lines of length n.  LF (line-fast) layout [e][line]; otherwise
+// [line][e] with one pad element per 16 to spread the stride-R writes of a stage.
+template <typename T, int n, int NL, bool LF>
+struct WorkTile {
+  cpx<T>* p;
+  static constexpr int LS = n + n / 16 + 1;
+  static __host__ __device__ constexpr int elems() { return LF ? n * NL : NL * LS; }
+  __device__ __forceinline__ int idx(int line, int e) const {
+    return LF ? e * NL + line : line * LS + e + (e >> 4);
+  }
+  __device__ __forceinline__ cpx<T> get(int line, int e) const { return p[idx(line, e)]; }
+  __device__ __forceinline__ void put(int line, int e, cpx<T> v) const { p[idx(line, e)] = v; }
+};
+
+// One Stockham stage: butterfly j of a line reads elements j + r n/R, applies the
+// twiddles W_{NS R}^{p r} (p = j mod NS), a radix-R DFT, and writes q NS R + p + r NS.
+// HOLD: every input is read (and a barrier passed) before any output is written.
+template <typename T, int n, int R, int NS, int TWS, int NL, int NT, bool LF, int DIR, bool HOLD,
+          class Src, class Dst>
+__device__ __forceinline__ void cstage(const Src& src, const Dst& dst, const cpx<T>* __restrict__ tw) {
+  constexpr int NB = n / R;
+  constexpr int TOT = NB * NL;
+  constexpr int KB = (TOT + NT - 1) / NT;
+  constexpr int TSTEP = (n / (NS * R)) * TWS;
+  const T s = T(DIR);
+  auto map = [](int b, int& line, int& j) {
+    if (LF) {
+      line = b % NL;
+      j = b / NL;
+    } else {
+      j = b % NB;
+      line = b / NB;
+    }
+  };
+  auto compute = [&](cpx<T>* v, int line, int j) {
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = src.get(line, j + r * NB);
+    if (NS > 1) {
+      const int base = (j % NS) * TSTEP;
+#pragma unroll
+      for (int r = 1; r < R; ++r) {
+        cpx<T> w = ldg(&tw[r * base]);
+        w.y *= -s;
+        v[r] = v[r] * w;
+      }
+    }
+    DFT<T, R>::run(v, s);
+  };
+  auto emit = [&](const cpx<T>* v, int line, int j) {
+    const int p = j % NS, q = j / NS;
+    const int o = q * NS * R + p;
+#pragma unroll
+    for (int r = 0; r < R; ++r) dst.put(line, o + r * NS, v[r]);
+  };
+  if (HOLD) {
+    cpx<T> v[KB][R];
+#pragma unroll
+    for (int c = 0; c < KB; ++c) {
+      const int b = threadIdx.x + c * NT;
+      if (TOT % NT == 0 || b < TOT) {
+        int line, j;
+        map(b, line, j);
+        compute(v[c], line, j);
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int c = 0; c < KB; ++c) {
+      const int b = threadIdx.x + c * NT;
+      if (TOT % NT == 0 || b < TOT) {
+        int line, j;
+        map(b, line, j);
+        emit(v[c], line, j);
+      }
+    }
+  } else {
+#pragma unroll
+    for (int c = 0; c < KB; ++c) {
+      const int b = threadIdx.x + c * NT;
+      if (TOT % NT == 0 || b < TOT) {
+        int line, j;
+        map(b, line, j);
+        cpx<T> v[R];
+        compute(v, line, j);
+        emit(v, line, j);
+      }
+    }
+  }
+}
+
+template <typename T, int n, int TWS, int NL, int NT, bool LF, int DIR, int S, int NS>
+struct CStages {
+  static constexpr CPlan P = cplan(n);
+  template <class Src, class Dst>
+  static __device__ __forceinline__ void run(const Src& src, const Dst& dst, cpx<T>* work,
+                                             const cpx<T>* __restrict__ tw) {
+    constexpr int R = P.r[S];
+    constexpr bool first = S == 0;
+    constexpr bool last = S == P.nst - 1;
+    const WorkTile<T, n, NL, LF> W{work};
+    if constexpr (first && last) {
+      cstage<T, n, R, NS, TWS, NL, NT, LF, DIR, true>(src, dst, tw);
+    } else if constexpr (first) {
+      cstage<T, n, R, NS, TWS, NL, NT, LF, DIR, false>(src, W, tw);
+      __syncthreads();
+      CStages<T, n, TWS, NL, NT, LF, DIR, (first ? S + 1 : S + 1), NS * R>::run(src, dst, work, tw);
+    } else if constexpr (last) {
+      cstage<T, n, R, NS, TWS, NL, NT, LF, DIR, false>(W, dst, tw);
+    } else {
+      cstage<T, n, R, NS, TWS, NL, NT, LF, DIR, true>(W, W, tw);
+      __syncthreads();
+      CStages<T, n, TWS, NL, NT, LF, DIR, S + 1, NS * R>::run(src, dst, work, tw);
+    }
+  }
+};
+
+// Transform of NL lines of length n: src -> dst through the shared work tile `work`
+// (WorkTile<T, n, NL, LF>::elems() values).  DIR = -1 forward, +1 inverse.  TWS = table
+// length / n.  The caller places a barrier after it before dst is read by other threads.
+template <typename T, int n, int TWS, int NL, int NT, bool LF, int DIR, class Src, class Dst>
+__device__ __forceinline__ void cfft(const Src& src, const Dst& dst, cpx<T>* work,
+                                     const cpx<T>* __restrict__ tw) {
+  CStages<T, n, TWS, NL, NT, LF, DIR, 0, 1>::run(src, dst, work, tw);
+}
+
+}  // namespace ns

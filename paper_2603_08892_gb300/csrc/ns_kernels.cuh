@@ -592,7 +592,7 @@ __global__ void __launch_bounds__(256) k_energy(const cpx<T>* __restrict__ S, in
   }
 }
 
-__global__ void k_sum_pairs(const double* partial, int nblk, double* out) {
+static __global__ void k_sum_pairs(const double* partial, int nblk, double* out) {
   __shared__ double s0[256], s1[256];
   double a = 0, b = 0;
   for (int i = threadIdx.x; i < nblk; i += blockDim.x) {
@@ -653,7 +653,7 @@ __global__ void __launch_bounds__(256) k_spectrum(const cpx<T>* __restrict__ S, 
   for (int i = threadIdx.x; i < nbins; i += blockDim.x) partial[(size_t)blockIdx.x * nbins + i] = bins[i];
 }
 
-__global__ void k_spectrum_final(const double* partial, int nblk, int nbins, double* out) {
+static __global__ void k_spectrum_final(const double* partial, int nblk, int nbins, double* out) {
   int bin = blockIdx.x * blockDim.x + threadIdx.x;
   if (bin >= nbins) return;
   double s = 0;

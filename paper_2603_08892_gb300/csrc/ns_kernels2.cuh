@@ -1,0 +1,461 @@
+// ns_kernels2.cuh -- the hot kernels specialised on the grid size N (compile-time FFTs).
+//
+// Same passes, layouts and arithmetic as the generic kernels of ns_kernels.cuh (see there
+// for the data layout): k2_pencil = z transforms + spectral stage of Sec. 4 / 6.1,
+// k2_yinv / k2_xrow / k2_yfwd = slab pass (y transforms, x rows with u x omega).  What
+// changes is how the transforms run: the first FFT stage reads global memory directly and
+// the last one writes it, every index is a compile-time expression, and the butterflies
+// are radix 16 in registers.
+#pragma once
+
+#include "ns_fft2.cuh"
+#include "ns_kernels.cuh"
+
+namespace ns {
+
+__host__ __device__ constexpr int cmin(int a, int b) { return a < b ? a : b; }
+__host__ __device__ constexpr int cmax(int a, int b) { return a > b ? a : b; }
+__host__ __device__ constexpr int pick_div(int m, int target, int cap) {
+  int t = cmin(cmax(target, 1), cap);
+  for (int d = t; d >= 1; --d)
+    if (m % d == 0) return d;
+  return 1;
+}
+__host__ __device__ constexpr int round_warps(int t) { return cmin(cmax((t + 31) / 32 * 32, 64), 512); }
+
+template <typename T, int N>
+struct K2Cfg {
+  static constexpr int M = N / 2;
+  static constexpr int CS = (int)sizeof(cpx<T>);
+  static constexpr int MINW = 32 / CS;  // 32-byte global segments
+  // pencil: TX columns of N
+  static constexpr int TX = pick_div(M, cmax(16384 / (N * CS), MINW), 16);
+  static constexpr int NTP = round_warps(TX * N / 16);
+  // y passes: TY columns of N
+  static constexpr int TY = pick_div(M, cmax(32768 / (N * CS), MINW), 16);
+  static constexpr int NTY = round_warps(TY * N / 16);
+  // inverse y pass: the 5 mixed input tiles are staged in shared memory (6 tiles in all)
+  static constexpr int TYI = pick_div(M, cmax(110000 / (6 * N * CS), MINW), 16);
+  static constexpr int NTYI = round_warps(TYI * N / 16);
+  // x rows: RX rows of M, processed three fields at a time
+  static constexpr int RX = cmin(cmax(8192 / (M * CS), 1), 16);
+  static constexpr int NTX = round_warps(3 * RX * M / 16);
+  static constexpr int XLS = WorkTile<T, M, 3 * RX, false>::LS;
+  static constexpr int XBUF = 3 * RX * XLS;  // elements of one 3-field row buffer
+  static __host__ __device__ constexpr int pencil_tiles(int nF) { return nF > 1 ? 5 : 4; }
+};
+
+// ---- accessors ------------------------------------------------------------------------
+template <typename T, int N, int W>
+struct ColIn {  // global [z|kz][ky][kx] column tile (element e = z index), read-only
+  const cpx<T>* p;
+  int iy, x0;
+  __device__ __forceinline__ cpx<T> get(int line, int e) const {
+    return ldg(&p[((size_t)e * N + iy) * (N / 2) + x0 + line]);
+  }
+};
+template <typename T, int N, int W>
+struct ColOut {
+  cpx<T>* p;
+  int iy, x0;
+  __device__ __forceinline__ void put(int line, int e, cpx<T> v) const {
+    p[((size_t)e * N + iy) * (N / 2) + x0 + line] = v;
+  }
+};
+template <typename T, int W>
+struct SmTile {  // shared [e][line]
+  cpx<T>* p;
+  __device__ __forceinline__ cpx<T> get(int line, int e) const { return p[e * W + line]; }
+  __device__ __forceinline__ void put(int line, int e, cpx<T> v) const { p[e * W + line] = v; }
+};
+// pencil output: shift, optional i kz factor, from a shared component tile
+template <typename T, int N, int W>
+struct PencilOutSrc {
+  const cpx<T>* s;
+  const cpx<T>* sh;
+  int iy, x0;
+  bool deriv;
+  __device__ __forceinline__ cpx<T> get(int line, int e) const {
+    cpx<T> v = s[e * W + line];
+    if (sh) v = v * phase3(sh, N, x0 + line, iy, e);
+    if (deriv) v = mul_si(v, (T)kof(e, N));
+    return v;
+  }
+};
+
+// ---- spectral stage at one mode (Sec. 4.1, 4.2, 6.1) ----------------------------------
+// nv: de-shifted, weighted transform of u x omega at the mode (ignored if nF == 0).
+// Returns S_next for every component and performs the mode's global writes.
+template <typename T>
+__device__ __forceinline__ void spectral_point(const PencilArgs<T>& a, int kx, int ky, int kz,
+                                               int iy, int iz, size_t g, size_t fstride,
+                                               cpx<T> nv[3], cpx<T> sn[3]) {
+  const int N = a.N;
+  const int D1 = 2 * a.fK + 1;
+  const int D = D1 * D1 * (a.fK + 1);
+  if (a.nF > 0) {
+    const int k2 = kx * kx + ky * ky + kz * kz;
+    bool keep;
+    if (a.trunc == 1) {
+      keep = max(kx, max(abs(ky), abs(kz))) <= a.Kimax;
+    } else {
+      keep = k2 <= a.K2max;
+    }
+    keep = keep && (k2 != 0);
+    if (keep) {
+      const cpx<T> v0 = nv[0], v1 = nv[1], v2 = nv[2];
+      const T fx = (T)kx, fy = (T)ky, fz = (T)kz;
+      const T ik2 = T(1) / (T)k2;
+      const cpx<T> kd = mk<T>(fx * v0.x + fy * v1.x + fz * v2.x, fx * v0.y + fy * v1.y + fz * v2.y);
+      nv[0] = v0 - (fx * ik2) * kd;
+      nv[1] = v1 - (fy * ik2) * kd;
+      nv[2] = v2 - (fz * ik2) * kd;
+    } else {
+      nv[0] = nv[1] = nv[2] = mk<T>(0, 0);
+    }
+    if (a.force && kx <= a.fK && abs(ky) <= a.fK && abs(kz) <= a.fK) {
+      const int fi = ((kz + a.fK) * D1 + (ky + a.fK)) * (a.fK + 1) + kx;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) nv[c] = nv[c] + a.force[c * D + fi];
+    }
+  }
+  const T dt = a.dt, hdt = T(0.5) * a.dt;
+  T E1 = 1, Eh = 1;
+  if (a.mode != MODE_INIT && a.mode != MODE_NL && a.mode != MODE_PROJECT) {
+    E1 = a.ifac[kx] * a.ifac[iy] * a.ifac[iz];
+    Eh = a.ifac[N + kx] * a.ifac[N + iy] * a.ifac[N + iz];
+  }
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const size_t gi = g + c * fstride;
+    cpx<T> s = mk<T>(0, 0);
+    switch (a.mode) {
+      case MODE_INIT:
+        s = a.src[gi];
+        break;
+      case MODE_RK2_1:
+        s = Eh * (a.state[gi] + hdt * nv[c]);
+        break;
+      case MODE_RK2_2:
+        s = E1 * a.state[gi] + (dt * Eh) * nv[c];
+        a.state[gi] = s;
+        break;
+      case MODE_RK4_1: {
+        const cpx<T> s0 = a.state[gi];
+        a.acc[gi] = E1 * s0 + (dt / T(6) * E1) * nv[c];
+        s = Eh * (s0 + hdt * nv[c]);
+      } break;
+      case MODE_RK4_2: {
+        const cpx<T> s0 = a.state[gi];
+        a.acc[gi] = a.acc[gi] + (dt / T(3) * Eh) * nv[c];
+        s = Eh * s0 + hdt * nv[c];
+      } break;
+      case MODE_RK4_3: {
+        const cpx<T> s0 = a.state[gi];
+        a.acc[gi] = a.acc[gi] + (dt / T(3) * Eh) * nv[c];
+        s = E1 * s0 + (dt * Eh) * nv[c];
+      } break;
+      case MODE_RK4_4:
+        s = a.acc[gi] + (dt / T(6)) * nv[c];
+        a.state[gi] = s;
+        break;
+      case MODE_ROG_1: {
+        const cpx<T> s0 = a.state[gi];
+        a.state[gi] = E1 * s0 + (hdt * Eh) * nv[c];
+        s = E1 * (s0 + dt * nv[c]);
+      } break;
+      case MODE_ROG_2:
+        s = a.state[gi] + (hdt * Eh) * nv[c];
+        a.state[gi] = s;
+        break;
+      case MODE_NL:
+        a.acc[gi] = nv[c];
+        break;
+      case MODE_PROJECT:
+        a.state[gi] = nv[c];
+        break;
+    }
+    sn[c] = s;
+    if (a.shell && kx <= a.fK && abs(ky) <= a.fK && abs(kz) <= a.fK) {
+      const int fi = ((kz + a.fK) * D1 + (ky + a.fK)) * (a.fK + 1) + kx;
+      a.shell[c * D + fi] = s;
+    }
+  }
+}
+
+// ---- pencil pass --------------------------------------------------------------------
+template <typename T, int N>
+__global__ void __launch_bounds__(K2Cfg<T, N>::NTP) k2_pencil(PencilArgs<T> a) {
+  using C = K2Cfg<T, N>;
+  constexpr int M = N / 2, TX = C::TX, NT = C::NTP, tile = N * TX;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cpx<T>* buf = reinterpret_cast<cpx<T>*>(smem_raw);
+  cpx<T>* bc[3] = {buf, buf + tile, buf + 2 * tile};
+  cpx<T>* W = buf + 3 * tile;
+  cpx<T>* b3 = buf + 4 * tile;
+  constexpr int ntx = M / TX;
+  const int iy = blockIdx.x / ntx;
+  const int x0 = (blockIdx.x % ntx) * TX;
+  const size_t fstride = (size_t)N * N * M;
+  const int ky = kof(iy, N);
+
+  if (a.nF > 0) {
+    for (int c = 0; c < 3; ++c) {
+      cfft<T, N, 1, TX, NT, true, -1>(ColIn<T, N, TX>{a.F[0] + c * fstride, iy, x0},
+                                      SmTile<T, TX>{bc[c]}, W, a.tw);
+      __syncthreads();
+      if (a.nF > 1) {
+        cfft<T, N, 1, TX, NT, true, -1>(ColIn<T, N, TX>{a.F[1] + c * fstride, iy, x0},
+                                        SmTile<T, TX>{b3}, W, a.tw);
+        __syncthreads();
+      }
+      for (int e = threadIdx.x; e < tile; e += NT) {
+        const int iz = e / TX, x = e % TX;
+        cpx<T> v = bc[c][e];
+        if (a.dsh[0]) v = mul_conj(v, phase3(a.dsh[0], N, x0 + x, iy, iz));
+        v = a.wF[0] * v;
+        if (a.nF > 1) {
+          cpx<T> w = b3[e];
+          if (a.dsh[1]) w = mul_conj(w, phase3(a.dsh[1], N, x0 + x, iy, iz));
+          v = v + a.wF[1] * w;
+        }
+        bc[c][e] = v;
+      }
+      __syncthreads();
+    }
+  }
+
+  for (int e = threadIdx.x; e < tile; e += NT) {
+    const int iz = e / TX, x = e % TX;
+    const int kx = x0 + x, kz = kof(iz, N);
+    const size_t g = ((size_t)iz * N + iy) * M + kx;
+    cpx<T> nv[3], sn[3];
+    if (a.nF > 0) {
+      nv[0] = bc[0][e];
+      nv[1] = bc[1][e];
+      nv[2] = bc[2][e];
+    }
+    spectral_point(a, kx, ky, kz, iy, iz, g, fstride, nv, sn);
+    bc[0][e] = sn[0];
+    bc[1][e] = sn[1];
+    bc[2][e] = sn[2];
+  }
+  __syncthreads();
+
+  for (int o = 0; o < a.nOut; ++o) {
+    for (int f = 0; f < 5; ++f) {
+      const int c = f < 3 ? f : f - 3;
+      cfft<T, N, 1, TX, NT, true, 1>(PencilOutSrc<T, N, TX>{bc[c], a.osh[o], iy, x0, f >= 3},
+                                     ColOut<T, N, TX>{a.out[o] + f * fstride, iy, x0}, W, a.tw);
+      __syncthreads();
+    }
+  }
+}
+
+// ---- slab pass: y transforms --------------------------------------------------------
+// field F of the spectral-in-xy pair (u, omega) formed on the fly from the 5 mixed
+// fields staged in shared memory ([f][e][line], TY lines)
+template <typename T, int N, int F, int TY>
+struct YInvSrc {
+  const cpx<T>* m;
+  int x0;
+  __device__ __forceinline__ cpx<T> get(int line, int e) const {
+    constexpr int fs = N * TY;
+    const int i = e * TY + line;
+    const T kx = (T)(x0 + line), ky = (T)kof(e, N);
+    if (F == 0) return m[i];
+    if (F == 1) return m[i + fs];
+    if (F == 2) return m[i + 2 * fs];
+    if (F == 3) return mul_si(m[i + 2 * fs], ky) - m[i + 4 * fs];   // i ky u_z - d_z u_y
+    if (F == 4) return m[i + 3 * fs] - mul_si(m[i + 2 * fs], kx);   // d_z u_x - i kx u_z
+    return mul_si(m[i + fs], kx) - mul_si(m[i], ky);                // i kx u_y - i ky u_x
+  }
+};
+template <typename T, int N>
+struct ScrCol {  // one field [plane][y|ky][kx], column tile of a plane (scratch or Ft)
+  cpx<T>* p;
+  int zg, x0;
+  __device__ __forceinline__ cpx<T> get(int line, int e) const {
+    return p[((size_t)zg * N + e) * (N / 2) + x0 + line];
+  }
+  __device__ __forceinline__ void put(int line, int e, cpx<T> v) const {
+    p[((size_t)zg * N + e) * (N / 2) + x0 + line] = v;
+  }
+};
+
+template <typename T, int N, int F>
+__device__ __forceinline__ void yinv_field(const SlabArgs<T>& a, const cpx<T>* in, cpx<T>* W,
+                                           int zg, int x0, size_t sstride) {
+  using C = K2Cfg<T, N>;
+  cfft<T, N, 1, C::TYI, C::NTYI, true, 1>(YInvSrc<T, N, F, C::TYI>{in, x0},
+                                          ScrCol<T, N>{a.scr + F * sstride, zg, x0}, W, a.tw);
+  __syncthreads();
+}
+
+template <typename T, int N>
+__global__ void __launch_bounds__(K2Cfg<T, N>::NTYI) k2_yinv(SlabArgs<T> a) {
+  using C = K2Cfg<T, N>;
+  constexpr int M = N / 2, TY = C::TYI, NT = C::NTYI, tile = N * TY;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cpx<T>* in = reinterpret_cast<cpx<T>*>(smem_raw);
+  cpx<T>* W = in + 5 * tile;
+  const int x0 = blockIdx.x * TY, zg = blockIdx.y, z = a.z0 + zg;
+  const size_t sstride = (size_t)a.G * N * M;
+  const size_t fs = (size_t)N * N * M;
+  for (int i = threadIdx.x; i < 5 * tile; i += NT) {
+    const int f = i / tile, rem = i % tile, e = rem / TY, line = rem % TY;
+    in[i] = ldg(&a.mixed[f * fs + ((size_t)z * N + e) * M + x0 + line]);
+  }
+  __syncthreads();
+  yinv_field<T, N, 0>(a, in, W, zg, x0, sstride);
+  yinv_field<T, N, 1>(a, in, W, zg, x0, sstride);
+  yinv_field<T, N, 2>(a, in, W, zg, x0, sstride);
+  yinv_field<T, N, 3>(a, in, W, zg, x0, sstride);
+  yinv_field<T, N, 4>(a, in, W, zg, x0, sstride);
+  yinv_field<T, N, 5>(a, in, W, zg, x0, sstride);
+}
+
+template <typename T, int N>
+__global__ void __launch_bounds__(K2Cfg<T, N>::NTY, 2) k2_yfwd(SlabArgs<T> a) {
+  using C = K2Cfg<T, N>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cpx<T>* W = reinterpret_cast<cpx<T>*>(smem_raw);
+  const int x0 = blockIdx.x * C::TY, zg = blockIdx.y, z = a.z0 + zg;
+  const size_t sstride = (size_t)a.G * N * (N / 2);
+  const size_t fstride = (size_t)N * N * (N / 2);
+  for (int f = 0; f < 3; ++f) {
+    cfft<T, N, 1, C::TY, C::NTY, true, -1>(ScrCol<T, N>{a.scr + f * sstride, zg, x0},
+                                           ScrCol<T, N>{a.Ft + f * fstride, z, x0}, W, a.tw);
+    __syncthreads();
+  }
+}
+
+// ---- slab pass: x rows --------------------------------------------------------------
+template <typename T, int N>
+__global__ void __launch_bounds__(K2Cfg<T, N>::NTX) k2_xrow(SlabArgs<T> a) {
+  using C = K2Cfg<T, N>;
+  constexpr int M = N / 2, RX = C::RX, NT = C::NTX;
+  using RowT = WorkTile<T, M, 3 * RX, false>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cpx<T>* buf = reinterpret_cast<cpx<T>*>(smem_raw);
+  const RowT U{buf}, V{buf + C::XBUF};
+  cpx<T>* work = buf + 2 * C::XBUF;
+  const int rows_total = a.G * N;
+  const int r0 = blockIdx.x * RX;
+  const int nr = min(RX, rows_total - r0);
+  const size_t sstride = (size_t)a.G * N * M;
+  constexpr int NP = M / 2 + 1;  // pairs (k, M-k), k = 0..M/2
+
+  // load the 6 fields with the c2r pre-processing (Hermitian half row -> packed Z')
+  for (int i = threadIdx.x; i < 6 * RX * NP; i += NT) {
+    const int f = i / (RX * NP), rem = i % (RX * NP), row = rem / NP, k = rem % NP;
+    const RowT& B = f < 3 ? U : V;
+    const int line = (f % 3) * RX + row;
+    if (row >= nr) {
+      if (k == 0 || k < M - k) {
+        B.put(line, k, mk<T>(0, 0));
+        if (k != 0) B.put(line, M - k, mk<T>(0, 0));
+        if (k == 0 && M % 2 == 0 && M > 1) B.put(line, M / 2, mk<T>(0, 0));
+      }
+      continue;
+    }
+    const cpx<T>* src = a.scr + f * sstride + (size_t)(r0 + row) * M;
+    if (k == 0) {
+      const T r = ldg(&src[0]).x;
+      B.put(line, 0, mk<T>(r, r));
+      if (M % 2 == 0 && M > 1) {
+        const cpx<T> X = ldg(&src[M / 2]);
+        B.put(line, M / 2, (X + conjg(X)) - (X - conjg(X)));
+      }
+    } else if (k < M - k) {
+      const cpx<T> Xk = ldg(&src[k]), Xm = ldg(&src[M - k]);
+      const cpx<T> tk = ldg(&a.tw[k]);
+      const cpx<T> A = Xk + conjg(Xm), Bv = Xk - conjg(Xm);
+      B.put(line, k, A + mul_si(conjg(tk) * Bv, T(1)));
+      const cpx<T> A2 = Xm + conjg(Xk), B2 = Xm - conjg(Xk);
+      B.put(line, M - k, A2 - mul_si(tk * B2, T(1)));
+    }
+  }
+  __syncthreads();
+  cfft<T, M, 2, 3 * RX, NT, false, 1>(U, U, work, a.tw);
+  __syncthreads();
+  cfft<T, M, 2, 3 * RX, NT, false, 1>(V, V, work, a.tw);
+  __syncthreads();
+
+  // u x omega on the packed real rows, written over u
+  for (int i = threadIdx.x; i < RX * M; i += NT) {
+    const int row = i / M, k = i % M;
+    cpx<T> u[3], w[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      u[c] = U.get(c * RX + row, k);
+      w[c] = V.get(c * RX + row, k);
+    }
+    // real parts are x_{2k}, imaginary parts x_{2k+1}
+    const cpx<T> f0 = mk<T>(u[1].x * w[2].x - u[2].x * w[1].x, u[1].y * w[2].y - u[2].y * w[1].y);
+    const cpx<T> f1 = mk<T>(u[2].x * w[0].x - u[0].x * w[2].x, u[2].y * w[0].y - u[0].y * w[2].y);
+    const cpx<T> f2 = mk<T>(u[0].x * w[1].x - u[1].x * w[0].x, u[0].y * w[1].y - u[1].y * w[0].y);
+    U.put(row, k, f0);
+    U.put(RX + row, k, f1);
+    U.put(2 * RX + row, k, f2);
+  }
+  __syncthreads();
+  cfft<T, M, 2, 3 * RX, NT, false, -1>(U, U, work, a.tw);
+  __syncthreads();
+
+  // r2c post-processing and store
+  for (int i = threadIdx.x; i < 3 * RX * NP; i += NT) {
+    const int f = i / (RX * NP), rem = i % (RX * NP), row = rem / NP, k = rem % NP;
+    if (row >= nr) continue;
+    const int line = f * RX + row;
+    cpx<T>* dst = a.scr + f * sstride + (size_t)(r0 + row) * M;
+    if (k == 0) {
+      const cpx<T> Z = U.get(line, 0);
+      dst[0] = mk<T>(Z.x + Z.y, T(0));
+      if (M % 2 == 0 && M > 1) {
+        const cpx<T> Zk = U.get(line, M / 2);
+        dst[M / 2] = T(0.5) * ((Zk + conjg(Zk)) - (Zk - conjg(Zk)));
+      }
+    } else if (k < M - k) {
+      const cpx<T> Zk = U.get(line, k), Zm = U.get(line, M - k);
+      const cpx<T> Wk = ldg(&a.tw[k]);
+      const cpx<T> A = Zk + conjg(Zm), B = Zk - conjg(Zm);
+      dst[k] = T(0.5) * (A - mul_si(Wk * B, T(1)));
+      const cpx<T> A2 = Zm + conjg(Zk), B2 = Zm - conjg(Zk);
+      dst[M - k] = T(0.5) * (A2 + mul_si(conjg(Wk) * B2, T(1)));
+    }
+  }
+}
+
+// ---- registry entry of one size ------------------------------------------------------
+template <typename T>
+struct K2Entry {
+  int N = 0;
+  void (*pencil)(PencilArgs<T>) = nullptr;
+  void (*yinv)(SlabArgs<T>) = nullptr;
+  void (*yfwd)(SlabArgs<T>) = nullptr;
+  void (*xrow)(SlabArgs<T>) = nullptr;
+  int TX = 0, NTP = 0, TY = 0, NTY = 0, TYI = 0, NTYI = 0, RX = 0, NTX = 0;
+  size_t smP4 = 0, smP5 = 0, smY = 0, smYI = 0, smX = 0;
+};
+
+template <typename T, int N>
+K2Entry<T> make_k2_entry() {
+  using C = K2Cfg<T, N>;
+  K2Entry<T> e;
+  e.N = N;
+  e.pencil = k2_pencil<T, N>;
+  e.yinv = k2_yinv<T, N>;
+  e.yfwd = k2_yfwd<T, N>;
+  e.xrow = k2_xrow<T, N>;
+  e.TX = C::TX; e.NTP = C::NTP; e.TY = C::TY; e.NTY = C::NTY; e.RX = C::RX; e.NTX = C::NTX;
+  e.TYI = C::TYI; e.NTYI = C::NTYI;
+  e.smYI = 6 * (size_t)N * C::TYI * sizeof(cpx<T>);
+  e.smP4 = 4 * (size_t)N * C::TX * sizeof(cpx<T>);
+  e.smP5 = 5 * (size_t)N * C::TX * sizeof(cpx<T>);
+  e.smY = (size_t)N * C::TY * sizeof(cpx<T>);
+  e.smX = 3 * (size_t)C::XBUF * sizeof(cpx<T>);
+  return e;
+}
+
+}  // namespace ns

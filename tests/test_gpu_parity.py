@@ -262,3 +262,38 @@ def test_contexts_of_different_sizes_coexist(ns):
     e, _ = a.energy()
     assert math.isfinite(e)
     a.close()
+
+
+@pytest.mark.parametrize("prec", [1, 0])
+@pytest.mark.parametrize("N", [36, 72])
+def test_generic_kernel_sizes(ns, N, prec):
+    # sizes outside the compile-time specialised set run the generic kernels
+    kmax = N / 2
+    S = osp.set_velocity(field(N, seed=17), kmax)
+    dx = 2 * math.pi / N
+    delta = [0.2 * dx, 0.9 * dx, 0.4 * dx]
+    with ns.Solver(N, 0.01, kmax, scheme=4, precision=prec, seed=2) as s:
+        got = s.nonlinear(delta, S)
+        assert rel(got, onl.nonlinear(S, delta, kmax)) < TOL[prec] * 5
+        s.set_state(S)
+        s.step(0.01, 2)
+        out = s.get_state()
+    prob = sc.Problem(N, 0.01, kmax)
+    ref, _ = sc.run(S, 0.01, 2, prob, sc.SCHEME_PS_RANDOM, seed=2)
+    assert rel(out, ref) < 2 * TOL[prec]
+
+
+@pytest.mark.parametrize("prec", [1, 0])
+@pytest.mark.parametrize("code", [1, 2, 4])
+def test_specialised_and_generic_kernels_agree(ns, prec, code, monkeypatch):
+    N = 48
+    u = field(N, seed=23)
+    out = []
+    for generic in (False, True):
+        if generic:
+            monkeypatch.setenv("NS_GENERIC_KERNELS", "1")
+        with ns.Solver(N, 0.01, N / 2, scheme=code, precision=prec, seed=8) as s:
+            s.set_velocity(u)
+            s.step(0.01, 3)
+            out.append(s.get_state())
+    assert rel(out[0], out[1]) < (1e-13 if prec else 3e-6)
