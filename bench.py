@@ -75,7 +75,7 @@ def peaks():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("ns_fft.cuh", "ns_kernels.cuh"):
+    for f in ("ns_fft.cuh", "ns_kernels.cuh", "ns_fft2.cuh", "ns_kernels2.cuh"):
         with open(os.path.join(ROOT, "paper_2603_08892_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
