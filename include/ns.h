@@ -135,6 +135,39 @@ enum { NS_PROF_PENCIL = 0, NS_PROF_YINV = 1, NS_PROF_XROW = 2, NS_PROF_YFWD = 3,
 int ns_profile(ns_ctx* ctx, int enable);
 int ns_profile_read(ns_ctx* ctx, int kind, double* total_ms, int64_t* timed, int64_t* launches);
 
+/* ---- Batched ensembles (no counterpart in the paper) -----------------------------------
+ * Independent simulations of uneven N advanced together by ONE persistent kernel launch per
+ * ns_batch_step call (captured in a CUDA graph and replayed), each member running the RK2
+ * phase-shift random (Rogallo, Sec. 4.2) or approx scheme exactly as a single context does.
+ * The CTAs of the launch take (step, pass, member, tile) work items in order from an atomic
+ * counter and wait, with a bounded spin, until the member's earlier passes are complete;
+ * an expired wait ends the launch with NS_ERR_TIMEOUT instead of hanging.
+ * Supported member sizes: N in {16, 32, 48, 64, 96, 128}; spherical truncation. */
+typedef struct ns_batch ns_batch;
+/* count members (1..1024) with sizes N[i], viscosities nu[i], truncation kmax[i] and shift
+ * seeds seeds[i] (NULL: seed i); scheme NS_RK2_PS_RANDOM or NS_RK2_PS_APPROX; precision
+ * NS_FP32 / NS_FP64; stream: cudaStream_t shared by all members (NULL: the batch creates one). */
+int ns_batch_init(ns_batch** b, int count, const int* N, const double* nu, const double* kmax,
+                  const uint64_t* seeds, int scheme, int precision, void* stream);
+int ns_batch_destroy(ns_batch* b);
+const char* ns_batch_last_error(ns_batch* b);
+/* The member's own context (owned by the batch): every single-context call applies to it. */
+ns_ctx* ns_batch_member(ns_batch* b, int i);
+/* Same as ns_set_velocity / ns_get_state on member i. */
+int ns_batch_set_velocity(ns_batch* b, int i, const double* u);
+int ns_batch_get_state(ns_batch* b, int i, double* re_im_out);
+/* Advances every member by nsteps steps of its own dt[i] (host array of count) in one launch. */
+int ns_batch_step(ns_batch* b, const double* dt, int nsteps);
+/* E[i], eps[i] of every member (host arrays of count). */
+int ns_batch_energy(ns_batch* b, double* E, double* eps);
+/* Poll budget of each bounded wait of the persistent kernel (default 2e6 polls of >= 100 ns). */
+int ns_batch_set_spin_limit(ns_batch* b, long long polls);
+/* Test hook: nonzero makes every per-step wait unreachable, so the next ns_batch_step must
+ * return NS_ERR_TIMEOUT after the bounded waits expire (the GPU stays usable). */
+int ns_batch_test_stall(ns_batch* b, int on);
+/* CTAs of the last persistent launch (diagnostics). */
+int ns_batch_grid(ns_batch* b);
+
 /* Nonlinear term N~_D(S) like ns_nonlinear, on device buffers, without allocating any device
  * memory.  No counterpart in the paper: it serves callers that cannot call cudaMalloc --
  * host applications whose device memory is entirely reserved by their own allocator, and

@@ -77,13 +77,28 @@ _profile_read = _sig("ns_profile_read", ctypes.c_int,
                       ctypes.POINTER(ctypes.c_int64)])
 _nonlinear_noalloc = _sig("ns_nonlinear_noalloc", ctypes.c_int,
                          [_vp, _vp, ctypes.c_int, ctypes.c_double, ctypes.c_int, _dp, _vp])
+_batch_init = _sig("ns_batch_init", ctypes.c_int,
+                   [ctypes.POINTER(_vp), ctypes.c_int, ctypes.POINTER(ctypes.c_int), _dp, _dp,
+                    ctypes.POINTER(ctypes.c_uint64), ctypes.c_int, ctypes.c_int, _vp])
+_batch_destroy = _sig("ns_batch_destroy", ctypes.c_int, [_vp])
+_batch_last_error = _sig("ns_batch_last_error", ctypes.c_char_p, [_vp])
+_batch_member = _sig("ns_batch_member", _vp, [_vp, ctypes.c_int])
+_batch_set_velocity = _sig("ns_batch_set_velocity", ctypes.c_int, [_vp, ctypes.c_int, _dp])
+_batch_get_state = _sig("ns_batch_get_state", ctypes.c_int, [_vp, ctypes.c_int, _dp])
+_batch_step = _sig("ns_batch_step", ctypes.c_int, [_vp, _dp, ctypes.c_int])
+_batch_energy = _sig("ns_batch_energy", ctypes.c_int, [_vp, _dp, _dp])
+_batch_spin = _sig("ns_batch_set_spin_limit", ctypes.c_int, [_vp, ctypes.c_longlong])
+_batch_stall = _sig("ns_batch_test_stall", ctypes.c_int, [_vp, ctypes.c_int])
+_batch_grid = _sig("ns_batch_grid", ctypes.c_int, [_vp])
 PROF_KINDS = {"k_pencil": 0, "k_yinv": 1, "k_xrow": 2, "k_yfwd": 3, "slab_pass": 4}
 
 EXPORTED = ["ns_init", "ns_init_ex", "ns_init_error", "ns_destroy", "ns_last_error",
             "ns_set_velocity", "ns_get_velocity", "ns_get_state", "ns_set_state",
             "ns_set_forcing", "ns_step", "ns_set_shifts", "ns_nonlinear", "ns_energy",
             "ns_energy_spectrum", "ns_time", "ns_set_time", "ns_device_state",
-            "ns_model_bytes_per_step", "ns_profile", "ns_profile_read", "ns_nonlinear_noalloc"]
+            "ns_model_bytes_per_step", "ns_profile", "ns_profile_read", "ns_nonlinear_noalloc", "ns_batch_init", "ns_batch_destroy", "ns_batch_last_error",
+            "ns_batch_member", "ns_batch_set_velocity", "ns_batch_get_state", "ns_batch_step",
+            "ns_batch_energy", "ns_batch_set_spin_limit", "ns_batch_test_stall", "ns_batch_grid"]
 
 
 class NSError(RuntimeError):
@@ -233,3 +248,73 @@ def nonlinear_noalloc(state_ptr, out_ptr, N, kmax, delta, truncation=TRUNC_SPHER
                             _vp(stream) if stream else None)
     if rc != NS_OK:
         raise NSError(rc, "ns_nonlinear_noalloc failed")
+
+
+class Batch:
+    """Ensemble of independent members of uneven N advanced by one persistent launch."""
+
+    def __init__(self, Ns, nus, kmaxs, seeds=None, scheme=RK2_PS_RANDOM, precision=FP32,
+                 stream=None):
+        n = len(Ns)
+        Na = (ctypes.c_int * n)(*Ns)
+        nu = np.ascontiguousarray(nus, dtype=np.float64)
+        km = np.ascontiguousarray(kmaxs, dtype=np.float64)
+        sd = (ctypes.c_uint64 * n)(*seeds) if seeds is not None else None
+        h = _vp()
+        rc = _batch_init(ctypes.byref(h), n, Na, _ptr(nu), _ptr(km), sd, scheme, precision,
+                         _vp(stream) if stream else None)
+        if rc != NS_OK:
+            raise NSError(rc, "ns_batch_init failed")
+        self._h = h
+        self.Ns = list(Ns)
+        self.count = n
+
+    def _check(self, rc):
+        if rc != NS_OK:
+            raise NSError(rc, _batch_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_velocity(self, i, u):
+        u = np.ascontiguousarray(u, dtype=np.float64)
+        self._check(_batch_set_velocity(self._h, i, _ptr(u)))
+
+    def get_state(self, i):
+        N = self.Ns[i]
+        s = np.empty((3, N, N, N // 2), dtype=np.complex128)
+        self._check(_batch_get_state(self._h, i, s.ctypes.data_as(_dp)))
+        return s
+
+    def step(self, dts, nsteps):
+        d = np.ascontiguousarray(np.broadcast_to(dts, (self.count,)), dtype=np.float64)
+        self._check(_batch_step(self._h, _ptr(d), nsteps))
+
+    def energy(self):
+        E = np.empty(self.count)
+        eps = np.empty(self.count)
+        self._check(_batch_energy(self._h, _ptr(E), _ptr(eps)))
+        return E, eps
+
+    def set_spin_limit(self, polls):
+        self._check(_batch_spin(self._h, polls))
+
+    def test_stall(self, on):
+        self._check(_batch_stall(self._h, 1 if on else 0))
+
+    def grid(self):
+        return _batch_grid(self._h)

@@ -20,6 +20,7 @@
 #include <vector>
 
 #include "../../include/ns.h"
+#include "ns_internal.h"
 #include "ns_kernels.cuh"
 #include "ns_kernels2.cuh"
 
@@ -126,6 +127,7 @@ struct SolverBase {
   virtual void set_forcing(int kind, double kfmin, double kfmax, double eps, double tcorr,
                            uint64_t seed) = 0;
   virtual void* state_ptr() = 0;
+  virtual void buffers(double dt, NsCtxBuffers* b) = 0;
   virtual void profile(int on) = 0;
   virtual void profile_read(int k, double* ms, int64_t* n, int64_t* launches) = 0;
 };
@@ -337,6 +339,14 @@ struct Solver : SolverBase {
   }
 
   void* state_ptr() override { return state; }
+
+  void buffers(double dt, NsCtxBuffers* b) override {
+    if (dt > 0) set_dt(dt);
+    b->N = N; b->precision = c->p.precision; b->scheme = c->p.scheme; b->truncation = c->p.truncation;
+    b->K2max = c->K2max; b->Kimax = c->Kimax; b->G = G; b->nu = c->p.nu; b->kmax = c->p.kmax;
+    b->state = state; b->mixed = mixed[0]; b->Ft = Ft[0]; b->scr = scr; b->tw = tw; b->ifac = ifac;
+    b->err = d_err; b->seed = c->p.seed; b->step = c->step; b->t = c->t;
+  }
 
   // ---- device error flag ------------------------------------------------------------
   void sync_check() {
@@ -813,6 +823,20 @@ int guarded(ns_ctx* c, F&& f) {
 }
 
 }  // namespace
+
+int ns_ctx_buffers(ns_ctx* c, double dt, NsCtxBuffers* b) {
+  return guarded(c, [&]() {
+    c->solver->buffers(dt, b);
+    return (int)NS_OK;
+  });
+}
+
+int ns_ctx_advance(ns_ctx* c, double dt, int nsteps) {
+  if (!c) return NS_ERR_INVALID_ARG;
+  for (int i = 0; i < nsteps; ++i) c->t += dt;  // same accumulation as ns_step
+  c->step += nsteps;
+  return NS_OK;
+}
 
 extern "C" {
 

@@ -85,6 +85,7 @@ struct WorkTile {
 // One Stockham stage: butterfly j of a line reads elements j + r n/R, applies the
 // twiddles W_{NS R}^{p r} (p = j mod NS), a radix-R DFT, and writes q NS R + p + r NS.
 // HOLD: every input is read (and a barrier passed) before any output is written.
+// Threads with threadIdx.x >= NT take no butterflies but pass the barriers.
 template <typename T, int n, int R, int NS, int TWS, int NL, int NT, bool LF, int DIR, bool HOLD,
           class Src, class Dst>
 __device__ __forceinline__ void cstage(const Src& src, const Dst& dst, const cpx<T>* __restrict__ tw) {
@@ -127,7 +128,7 @@ __device__ __forceinline__ void cstage(const Src& src, const Dst& dst, const cpx
 #pragma unroll
     for (int c = 0; c < KB; ++c) {
       const int b = threadIdx.x + c * NT;
-      if (TOT % NT == 0 || b < TOT) {
+      if (threadIdx.x < NT && (TOT % NT == 0 || b < TOT)) {
         int line, j;
         map(b, line, j);
         compute(v[c], line, j);
@@ -137,7 +138,7 @@ __device__ __forceinline__ void cstage(const Src& src, const Dst& dst, const cpx
 #pragma unroll
     for (int c = 0; c < KB; ++c) {
       const int b = threadIdx.x + c * NT;
-      if (TOT % NT == 0 || b < TOT) {
+      if (threadIdx.x < NT && (TOT % NT == 0 || b < TOT)) {
         int line, j;
         map(b, line, j);
         emit(v[c], line, j);
@@ -147,7 +148,7 @@ __device__ __forceinline__ void cstage(const Src& src, const Dst& dst, const cpx
 #pragma unroll
     for (int c = 0; c < KB; ++c) {
       const int b = threadIdx.x + c * NT;
-      if (TOT % NT == 0 || b < TOT) {
+      if (threadIdx.x < NT && (TOT % NT == 0 || b < TOT)) {
         int line, j;
         map(b, line, j);
         cpx<T> v[R];

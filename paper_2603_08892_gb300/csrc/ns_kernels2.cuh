@@ -23,6 +23,36 @@ __host__ __device__ constexpr int pick_div(int m, int target, int cap) {
 }
 __host__ __device__ constexpr int round_warps(int t) { return cmin(cmax((t + 31) / 32 * 32, 64), 512); }
 
+// Global-memory access policy.  MemNC: data written by earlier launches (read-only path).
+// MemCG: data written by other blocks of the same launch (persistent kernel): loads and
+// stores go to L2 (.cg) so a block never sees a stale line in its own L1.
+struct MemNC {
+  template <typename T>
+  static __device__ __forceinline__ cpx<T> ld(const cpx<T>* p) { return ldg(p); }
+  template <typename T>
+  static __device__ __forceinline__ cpx<T> ldw(const cpx<T>* p) { return *p; }
+  template <typename T>
+  static __device__ __forceinline__ void st(cpx<T>* p, cpx<T> v) { *p = v; }
+};
+struct MemCG {
+  static __device__ __forceinline__ cpx<float> ld(const cpx<float>* p) {
+    const float2 v = __ldcg(reinterpret_cast<const float2*>(p));
+    return mk<float>(v.x, v.y);
+  }
+  static __device__ __forceinline__ cpx<double> ld(const cpx<double>* p) {
+    const double2 v = __ldcg(reinterpret_cast<const double2*>(p));
+    return mk<double>(v.x, v.y);
+  }
+  template <typename T>
+  static __device__ __forceinline__ cpx<T> ldw(const cpx<T>* p) { return ld(p); }
+  static __device__ __forceinline__ void st(cpx<float>* p, cpx<float> v) {
+    __stcg(reinterpret_cast<float2*>(p), make_float2(v.x, v.y));
+  }
+  static __device__ __forceinline__ void st(cpx<double>* p, cpx<double> v) {
+    __stcg(reinterpret_cast<double2*>(p), make_double2(v.x, v.y));
+  }
+};
+
 template <typename T, int N>
 struct K2Cfg {
   static constexpr int M = N / 2;
@@ -46,20 +76,20 @@ struct K2Cfg {
 };
 
 // ---- accessors ------------------------------------------------------------------------
-template <typename T, int N, int W>
+template <typename T, int N, int W, class MP>
 struct ColIn {  // global [z|kz][ky][kx] column tile (element e = z index), read-only
   const cpx<T>* p;
   int iy, x0;
   __device__ __forceinline__ cpx<T> get(int line, int e) const {
-    return ldg(&p[((size_t)e * N + iy) * (N / 2) + x0 + line]);
+    return MP::ld(&p[((size_t)e * N + iy) * (N / 2) + x0 + line]);
   }
 };
-template <typename T, int N, int W>
+template <typename T, int N, int W, class MP>
 struct ColOut {
   cpx<T>* p;
   int iy, x0;
   __device__ __forceinline__ void put(int line, int e, cpx<T> v) const {
-    p[((size_t)e * N + iy) * (N / 2) + x0 + line] = v;
+    MP::st(&p[((size_t)e * N + iy) * (N / 2) + x0 + line], v);
   }
 };
 template <typename T, int W>
@@ -68,8 +98,12 @@ struct SmTile {  // shared [e][line]
   __device__ __forceinline__ cpx<T> get(int line, int e) const { return p[e * W + line]; }
   __device__ __forceinline__ void put(int line, int e, cpx<T> v) const { p[e * W + line] = v; }
 };
+template <class MP, typename T>
+__device__ __forceinline__ cpx<T> phase3p(const cpx<T>* tab, int N, int ix, int iy, int iz) {
+  return (MP::ld(&tab[ix]) * MP::ld(&tab[N + iy])) * MP::ld(&tab[2 * N + iz]);
+}
 // pencil output: shift, optional i kz factor, from a shared component tile
-template <typename T, int N, int W>
+template <typename T, int N, int W, class MP>
 struct PencilOutSrc {
   const cpx<T>* s;
   const cpx<T>* sh;
@@ -77,7 +111,7 @@ struct PencilOutSrc {
   bool deriv;
   __device__ __forceinline__ cpx<T> get(int line, int e) const {
     cpx<T> v = s[e * W + line];
-    if (sh) v = v * phase3(sh, N, x0 + line, iy, e);
+    if (sh) v = v * phase3p<MP>(sh, N, x0 + line, iy, e);
     if (deriv) v = mul_si(v, (T)kof(e, N));
     return v;
   }
@@ -86,7 +120,7 @@ struct PencilOutSrc {
 // ---- spectral stage at one mode (Sec. 4.1, 4.2, 6.1) ----------------------------------
 // nv: de-shifted, weighted transform of u x omega at the mode (ignored if nF == 0).
 // Returns S_next for every component and performs the mode's global writes.
-template <typename T>
+template <typename T, class MP>
 __device__ __forceinline__ void spectral_point(const PencilArgs<T>& a, int kx, int ky, int kz,
                                                int iy, int iz, size_t g, size_t fstride,
                                                cpx<T> nv[3], cpx<T> sn[3]) {
@@ -131,92 +165,92 @@ __device__ __forceinline__ void spectral_point(const PencilArgs<T>& a, int kx, i
     cpx<T> s = mk<T>(0, 0);
     switch (a.mode) {
       case MODE_INIT:
-        s = a.src[gi];
+        s = MP::ldw(&a.src[gi]);
         break;
       case MODE_RK2_1:
-        s = Eh * (a.state[gi] + hdt * nv[c]);
+        s = Eh * (MP::ldw(&a.state[gi]) + hdt * nv[c]);
         break;
       case MODE_RK2_2:
-        s = E1 * a.state[gi] + (dt * Eh) * nv[c];
-        a.state[gi] = s;
+        s = E1 * MP::ldw(&a.state[gi]) + (dt * Eh) * nv[c];
+        MP::st(&a.state[gi], s);
         break;
       case MODE_RK4_1: {
-        const cpx<T> s0 = a.state[gi];
-        a.acc[gi] = E1 * s0 + (dt / T(6) * E1) * nv[c];
+        const cpx<T> s0 = MP::ldw(&a.state[gi]);
+        MP::st(&a.acc[gi], E1 * s0 + (dt / T(6) * E1) * nv[c]);
         s = Eh * (s0 + hdt * nv[c]);
       } break;
       case MODE_RK4_2: {
-        const cpx<T> s0 = a.state[gi];
-        a.acc[gi] = a.acc[gi] + (dt / T(3) * Eh) * nv[c];
+        const cpx<T> s0 = MP::ldw(&a.state[gi]);
+        MP::st(&a.acc[gi], MP::ldw(&a.acc[gi]) + (dt / T(3) * Eh) * nv[c]);
         s = Eh * s0 + hdt * nv[c];
       } break;
       case MODE_RK4_3: {
-        const cpx<T> s0 = a.state[gi];
-        a.acc[gi] = a.acc[gi] + (dt / T(3) * Eh) * nv[c];
+        const cpx<T> s0 = MP::ldw(&a.state[gi]);
+        MP::st(&a.acc[gi], MP::ldw(&a.acc[gi]) + (dt / T(3) * Eh) * nv[c]);
         s = E1 * s0 + (dt * Eh) * nv[c];
       } break;
       case MODE_RK4_4:
-        s = a.acc[gi] + (dt / T(6)) * nv[c];
-        a.state[gi] = s;
+        s = MP::ldw(&a.acc[gi]) + (dt / T(6)) * nv[c];
+        MP::st(&a.state[gi], s);
         break;
       case MODE_ROG_1: {
-        const cpx<T> s0 = a.state[gi];
-        a.state[gi] = E1 * s0 + (hdt * Eh) * nv[c];
+        const cpx<T> s0 = MP::ldw(&a.state[gi]);
+        MP::st(&a.state[gi], E1 * s0 + (hdt * Eh) * nv[c]);
         s = E1 * (s0 + dt * nv[c]);
       } break;
       case MODE_ROG_2:
-        s = a.state[gi] + (hdt * Eh) * nv[c];
-        a.state[gi] = s;
+        s = MP::ldw(&a.state[gi]) + (hdt * Eh) * nv[c];
+        MP::st(&a.state[gi], s);
         break;
       case MODE_NL:
-        a.acc[gi] = nv[c];
+        MP::st(&a.acc[gi], nv[c]);
         break;
       case MODE_PROJECT:
-        a.state[gi] = nv[c];
+        MP::st(&a.state[gi], nv[c]);
         break;
     }
     sn[c] = s;
     if (a.shell && kx <= a.fK && abs(ky) <= a.fK && abs(kz) <= a.fK) {
       const int fi = ((kz + a.fK) * D1 + (ky + a.fK)) * (a.fK + 1) + kx;
-      a.shell[c * D + fi] = s;
+      MP::st(&a.shell[c * D + fi], s);
     }
   }
 }
 
 // ---- pencil pass --------------------------------------------------------------------
-template <typename T, int N>
-__global__ void __launch_bounds__(K2Cfg<T, N>::NTP) k2_pencil(PencilArgs<T> a) {
+// One tile: TX consecutive kx at one ky, all kz.  smem: 4 tiles (5 with two inputs).
+template <typename T, int N, class MP>
+__device__ __forceinline__ void pencil_tile(const PencilArgs<T>& a, int tile_id, cpx<T>* buf) {
   using C = K2Cfg<T, N>;
   constexpr int M = N / 2, TX = C::TX, NT = C::NTP, tile = N * TX;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  cpx<T>* buf = reinterpret_cast<cpx<T>*>(smem_raw);
   cpx<T>* bc[3] = {buf, buf + tile, buf + 2 * tile};
   cpx<T>* W = buf + 3 * tile;
   cpx<T>* b3 = buf + 4 * tile;
   constexpr int ntx = M / TX;
-  const int iy = blockIdx.x / ntx;
-  const int x0 = (blockIdx.x % ntx) * TX;
+  const int iy = tile_id / ntx;
+  const int x0 = (tile_id % ntx) * TX;
   const size_t fstride = (size_t)N * N * M;
   const int ky = kof(iy, N);
+  const bool act = threadIdx.x < NT;
 
   if (a.nF > 0) {
     for (int c = 0; c < 3; ++c) {
-      cfft<T, N, 1, TX, NT, true, -1>(ColIn<T, N, TX>{a.F[0] + c * fstride, iy, x0},
+      cfft<T, N, 1, TX, NT, true, -1>(ColIn<T, N, TX, MP>{a.F[0] + c * fstride, iy, x0},
                                       SmTile<T, TX>{bc[c]}, W, a.tw);
       __syncthreads();
       if (a.nF > 1) {
-        cfft<T, N, 1, TX, NT, true, -1>(ColIn<T, N, TX>{a.F[1] + c * fstride, iy, x0},
+        cfft<T, N, 1, TX, NT, true, -1>(ColIn<T, N, TX, MP>{a.F[1] + c * fstride, iy, x0},
                                         SmTile<T, TX>{b3}, W, a.tw);
         __syncthreads();
       }
-      for (int e = threadIdx.x; e < tile; e += NT) {
+      for (int e = threadIdx.x; act && e < tile; e += NT) {
         const int iz = e / TX, x = e % TX;
         cpx<T> v = bc[c][e];
-        if (a.dsh[0]) v = mul_conj(v, phase3(a.dsh[0], N, x0 + x, iy, iz));
+        if (a.dsh[0]) v = mul_conj(v, phase3p<MP>(a.dsh[0], N, x0 + x, iy, iz));
         v = a.wF[0] * v;
         if (a.nF > 1) {
           cpx<T> w = b3[e];
-          if (a.dsh[1]) w = mul_conj(w, phase3(a.dsh[1], N, x0 + x, iy, iz));
+          if (a.dsh[1]) w = mul_conj(w, phase3p<MP>(a.dsh[1], N, x0 + x, iy, iz));
           v = v + a.wF[1] * w;
         }
         bc[c][e] = v;
@@ -225,7 +259,7 @@ __global__ void __launch_bounds__(K2Cfg<T, N>::NTP) k2_pencil(PencilArgs<T> a) {
     }
   }
 
-  for (int e = threadIdx.x; e < tile; e += NT) {
+  for (int e = threadIdx.x; act && e < tile; e += NT) {
     const int iz = e / TX, x = e % TX;
     const int kx = x0 + x, kz = kof(iz, N);
     const size_t g = ((size_t)iz * N + iy) * M + kx;
@@ -235,7 +269,7 @@ __global__ void __launch_bounds__(K2Cfg<T, N>::NTP) k2_pencil(PencilArgs<T> a) {
       nv[1] = bc[1][e];
       nv[2] = bc[2][e];
     }
-    spectral_point(a, kx, ky, kz, iy, iz, g, fstride, nv, sn);
+    spectral_point<T, MP>(a, kx, ky, kz, iy, iz, g, fstride, nv, sn);
     bc[0][e] = sn[0];
     bc[1][e] = sn[1];
     bc[2][e] = sn[2];
@@ -245,11 +279,17 @@ __global__ void __launch_bounds__(K2Cfg<T, N>::NTP) k2_pencil(PencilArgs<T> a) {
   for (int o = 0; o < a.nOut; ++o) {
     for (int f = 0; f < 5; ++f) {
       const int c = f < 3 ? f : f - 3;
-      cfft<T, N, 1, TX, NT, true, 1>(PencilOutSrc<T, N, TX>{bc[c], a.osh[o], iy, x0, f >= 3},
-                                     ColOut<T, N, TX>{a.out[o] + f * fstride, iy, x0}, W, a.tw);
+      cfft<T, N, 1, TX, NT, true, 1>(PencilOutSrc<T, N, TX, MP>{bc[c], a.osh[o], iy, x0, f >= 3},
+                                     ColOut<T, N, TX, MP>{a.out[o] + f * fstride, iy, x0}, W, a.tw);
       __syncthreads();
     }
   }
+}
+
+template <typename T, int N>
+__global__ void __launch_bounds__(K2Cfg<T, N>::NTP) k2_pencil(PencilArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  pencil_tile<T, N, MemNC>(a, blockIdx.x, reinterpret_cast<cpx<T>*>(smem_raw));
 }
 
 // ---- slab pass: y transforms --------------------------------------------------------
@@ -271,83 +311,92 @@ struct YInvSrc {
     return mul_si(m[i + fs], kx) - mul_si(m[i], ky);                // i kx u_y - i ky u_x
   }
 };
-template <typename T, int N>
+template <typename T, int N, class MP>
 struct ScrCol {  // one field [plane][y|ky][kx], column tile of a plane (scratch or Ft)
   cpx<T>* p;
   int zg, x0;
   __device__ __forceinline__ cpx<T> get(int line, int e) const {
-    return p[((size_t)zg * N + e) * (N / 2) + x0 + line];
+    return MP::ldw(&p[((size_t)zg * N + e) * (N / 2) + x0 + line]);
   }
   __device__ __forceinline__ void put(int line, int e, cpx<T> v) const {
-    p[((size_t)zg * N + e) * (N / 2) + x0 + line] = v;
+    MP::st(&p[((size_t)zg * N + e) * (N / 2) + x0 + line], v);
   }
 };
 
-template <typename T, int N, int F>
+template <typename T, int N, int F, class MP>
 __device__ __forceinline__ void yinv_field(const SlabArgs<T>& a, const cpx<T>* in, cpx<T>* W,
                                            int zg, int x0, size_t sstride) {
   using C = K2Cfg<T, N>;
   cfft<T, N, 1, C::TYI, C::NTYI, true, 1>(YInvSrc<T, N, F, C::TYI>{in, x0},
-                                          ScrCol<T, N>{a.scr + F * sstride, zg, x0}, W, a.tw);
+                                          ScrCol<T, N, MP>{a.scr + F * sstride, zg, x0}, W, a.tw);
   __syncthreads();
+}
+
+// One tile: TYI consecutive kx of plane zg; the 5 mixed input tiles are staged first.
+template <typename T, int N, class MP>
+__device__ __forceinline__ void yinv_tile(const SlabArgs<T>& a, int tx, int zg, cpx<T>* in) {
+  using C = K2Cfg<T, N>;
+  constexpr int M = N / 2, TY = C::TYI, NT = C::NTYI, tile = N * TY;
+  cpx<T>* W = in + 5 * tile;
+  const int x0 = tx * TY, z = a.z0 + zg;
+  const size_t sstride = (size_t)a.G * N * M;
+  const size_t fs = (size_t)N * N * M;
+  for (int i = threadIdx.x; threadIdx.x < NT && i < 5 * tile; i += NT) {
+    const int f = i / tile, rem = i % tile, e = rem / TY, line = rem % TY;
+    in[i] = MP::ld(&a.mixed[f * fs + ((size_t)z * N + e) * M + x0 + line]);
+  }
+  __syncthreads();
+  yinv_field<T, N, 0, MP>(a, in, W, zg, x0, sstride);
+  yinv_field<T, N, 1, MP>(a, in, W, zg, x0, sstride);
+  yinv_field<T, N, 2, MP>(a, in, W, zg, x0, sstride);
+  yinv_field<T, N, 3, MP>(a, in, W, zg, x0, sstride);
+  yinv_field<T, N, 4, MP>(a, in, W, zg, x0, sstride);
+  yinv_field<T, N, 5, MP>(a, in, W, zg, x0, sstride);
 }
 
 template <typename T, int N>
 __global__ void __launch_bounds__(K2Cfg<T, N>::NTYI) k2_yinv(SlabArgs<T> a) {
-  using C = K2Cfg<T, N>;
-  constexpr int M = N / 2, TY = C::TYI, NT = C::NTYI, tile = N * TY;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  cpx<T>* in = reinterpret_cast<cpx<T>*>(smem_raw);
-  cpx<T>* W = in + 5 * tile;
-  const int x0 = blockIdx.x * TY, zg = blockIdx.y, z = a.z0 + zg;
-  const size_t sstride = (size_t)a.G * N * M;
-  const size_t fs = (size_t)N * N * M;
-  for (int i = threadIdx.x; i < 5 * tile; i += NT) {
-    const int f = i / tile, rem = i % tile, e = rem / TY, line = rem % TY;
-    in[i] = ldg(&a.mixed[f * fs + ((size_t)z * N + e) * M + x0 + line]);
-  }
-  __syncthreads();
-  yinv_field<T, N, 0>(a, in, W, zg, x0, sstride);
-  yinv_field<T, N, 1>(a, in, W, zg, x0, sstride);
-  yinv_field<T, N, 2>(a, in, W, zg, x0, sstride);
-  yinv_field<T, N, 3>(a, in, W, zg, x0, sstride);
-  yinv_field<T, N, 4>(a, in, W, zg, x0, sstride);
-  yinv_field<T, N, 5>(a, in, W, zg, x0, sstride);
+  yinv_tile<T, N, MemNC>(a, blockIdx.x, blockIdx.y, reinterpret_cast<cpx<T>*>(smem_raw));
 }
 
-template <typename T, int N>
-__global__ void __launch_bounds__(K2Cfg<T, N>::NTY, 2) k2_yfwd(SlabArgs<T> a) {
+template <typename T, int N, class MP>
+__device__ __forceinline__ void yfwd_tile(const SlabArgs<T>& a, int tx, int zg, cpx<T>* W) {
   using C = K2Cfg<T, N>;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  cpx<T>* W = reinterpret_cast<cpx<T>*>(smem_raw);
-  const int x0 = blockIdx.x * C::TY, zg = blockIdx.y, z = a.z0 + zg;
+  const int x0 = tx * C::TY, z = a.z0 + zg;
   const size_t sstride = (size_t)a.G * N * (N / 2);
   const size_t fstride = (size_t)N * N * (N / 2);
   for (int f = 0; f < 3; ++f) {
-    cfft<T, N, 1, C::TY, C::NTY, true, -1>(ScrCol<T, N>{a.scr + f * sstride, zg, x0},
-                                           ScrCol<T, N>{a.Ft + f * fstride, z, x0}, W, a.tw);
+    cfft<T, N, 1, C::TY, C::NTY, true, -1>(ScrCol<T, N, MP>{a.scr + f * sstride, zg, x0},
+                                           ScrCol<T, N, MP>{a.Ft + f * fstride, z, x0}, W, a.tw);
     __syncthreads();
   }
 }
 
-// ---- slab pass: x rows --------------------------------------------------------------
 template <typename T, int N>
-__global__ void __launch_bounds__(K2Cfg<T, N>::NTX) k2_xrow(SlabArgs<T> a) {
+__global__ void __launch_bounds__(K2Cfg<T, N>::NTY, 2) k2_yfwd(SlabArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  yfwd_tile<T, N, MemNC>(a, blockIdx.x, blockIdx.y, reinterpret_cast<cpx<T>*>(smem_raw));
+}
+
+// ---- slab pass: x rows --------------------------------------------------------------
+// One tile: RX consecutive rows (plane, y) of the group.
+template <typename T, int N, class MP>
+__device__ __forceinline__ void xrow_tile(const SlabArgs<T>& a, int tile_id, cpx<T>* buf) {
   using C = K2Cfg<T, N>;
   constexpr int M = N / 2, RX = C::RX, NT = C::NTX;
   using RowT = WorkTile<T, M, 3 * RX, false>;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  cpx<T>* buf = reinterpret_cast<cpx<T>*>(smem_raw);
   const RowT U{buf}, V{buf + C::XBUF};
   cpx<T>* work = buf + 2 * C::XBUF;
+  const bool act = threadIdx.x < NT;
   const int rows_total = a.G * N;
-  const int r0 = blockIdx.x * RX;
+  const int r0 = tile_id * RX;
   const int nr = min(RX, rows_total - r0);
   const size_t sstride = (size_t)a.G * N * M;
   constexpr int NP = M / 2 + 1;  // pairs (k, M-k), k = 0..M/2
 
   // load the 6 fields with the c2r pre-processing (Hermitian half row -> packed Z')
-  for (int i = threadIdx.x; i < 6 * RX * NP; i += NT) {
+  for (int i = threadIdx.x; act && i < 6 * RX * NP; i += NT) {
     const int f = i / (RX * NP), rem = i % (RX * NP), row = rem / NP, k = rem % NP;
     const RowT& B = f < 3 ? U : V;
     const int line = (f % 3) * RX + row;
@@ -361,14 +410,14 @@ __global__ void __launch_bounds__(K2Cfg<T, N>::NTX) k2_xrow(SlabArgs<T> a) {
     }
     const cpx<T>* src = a.scr + f * sstride + (size_t)(r0 + row) * M;
     if (k == 0) {
-      const T r = ldg(&src[0]).x;
+      const T r = MP::ld(&src[0]).x;
       B.put(line, 0, mk<T>(r, r));
       if (M % 2 == 0 && M > 1) {
-        const cpx<T> X = ldg(&src[M / 2]);
+        const cpx<T> X = MP::ld(&src[M / 2]);
         B.put(line, M / 2, (X + conjg(X)) - (X - conjg(X)));
       }
     } else if (k < M - k) {
-      const cpx<T> Xk = ldg(&src[k]), Xm = ldg(&src[M - k]);
+      const cpx<T> Xk = MP::ld(&src[k]), Xm = MP::ld(&src[M - k]);
       const cpx<T> tk = ldg(&a.tw[k]);
       const cpx<T> A = Xk + conjg(Xm), Bv = Xk - conjg(Xm);
       B.put(line, k, A + mul_si(conjg(tk) * Bv, T(1)));
@@ -383,7 +432,7 @@ __global__ void __launch_bounds__(K2Cfg<T, N>::NTX) k2_xrow(SlabArgs<T> a) {
   __syncthreads();
 
   // u x omega on the packed real rows, written over u
-  for (int i = threadIdx.x; i < RX * M; i += NT) {
+  for (int i = threadIdx.x; act && i < RX * M; i += NT) {
     const int row = i / M, k = i % M;
     cpx<T> u[3], w[3];
 #pragma unroll
@@ -404,27 +453,33 @@ __global__ void __launch_bounds__(K2Cfg<T, N>::NTX) k2_xrow(SlabArgs<T> a) {
   __syncthreads();
 
   // r2c post-processing and store
-  for (int i = threadIdx.x; i < 3 * RX * NP; i += NT) {
+  for (int i = threadIdx.x; act && i < 3 * RX * NP; i += NT) {
     const int f = i / (RX * NP), rem = i % (RX * NP), row = rem / NP, k = rem % NP;
     if (row >= nr) continue;
     const int line = f * RX + row;
     cpx<T>* dst = a.scr + f * sstride + (size_t)(r0 + row) * M;
     if (k == 0) {
       const cpx<T> Z = U.get(line, 0);
-      dst[0] = mk<T>(Z.x + Z.y, T(0));
+      MP::st(&dst[0], mk<T>(Z.x + Z.y, T(0)));
       if (M % 2 == 0 && M > 1) {
         const cpx<T> Zk = U.get(line, M / 2);
-        dst[M / 2] = T(0.5) * ((Zk + conjg(Zk)) - (Zk - conjg(Zk)));
+        MP::st(&dst[M / 2], T(0.5) * ((Zk + conjg(Zk)) - (Zk - conjg(Zk))));
       }
     } else if (k < M - k) {
       const cpx<T> Zk = U.get(line, k), Zm = U.get(line, M - k);
       const cpx<T> Wk = ldg(&a.tw[k]);
       const cpx<T> A = Zk + conjg(Zm), B = Zk - conjg(Zm);
-      dst[k] = T(0.5) * (A - mul_si(Wk * B, T(1)));
+      MP::st(&dst[k], T(0.5) * (A - mul_si(Wk * B, T(1))));
       const cpx<T> A2 = Zm + conjg(Zk), B2 = Zm - conjg(Zk);
-      dst[M - k] = T(0.5) * (A2 + mul_si(conjg(Wk) * B2, T(1)));
+      MP::st(&dst[M - k], T(0.5) * (A2 + mul_si(conjg(Wk) * B2, T(1))));
     }
   }
+}
+
+template <typename T, int N>
+__global__ void __launch_bounds__(K2Cfg<T, N>::NTX) k2_xrow(SlabArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  xrow_tile<T, N, MemNC>(a, blockIdx.x, reinterpret_cast<cpx<T>*>(smem_raw));
 }
 
 // ---- registry entry of one size ------------------------------------------------------
