@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=50)
     ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
     ap.add_argument("--no-rk4", action="store_true")
+    ap.add_argument("--batch-steps", type=int, default=200,
+                    help="steps of the 64-member ensemble leg (0: skip)")
     return ap.parse_args()
 
 
@@ -320,6 +322,38 @@ def main():
             "ms_per_step": ms4 / Kr, "step_frac_hbm": (mb4 / (ms4 / Kr / 1000.0) / 1e9) / hbm}
         line["sim_time_speedup_vs_rk4"] = line["sim_time_per_s"] / line["rk4_two_thirds"]["sim_time_per_s"]
         r.close()
+
+    # batched ensemble: 64 Taylor-Green members with 1% perturbations, 16 each of
+    # N = 32, 64, 96, 128, Rogallo RK2 FP32, one persistent launch per call
+    if args.batch_steps > 0:
+        Ns = [32] * 16 + [64] * 16 + [96] * 16 + [128] * 16
+        dts = [0.5 * (2 * math.pi / n) / 2.0 for n in Ns]
+        b = ns.Batch(Ns, [NU] * len(Ns), [n / 2.0 for n in Ns], seeds=list(range(len(Ns))),
+                     scheme=ns.RK2_PS_RANDOM, precision=ns.FP32, stream=stream.cuda_stream)
+        for i, n in enumerate(Ns):
+            b.set_velocity(i, inputs.taylor_green_perturbed(n, i))
+        b.step(dts, 3)
+        Kb = args.batch_steps
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        b.step(dts, Kb)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        msb = reduce_max(e0.elapsed_time(e1), world)
+        Eb, _ = b.energy()
+        model = sum(44.0 * n ** 3 * 4.0 for n in Ns)
+        line["batched_ensemble"] = {
+            "members": len(Ns), "sizes": "16 x {32, 64, 96, 128}", "steps": Kb,
+            "member_steps_per_s": world * len(Ns) * Kb / (msb / 1000.0),
+            "ensemble_steps_per_s": world * Kb / (msb / 1000.0), "ms_per_step": msb / Kb,
+            "launches_per_call": 1, "persistent_ctas": b.grid(),
+            "gcells_per_s": world * sum(n ** 3 for n in Ns) * Kb / (msb / 1000.0) / 1e9,
+            "model_bytes_per_step": model,
+            "frac_hbm": (model / (msb / Kb / 1000.0) / 1e9) / hbm,
+            "finite": bool(np.all(np.isfinite(Eb)))}
+        b.close()
 
     # end to end through the C ABI with host buffers: host velocity in, E/eps out every step
     Ke = max(3, min(args.e2e_steps, K))
