@@ -110,6 +110,24 @@ int ns_set_shifts(ns_ctx* ctx, const double* delta_alpha, int nsteps);
  * FFT[u_D x w_D], mean mode zero.  Writes host re_im_out[3][N][N][N/2][2]. */
 int ns_nonlinear(ns_ctx* ctx, const double* re_im_in, const double* delta, double* re_im_out);
 
+/* Gradient of a loss on the final state with respect to the initial physical velocity
+ * (hand-written adjoint; the paper has none).  From u0 (host [3][N][N][N]) runs nsteps steps
+ * of size dt of the context's scheme (NS_RK2_PS_RANDOM or _APPROX, with the forcing if set;
+ * shifts from the context's seed, step counter starting at 0), keeping the state every
+ * ckpt_every steps; loss NS_LOSS_DISSIPATION: L = eps(T) = nu sum_k k^2 |uh|^2, or
+ * NS_LOSS_ENERGY: L = E(T).  The reverse sweep recomputes each segment's states from its
+ * checkpoint and applies the transposed step: with <a,b> = sum_k Re(conj(a).b) and
+ * lambda the cotangent of S_{n+1}, rho = dt/2 E_{dt/2} lambda,
+ *   mu = J*_beta(S1; rho) + O*(S1; rho),  sigma = dt E_dt mu,
+ *   lambda_n = E_dt (lambda + mu) + J*_alpha(S0; rho + sigma) + O*(S0; rho + sigma),
+ * J*_D(S; r) = T P e^{-ik.D} [F(w x r') + ik x F(r' x u)], r' = F^{-1}(e^{ik.D} r), and
+ * O*(S; r) = (da/db) Re<f, r> f for the forcing O = a f.  Writes L to *loss_out and dL/du0
+ * to grad_u0_out (host [3][N][N][N], gradient for the physical dot product).  Leaves the
+ * context at the final state (t = nsteps dt). */
+enum { NS_LOSS_DISSIPATION = 0, NS_LOSS_ENERGY = 1 };
+int ns_vjp(ns_ctx* ctx, const double* u0, int nsteps, double dt, int ckpt_every, int loss,
+           double* loss_out, double* grad_u0_out);
+
 /* Kinetic energy E = (1/2) sum_k |uh|^2 and dissipation eps = nu sum_k k^2 |uh|^2 (full
  * spectrum sums, FP64 accumulation; Sec. 3.4).  NS_ERR_NONFINITE if either is not finite. */
 int ns_energy(ns_ctx* ctx, double* E, double* eps);

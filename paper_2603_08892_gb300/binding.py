@@ -77,6 +77,9 @@ _profile_read = _sig("ns_profile_read", ctypes.c_int,
                       ctypes.POINTER(ctypes.c_int64)])
 _nonlinear_noalloc = _sig("ns_nonlinear_noalloc", ctypes.c_int,
                          [_vp, _vp, ctypes.c_int, ctypes.c_double, ctypes.c_int, _dp, _vp])
+_vjp = _sig("ns_vjp", ctypes.c_int, [_vp, _dp, ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                                     ctypes.c_int, _dp, _dp])
+LOSS_DISSIPATION, LOSS_ENERGY = 0, 1
 _batch_init = _sig("ns_batch_init", ctypes.c_int,
                    [ctypes.POINTER(_vp), ctypes.c_int, ctypes.POINTER(ctypes.c_int), _dp, _dp,
                     ctypes.POINTER(ctypes.c_uint64), ctypes.c_int, ctypes.c_int, _vp])
@@ -96,7 +99,7 @@ EXPORTED = ["ns_init", "ns_init_ex", "ns_init_error", "ns_destroy", "ns_last_err
             "ns_set_velocity", "ns_get_velocity", "ns_get_state", "ns_set_state",
             "ns_set_forcing", "ns_step", "ns_set_shifts", "ns_nonlinear", "ns_energy",
             "ns_energy_spectrum", "ns_time", "ns_set_time", "ns_device_state",
-            "ns_model_bytes_per_step", "ns_profile", "ns_profile_read", "ns_nonlinear_noalloc", "ns_batch_init", "ns_batch_destroy", "ns_batch_last_error",
+            "ns_model_bytes_per_step", "ns_profile", "ns_profile_read", "ns_nonlinear_noalloc", "ns_vjp", "ns_batch_init", "ns_batch_destroy", "ns_batch_last_error",
             "ns_batch_member", "ns_batch_set_velocity", "ns_batch_get_state", "ns_batch_step",
             "ns_batch_energy", "ns_batch_set_spin_limit", "ns_batch_test_stall", "ns_batch_grid"]
 
@@ -221,6 +224,14 @@ class Solver:
 
     def model_bytes_per_step(self):
         return _model_bytes(self._h)
+
+    def vjp(self, u0, nsteps, dt, ckpt_every=10, loss=LOSS_DISSIPATION):
+        """(L, dL/du0) of the loss on the state after nsteps steps from u0 (see ns_vjp)."""
+        u = np.ascontiguousarray(u0, dtype=np.float64)
+        g = np.empty_like(u)
+        L = ctypes.c_double()
+        self._check(_vjp(self._h, _ptr(u), nsteps, dt, ckpt_every, loss, ctypes.byref(L), _ptr(g)))
+        return L.value, g
 
     def profile(self, enable=True):
         self._check(_profile(self._h, 1 if enable else 0))

@@ -128,6 +128,8 @@ struct SolverBase {
                            uint64_t seed) = 0;
   virtual void* state_ptr() = 0;
   virtual void buffers(double dt, NsCtxBuffers* b) = 0;
+  virtual void vjp(const double* u0, int nsteps, double dt, int ckpt, int loss, double* L,
+                   double* grad) = 0;
   virtual void profile(int on) = 0;
   virtual void profile_read(int k, double* ms, int64_t* n, int64_t* launches) = 0;
 };
@@ -331,6 +333,8 @@ struct Solver : SolverBase {
     cudaFree(Ft[0]); cudaFree(Ft[1]); cudaFree(scr); cudaFree(tw); cudaFree(ifac);
     cudaFree(shtab); cudaFree(d_shifts); cudaFree(red); cudaFree(d_err);
     cudaFree(fpat); cudaFree(force); cudaFree(shell);
+    for (auto* p : adj) cudaFree(p);
+    cudaFree(mixedB); cudaFree(FtB); cudaFree(shS); cudaFree(shR); cudaFree(ftab);
     for (auto& r : prof.rec) {
       cudaEventDestroy(r.second.first);
       cudaEventDestroy(r.second.second);
@@ -706,10 +710,13 @@ struct Solver : SolverBase {
     sync_check();
   }
 
-  void get_velocity(double* u) override {
+  void get_velocity(double* u) override { to_physical(state, u); }
+
+  // spectral [3][N][N][M] -> physical host [3][N][N][N] (inverse z, y, x transforms)
+  void to_physical(const cpx<T>* src, double* u) {
     PencilArgs<T> p = pencil_args(MODE_INIT);
     p.shell = nullptr;
-    p.src = state;
+    p.src = src;
     p.nOut = 1; p.out[0] = mixed[0];
     pencil(p);
     T* rout = reinterpret_cast<T*>(Ft[0]);  // 3 N^3 reals
@@ -772,6 +779,218 @@ struct Solver : SolverBase {
     q.nF = 1; q.F[0] = Ft[0]; q.dsh[0] = shift_tab(0); q.wF[0] = (T)(1.0 / ((double)N * N * N));
     pencil(q);
     download(acc, out);
+  }
+
+  // ---- adjoint (transposed linearisation) of the RK2 phase-shift random / split step ----
+  // Formulas: oracle-independent restatement in include/ns.h (ns_vjp).  Buffers are
+  // allocated on first use and kept by the context.
+  std::vector<cpx<T>*> adj;  // work vectors of 3 fields
+  cpx<T>* mixedB = nullptr;
+  cpx<T>* FtB = nullptr;
+  cpx<T>* shS = nullptr;
+  cpx<T>* shR = nullptr;
+  cpx<T>* ftab = nullptr;
+
+  cpx<T>* vec(int i) { return adj[i]; }
+
+  void ew(int op, const cpx<T>* x, const cpx<T>* y, const cpx<T>* z, cpx<T>* o, double c = 0.0) {
+    k_elementwise<T><<<4 * nsm, 256, 0, st>>>(op, N, (T)cur_dt, (T)c, ifac, x, y, z, o);
+    LAUNCH_CHECK();
+  }
+
+  // Nt_D(S) -> out  (D = shift table or null)
+  void nl_eval(const cpx<T>* S, const cpx<T>* tab, cpx<T>* out) {
+    PencilArgs<T> p = pencil_args(MODE_INIT);
+    p.shell = nullptr;
+    p.src = S;
+    p.nOut = 1; p.osh[0] = tab; p.out[0] = mixed[0];
+    pencil(p);
+    slab(mixed[0], Ft[0]);
+    PencilArgs<T> q = pencil_args(MODE_NL);
+    q.shell = nullptr;
+    q.acc = out;
+    q.nF = 1; q.F[0] = Ft[0]; q.dsh[0] = tab; q.wF[0] = (T)(1.0 / ((double)N * N * N));
+    pencil(q);
+  }
+
+  // slab pass of an adjoint cross product with the generic kernels
+  void slab_adj(int xmode, cpx<T>* out) {
+    SlabArgs<T> a = slab_args();
+    a.mixed = mixed[0];
+    a.mixedB = mixedB;
+    a.Ft = out;
+    a.xmode = xmode;
+    for (int z0 = 0; z0 < N; z0 += G) {
+      a.z0 = z0;
+      a.G = (z0 + G <= N) ? G : N - z0;
+      k_yinv<T><<<dim3(M / TY, a.G), bdYi, smYi, st>>>(a);
+      k_xrow<T><<<(a.G * N + RX - 1) / RX, bdX, smX, st>>>(a);
+      k_yfwd<T><<<dim3(M / TY, a.G), bdYf, smYf, st>>>(a);
+    }
+    LAUNCH_CHECK();
+  }
+
+  // J*(rho) at state S for shift table tab: T P e^{-ikD}[F(w x r) + ik x F(r x u)]
+  void nl_vjp(const cpx<T>* S, const cpx<T>* tab, const cpx<T>* rho, cpx<T>* out, cpx<T>* tmpA,
+              cpx<T>* tmpB) {
+    PencilArgs<T> p = pencil_args(MODE_INIT);
+    p.shell = nullptr;
+    p.src = S;
+    p.nOut = 1; p.osh[0] = tab; p.out[0] = mixed[0];
+    pencil(p);
+    p.src = rho;
+    p.out[0] = mixedB;
+    pencil(p);
+    slab_adj(XMODE_ADJ_WR, Ft[0]);
+    slab_adj(XMODE_ADJ_RU, FtB);
+    PencilArgs<T> q = pencil_args(MODE_NL);
+    q.shell = nullptr;
+    q.nF = 1; q.dsh[0] = tab; q.wF[0] = (T)(1.0 / ((double)N * N * N));
+    q.F[0] = Ft[0]; q.acc = tmpA;
+    pencil(q);
+    q.F[0] = FtB; q.acc = tmpB;
+    pencil(q);
+    ew(EW_CURL_ADD, tmpA, tmpB, nullptr, out);
+  }
+
+  const cpx<double>* pattern_ptr(double ts, double* theta) {
+    const double x = ts / ftcorr;
+    const int64_t j = (int64_t)std::floor(x);
+    *theta = x - (double)j;
+    if (j < fj0 || j - fj0 + 1 >= fpat_cap)
+      throw NsError{NS_ERR_INTERNAL, "forcing pattern index out of the prepared range"};
+    return fpat + (size_t)(j - fj0) * 3 * fDn();
+  }
+
+  // out += O(S) at time ts
+  void add_forcing(const cpx<T>* S, double ts, cpx<T>* out) {
+    if (fkind == NS_FORCE_NONE) return;
+    double th;
+    const cpx<double>* pj = pattern_ptr(ts, &th);
+    k_shell_gather<T><<<1, 256, 0, st>>>(S, N, fK, shS);
+    k_force_coef<T><<<1, 256, 0, st>>>(pj, pj + 3 * fDn(), th, shS, fK, cur_dt, feps, ftab, nullptr);
+    k_shell_add<T><<<1, 256, 0, st>>>(out, N, fK, ftab);
+    LAUNCH_CHECK();
+  }
+
+  // out += (dO/dS at S, time ts)^T rho
+  void add_forcing_vjp(const cpx<T>* S, double ts, const cpx<T>* rho, cpx<T>* out) {
+    if (fkind == NS_FORCE_NONE) return;
+    double th;
+    const cpx<double>* pj = pattern_ptr(ts, &th);
+    k_shell_gather<T><<<1, 256, 0, st>>>(S, N, fK, shS);
+    k_shell_gather<T><<<1, 256, 0, st>>>(rho, N, fK, shR);
+    k_force_vjp<T><<<1, 256, 0, st>>>(pj, pj + 3 * fDn(), th, shS, shR, fK, cur_dt, feps, ftab);
+    k_shell_add<T><<<1, 256, 0, st>>>(out, N, fK, ftab);
+    LAUNCH_CHECK();
+  }
+
+  void vjp(const double* u0, int nsteps, double dt, int ckpt, int loss, double* Lout,
+           double* grad) override {
+    const size_t vb = 3 * F1 * sizeof(cpx<T>);
+    const int nseg_states = ckpt;
+    const int nck = (nsteps + ckpt - 1) / ckpt + 1;
+    const int nvec = 12 + nseg_states + nck;
+    if ((int)adj.size() < nvec) {
+      for (auto* p : adj) cudaFree(p);
+      adj.assign(nvec, nullptr);
+      for (int i = 0; i < nvec; ++i) CUDA_TRY(cudaMalloc(&adj[i], vb));
+      if (!mixedB) CUDA_TRY(cudaMalloc(&mixedB, 5 * F1 * sizeof(cpx<T>)));
+      if (!FtB) CUDA_TRY(cudaMalloc(&FtB, 3 * F1 * sizeof(cpx<T>)));
+    }
+    if (fkind != NS_FORCE_NONE) {
+      cudaFree(shS); cudaFree(shR); cudaFree(ftab);
+      shS = shR = ftab = nullptr;
+      CUDA_TRY(cudaMalloc(&shS, 3 * (size_t)fDn() * sizeof(cpx<T>)));
+      CUDA_TRY(cudaMalloc(&shR, 3 * (size_t)fDn() * sizeof(cpx<T>)));
+      CUDA_TRY(cudaMalloc(&ftab, 3 * (size_t)fDn() * sizeof(cpx<T>)));
+    }
+    cpx<T>* N0 = vec(0);
+    cpx<T>* N1 = vec(1);
+    cpx<T>* S1 = vec(2);
+    cpx<T>* lam = vec(3);
+    cpx<T>* mu = vec(4);
+    cpx<T>* rho = vec(5);
+    cpx<T>* sig = vec(6);
+    cpx<T>* rs = vec(7);
+    cpx<T>* J = vec(8);
+    cpx<T>* tA = vec(9);
+    cpx<T>* tB = vec(10);
+    cpx<T>* tmp = vec(11);
+    cpx<T>** seg = &adj[12];
+    cpx<T>** ck = &adj[12 + nseg_states];
+
+    set_velocity(u0);
+    set_dt(dt);
+    const double dx = 2.0 * M_PI / N;
+    const bool approx = c->p.scheme == NS_RK2_PS_APPROX;
+    std::vector<double> sh(6 * (size_t)nsteps);
+    for (int n = 0; n < nsteps; ++n)
+      for (int i = 0; i < 3; ++i) {
+        const double da = approx ? 0.0 : dx * uniform01(c->p.seed, (uint64_t)(3 * n + i));
+        sh[6 * n + i] = da;
+        sh[6 * n + 3 + i] = da + 0.5 * dx;
+      }
+    upload_shifts(sh);
+    std::vector<double> times(nsteps + 1, 0.0);
+    for (int n = 0; n < nsteps; ++n) times[n + 1] = times[n] + dt;
+    if (fkind != NS_FORCE_NONE) prepare_forcing(0.0, times[nsteps]);
+
+    auto fwd = [&](const cpx<T>* S0, cpx<T>* Sout, int n) {
+      nl_eval(S0, shift_tab(2 * n), N0);
+      add_forcing(S0, times[n], N0);
+      ew(EW_ROG_S1, S0, N0, nullptr, S1);
+      nl_eval(S1, shift_tab(2 * n + 1), N1);
+      add_forcing(S1, times[n] + dt, N1);
+      ew(EW_ROG_SN, S0, N0, N1, Sout);
+    };
+
+    // forward sweep with checkpoints every ckpt steps
+    CUDA_TRY(cudaMemcpyAsync(ck[0], state, vb, cudaMemcpyDeviceToDevice, st));
+    CUDA_TRY(cudaMemcpyAsync(tmp, state, vb, cudaMemcpyDeviceToDevice, st));
+    for (int n = 0; n < nsteps; ++n) {
+      fwd(tmp, tmp, n);
+      if ((n + 1) % ckpt == 0 && n + 1 < nsteps) {
+        CUDA_TRY(cudaMemcpyAsync(ck[(n + 1) / ckpt], tmp, vb, cudaMemcpyDeviceToDevice, st));
+      }
+    }
+    CUDA_TRY(cudaMemcpyAsync(state, tmp, vb, cudaMemcpyDeviceToDevice, st));
+    double E, eps;
+    energy(&E, &eps);
+    *Lout = loss == NS_LOSS_ENERGY ? E : eps;
+    if (loss == NS_LOSS_ENERGY)
+      ew(EW_SCALE, state, nullptr, nullptr, lam, 1.0);
+    else
+      ew(EW_LOSS, state, nullptr, nullptr, lam, c->p.nu);
+
+    // reverse sweep, segment by segment, recomputing the forward states of the segment
+    for (int seg0 = ((nsteps - 1) / ckpt) * ckpt; seg0 >= 0; seg0 -= ckpt) {
+      const int seg1 = seg0 + ckpt < nsteps ? seg0 + ckpt : nsteps;
+      CUDA_TRY(cudaMemcpyAsync(seg[0], ck[seg0 / ckpt], vb, cudaMemcpyDeviceToDevice, st));
+      for (int n = seg0; n < seg1 - 1; ++n) fwd(seg[n - seg0], seg[n - seg0 + 1], n);
+      for (int n = seg1 - 1; n >= seg0; --n) {
+        const cpx<T>* S0 = seg[n - seg0];
+        const cpx<T>* ta = shift_tab(2 * n);
+        const cpx<T>* tb = shift_tab(2 * n + 1);
+        nl_eval(S0, ta, N0);
+        add_forcing(S0, times[n], N0);
+        ew(EW_ROG_S1, S0, N0, nullptr, S1);
+        ew(EW_RHO, lam, nullptr, nullptr, rho);
+        nl_vjp(S1, tb, rho, mu, tA, tB);
+        add_forcing_vjp(S1, times[n] + dt, rho, mu);
+        ew(EW_SIGMA, mu, nullptr, nullptr, sig);
+        ew(EW_ADD, rho, sig, nullptr, rs);
+        nl_vjp(S0, ta, rs, J, tA, tB);
+        add_forcing_vjp(S0, times[n], rs, J);
+        ew(EW_LAMBDA, lam, mu, J, lam);
+      }
+    }
+    // dL/du0 = F^{-1}(lambda_0) / N^3 (the initial truncation and projection are
+    // self-adjoint and lambda_0 already lies in their range)
+    ew(EW_SCALE, lam, nullptr, nullptr, tmp, 1.0 / ((double)N * N * N));
+    to_physical(tmp, grad);
+    c->t = times[nsteps];
+    c->step = nsteps;
   }
 
   void energy(double* E, double* eps) override {
@@ -1051,6 +1270,20 @@ int ns_device_state(ns_ctx* c, void** state, void** stream, int* precision) {
   if (stream) *stream = (void*)c->stream;
   if (precision) *precision = c->p.precision;
   return NS_OK;
+}
+
+int ns_vjp(ns_ctx* c, const double* u0, int nsteps, double dt, int ckpt_every, int loss,
+           double* loss_out, double* grad_u0_out) {
+  return guarded(c, [&]() {
+    if (!u0 || !loss_out || !grad_u0_out) return fail(c, NS_ERR_INVALID_ARG, "NULL argument");
+    if (c->p.scheme != NS_RK2_PS_RANDOM && c->p.scheme != NS_RK2_PS_APPROX)
+      return fail(c, NS_ERR_INVALID_ARG, "ns_vjp supports the RK2 phase-shift random/approx schemes");
+    if (nsteps < 1 || ckpt_every < 1 || !(dt > 0.0) || (loss != NS_LOSS_DISSIPATION && loss != NS_LOSS_ENERGY))
+      return fail(c, NS_ERR_INVALID_ARG, "need nsteps >= 1, ckpt_every >= 1, dt > 0 and a known loss");
+    c->solver->vjp(u0, nsteps, dt, ckpt_every, loss, loss_out, grad_u0_out);
+    c->have_state = true;
+    return (int)NS_OK;
+  });
 }
 
 int ns_profile(ns_ctx* c, int enable) {

@@ -30,7 +30,12 @@ enum PencilMode {
   MODE_PROJECT = 10  // state = N (input is a velocity: truncation + projection only)
 };
 
-enum XMode { XMODE_NONLINEAR = 0, XMODE_C2R = 1, XMODE_R2C = 2 };
+// XMODE_ADJ_WR / XMODE_ADJ_RU: adjoint slab passes, u x omega replaced by omega x r and
+// r x u (r: the mixed fields of the cotangent, in SlabArgs::mixedB)
+enum XMode { XMODE_NONLINEAR = 0, XMODE_C2R = 1, XMODE_R2C = 2, XMODE_ADJ_WR = 3, XMODE_ADJ_RU = 4 };
+__host__ __device__ __forceinline__ bool xmode_cross(int m) {
+  return m == XMODE_NONLINEAR || m == XMODE_ADJ_WR || m == XMODE_ADJ_RU;
+}
 
 enum ErrBits { ERR_FFT_SHAPE = 1, ERR_LAUNCH_SHAPE = 2 };
 
@@ -293,6 +298,7 @@ struct SlabArgs {
   FFTPlan py, px;
   const cpx<T>* tw;
   const cpx<T>* mixed;  // [5][N][N][M]
+  const cpx<T>* mixedB; // [5][N][N][M] cotangent fields r (adjoint modes; first 3 used)
   cpx<T>* scr;          // [6][G][N][M]
   cpx<T>* Ft;           // [3][N][N][M]
   T* rio;               // physical rows [3][N][N][N] (C2R output / R2C input)
@@ -310,20 +316,31 @@ __global__ void __launch_bounds__(512) k_yinv(SlabArgs<T> a) {
   const int x0 = blockIdx.x * TY, zg = blockIdx.y, z = a.z0 + zg;
   const int tile = N * TY;
   const size_t fstride = (size_t)N * N * M;
-  const int nf = a.xmode == XMODE_NONLINEAR ? 6 : 3;
+  const int nf = xmode_cross(a.xmode) ? 6 : 3;
   for (int e = threadIdx.x; e < tile; e += blockDim.x) {
     const int iy = e / TY, x = e - iy * TY;
     const size_t g = ((size_t)z * N + iy) * M + x0 + x;
     cpx<T> ux = a.mixed[g], uy = a.mixed[g + fstride], uz = a.mixed[g + 2 * fstride];
-    buf[e] = ux;
-    buf[tile + e] = uy;
-    buf[2 * tile + e] = uz;
-    if (nf == 6) {
+    // slots 0..2 and 3..5 of the pair whose cross product the x rows form
+    int su = 0, sw = 3, sr = -1;
+    if (a.xmode == XMODE_ADJ_WR) { sw = 0; sr = 3; su = -1; }
+    if (a.xmode == XMODE_ADJ_RU) { sr = 0; su = 3; sw = -1; }
+    if (su >= 0) {
+      buf[su * tile + e] = ux;
+      buf[(su + 1) * tile + e] = uy;
+      buf[(su + 2) * tile + e] = uz;
+    }
+    if (nf == 6 && sw >= 0) {
       cpx<T> dzx = a.mixed[g + 3 * fstride], dzy = a.mixed[g + 4 * fstride];
       const T kx = (T)(x0 + x), ky = (T)kof(iy, N);
-      buf[3 * tile + e] = mul_si(uz, ky) - dzy;            // w_x = i ky uz - dz uy
-      buf[4 * tile + e] = dzx - mul_si(uz, kx);            // w_y = dz ux - i kx uz
-      buf[5 * tile + e] = mul_si(uy, kx) - mul_si(ux, ky); // w_z = i kx uy - i ky ux
+      buf[sw * tile + e] = mul_si(uz, ky) - dzy;                  // w_x = i ky uz - dz uy
+      buf[(sw + 1) * tile + e] = dzx - mul_si(uz, kx);            // w_y = dz ux - i kx uz
+      buf[(sw + 2) * tile + e] = mul_si(uy, kx) - mul_si(ux, ky); // w_z = i kx uy - i ky ux
+    }
+    if (sr >= 0) {
+      buf[sr * tile + e] = a.mixedB[g];
+      buf[(sr + 1) * tile + e] = a.mixedB[g + fstride];
+      buf[(sr + 2) * tile + e] = a.mixedB[g + 2 * fstride];
     }
   }
   __syncthreads();
@@ -428,7 +445,7 @@ __global__ void __launch_bounds__(512) k_xrow(SlabArgs<T> a) {
   if (nr <= 0) return;
   const int tile = RX * M;
   const size_t sstride = (size_t)a.G * N * M;
-  const int nin = a.xmode == XMODE_NONLINEAR ? 6 : 3;
+  const int nin = xmode_cross(a.xmode) ? 6 : 3;
   const size_t plane = (size_t)N * N;
 
   // load
@@ -473,8 +490,8 @@ __global__ void __launch_bounds__(512) k_xrow(SlabArgs<T> a) {
     return;
   }
 
-  if (a.xmode == XMODE_NONLINEAR) {
-    // u x omega on the packed real rows, written over fields 0..2
+  if (xmode_cross(a.xmode)) {
+    // (fields 0..2) x (fields 3..5) on the packed real rows, written over fields 0..2
     T* re = reinterpret_cast<T*>(buf);
     const int rt = 2 * tile;  // reals per field
     for (int e = threadIdx.x; e < 2 * nr * M; e += blockDim.x) {
@@ -659,6 +676,127 @@ static __global__ void k_spectrum_final(const double* partial, int nblk, int nbi
   double s = 0;
   for (int b = 0; b < nblk; ++b) s += partial[(size_t)b * nbins + bin];
   out[bin] = s;
+}
+
+// ----------------------------------------------------------------------------------------
+// Adjoint step building blocks (pointwise on [3][N][N][M] spectral arrays)
+// ----------------------------------------------------------------------------------------
+enum EwOp {
+  EW_ROG_S1 = 0,   // o = E_dt (x + dt y)                         (S1 = E(S0 + dt N0))
+  EW_ROG_SN = 1,   // o = E_dt x + dt/2 E_{dt/2} (y + z)          (S = E S0 + dt/2 Eh (N0 + N1))
+  EW_RHO = 2,      // o = dt/2 E_{dt/2} x
+  EW_SIGMA = 3,    // o = dt E_dt x
+  EW_LAMBDA = 4,   // o = E_dt (x + y) + z
+  EW_ADD = 5,      // o = x + y
+  EW_LOSS = 6,     // o = 2 nu k^2 x        (gradient of eps = nu <S, k^2 S>_w)
+  EW_SCALE = 7,    // o = c x
+  EW_CURL_ADD = 8  // o = x + i k x y
+};
+
+template <typename T>
+__global__ void k_elementwise(int op, int N, T dt, T c, const T* __restrict__ ifac,
+                              const cpx<T>* x, const cpx<T>* y, const cpx<T>* z, cpx<T>* o) {
+  const int M = N / 2;
+  const size_t nmode = (size_t)N * N * M;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < nmode;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const int kx = (int)(i % M);
+    const size_t r = i / M;
+    const int iy = (int)(r % N), iz = (int)(r / N);
+    const T E1 = ifac[kx] * ifac[iy] * ifac[iz];
+    const T Eh = ifac[N + kx] * ifac[N + iy] * ifac[N + iz];
+    const T fx = (T)kx, fy = (T)kof(iy, N), fz = (T)kof(iz, N);
+    if (op == EW_CURL_ADD) {
+      const cpx<T> y0 = y[i], y1 = y[i + nmode], y2 = y[i + 2 * nmode];
+      o[i] = x[i] + mul_si(fy * y2 - fz * y1, T(1));
+      o[i + nmode] = x[i + nmode] + mul_si(fz * y0 - fx * y2, T(1));
+      o[i + 2 * nmode] = x[i + 2 * nmode] + mul_si(fx * y1 - fy * y0, T(1));
+      continue;
+    }
+    for (int q = 0; q < 3; ++q) {
+      const size_t j = i + q * nmode;
+      cpx<T> v;
+      switch (op) {
+        case EW_ROG_S1: v = E1 * (x[j] + dt * y[j]); break;
+        case EW_ROG_SN: v = E1 * x[j] + (T(0.5) * dt * Eh) * (y[j] + z[j]); break;
+        case EW_RHO: v = (T(0.5) * dt * Eh) * x[j]; break;
+        case EW_SIGMA: v = (dt * E1) * x[j]; break;
+        case EW_LAMBDA: v = E1 * (x[j] + y[j]) + z[j]; break;
+        case EW_ADD: v = x[j] + y[j]; break;
+        case EW_LOSS: v = (T(2) * c * (fx * fx + fy * fy + fz * fz)) * x[j]; break;
+        default: v = c * x[j]; break;
+      }
+      o[j] = v;
+    }
+  }
+}
+
+// dense forcing table [3][D] <-> spectral array at the table's modes
+template <typename T>
+__global__ void k_shell_gather(const cpx<T>* __restrict__ S, int N, int fK, cpx<T>* shell) {
+  const int D1 = 2 * fK + 1, D = D1 * D1 * (fK + 1), M = N / 2;
+  const size_t nmode = (size_t)N * N * M;
+  for (int i = threadIdx.x; i < D; i += blockDim.x) {
+    const int kx = i % (fK + 1), ky = (i / (fK + 1)) % D1 - fK, kz = i / ((fK + 1) * D1) - fK;
+    const size_t g = ((size_t)((kz + N) % N) * N + (size_t)((ky + N) % N)) * M + kx;
+    for (int c = 0; c < 3; ++c) shell[c * D + i] = S[g + c * nmode];
+  }
+}
+template <typename T>
+__global__ void k_shell_add(cpx<T>* S, int N, int fK, const cpx<T>* __restrict__ tab) {
+  const int D1 = 2 * fK + 1, D = D1 * D1 * (fK + 1), M = N / 2;
+  const size_t nmode = (size_t)N * N * M;
+  for (int i = threadIdx.x; i < D; i += blockDim.x) {
+    const int kx = i % (fK + 1), ky = (i / (fK + 1)) % D1 - fK, kz = i / ((fK + 1) * D1) - fK;
+    const size_t g = ((size_t)((kz + N) % N) * N + (size_t)((ky + N) % N)) * M + kx;
+    for (int c = 0; c < 3; ++c) S[g + c * nmode] = S[g + c * nmode] + tab[c * D + i];
+  }
+}
+
+// adjoint of S -> a(S) f at one stage applied to rho: table = (da/db) Re<f, rho>_w f with
+// da/db = -|a| / sqrt(b^2 + 4 c eps), b = Re<S, f>_w, c = dt/2 <f, f>_w
+template <typename T>
+__global__ void k_force_vjp(const cpx<double>* __restrict__ pj, const cpx<double>* __restrict__ pj1,
+                            double theta, const cpx<T>* __restrict__ shS,
+                            const cpx<T>* __restrict__ shR, int fK, double dt, double eps,
+                            cpx<T>* tab) {
+  __shared__ double sb[256], sc[256], sr[256];
+  const int D1 = 2 * fK + 1, D = D1 * D1 * (fK + 1);
+  double b = 0, c = 0, r = 0;
+  for (int i = threadIdx.x; i < D; i += blockDim.x) {
+    const double w = (i % (fK + 1)) == 0 ? 1.0 : 2.0;
+    for (int q = 0; q < 3; ++q) {
+      const cpx<double> p0 = pj[q * D + i], p1 = pj1[q * D + i];
+      const double fx = (1.0 - theta) * p0.x + theta * p1.x, fy = (1.0 - theta) * p0.y + theta * p1.y;
+      const cpx<T> s = shS[q * D + i], x = shR[q * D + i];
+      b += w * ((double)s.x * fx + (double)s.y * fy);
+      c += w * (fx * fx + fy * fy);
+      r += w * ((double)x.x * fx + (double)x.y * fy);
+    }
+  }
+  sb[threadIdx.x] = b;
+  sc[threadIdx.x] = c;
+  sr[threadIdx.x] = r;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) {
+      sb[threadIdx.x] += sb[threadIdx.x + s];
+      sc[threadIdx.x] += sc[threadIdx.x + s];
+      sr[threadIdx.x] += sr[threadIdx.x + s];
+    }
+    __syncthreads();
+  }
+  const double B = sb[0], C = 0.5 * dt * sc[0], R = sr[0];
+  const double q = sqrt(B * B + 4.0 * C * eps);
+  const double amp = (B >= 0.0) ? 2.0 * eps / (B + q) : 2.0 * eps / (B - q);
+  const double coef = -fabs(amp) / q * R;
+  for (int i = threadIdx.x; i < D; i += blockDim.x) {
+    for (int k = 0; k < 3; ++k) {
+      const cpx<double> p0 = pj[k * D + i], p1 = pj1[k * D + i];
+      const double fx = (1.0 - theta) * p0.x + theta * p1.x, fy = (1.0 - theta) * p0.y + theta * p1.y;
+      tab[k * D + i] = mk<T>((T)(coef * fx), (T)(coef * fy));
+    }
+  }
 }
 
 // convert between the working precision and FP64 (state transfers)
