@@ -1,0 +1,142 @@
+"""The paper-derived workloads at their full sizes, on the GPU.
+
+Taylor-Green 32^3 PS exact FP64 (200 steps); Taylor-Green Re=1600 at 256^3 (Rogallo, FP32
+and FP64) against RK4 + 2/3 at 384^3 to t = 9 with the spectral error index of Appendix A;
+forced HIT at 512^3 (split) and 768^3 (RK4); the adjoint at 64^3 over 50 forced steps.
+Where the FP64 oracle cannot run the whole workload in seconds, the check uses properties
+that hold at any size or runs the oracle on the part it can afford.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import adjoint as ad
+from oracle import diagnostics as dg
+from oracle import forcing as fo
+from oracle import schemes as sc
+from oracle import spectral as osp
+from paper_2603_08892_gb300 import analysis, inputs
+
+pytestmark = pytest.mark.gpu
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def test_config1_taylor_green_32_ps_exact_fp64_200_steps(ns):
+    N, nu, dt = 32, 1.0 / 1600, 0.005
+    kmax = 2 * math.sqrt(2) / 3 * N / 2
+    u = inputs.taylor_green(N)
+    prob = sc.Problem(N, nu, kmax)
+    S = osp.set_velocity(u, kmax)
+    Eg, Dg, Er, Dr = [], [], [], []
+    with ns.Solver(N, nu, kmax, scheme=ns.RK2_PS_EXACT, precision=ns.FP64) as s:
+        s.set_velocity(u)
+        for n in range(200):
+            s.step(dt, 1)
+            e, d = s.energy()
+            Eg.append(e)
+            Dg.append(d)
+            S = sc.step_ps_exact(S, dt, prob)
+            Er.append(dg.energy(S))
+            Dr.append(dg.dissipation(S, nu))
+        got = s.get_state()
+    assert rel(got, S) < 1e-11
+    np.testing.assert_allclose(Eg, Er, rtol=1e-12)
+    np.testing.assert_allclose(Dg, Dr, rtol=1e-11)
+    # early-time closed form: E = 1/8 - (3 nu/4) t + O(t^2)
+    assert abs(Eg[0] - (0.125 - 0.75 * nu * dt)) < 1e-7
+
+
+def _run_to_t9(ns, N, scheme, prec, kmax):
+    dt = 9.0 / math.ceil(9.0 / (0.5 * (2 * math.pi / N) / 2.0))
+    with ns.Solver(N, 1.0 / 1600, kmax, scheme=scheme, precision=prec, seed=12345) as s:
+        s.set_velocity(inputs.taylor_green(N))
+        s.step(dt, int(round(9.0 / dt)))
+        t, _ = s.time()
+        E, eps = s.energy()
+        spec = [s.spectrum(k, 130) for k in (1, 2, 3)]
+    return t, E, eps, spec
+
+
+def test_config2_taylor_green_t9_accuracy(ns):
+    t32, E32, d32, sp32 = _run_to_t9(ns, 256, ns.RK2_PS_RANDOM, ns.FP32, 128.0)
+    t64, E64, d64, sp64 = _run_to_t9(ns, 256, ns.RK2_PS_RANDOM, ns.FP64, 128.0)
+    tr, Er, dr, spr = _run_to_t9(ns, 384, ns.RK4, ns.FP32, 128.0)
+    assert abs(t32 - 9.0) < 1e-9 and abs(tr - 9.0) < 1e-9
+    # precision policy: FP32 bulk vs FP64 of the same scheme and grid
+    assert abs(E32 - E64) < 1e-4 * E64
+    assert analysis.error_index([sp32], [sp64], 128.0) < 0.05
+    # the Taylor-Green Re = 1600 dissipation peak is near t = 9 (about 0.0125)
+    assert 0.011 < d64 < 0.0135
+    # phase-shift RK2 at 256^3 against RK4 + 2/3 at 384^3 (same kmax): small spectral error
+    err = analysis.error_index([sp32], [spr], 128.0)
+    assert err < 3.0
+    print("config2: E(9) PS %.6f RK4 %.6f, error index PS vs RK4 %.3f %%" % (E32, Er, err))
+
+
+def test_config3_forced_hit_512_split_and_768_rk4(ns):
+    kmax = 256.0
+    nu = kmax ** (-4.0 / 3.0)
+    # 512^3 RK2 phase-shift random split with the constant-rate forcing on a HIT field
+    N = 512
+    u = inputs.hit_initial(N, 2026)
+    umax = np.abs(u).reshape(3, -1).max(axis=1)
+    dt = 0.4 / float(np.sum(umax / (2 * math.pi / N)))
+    with ns.Solver(N, nu, kmax, scheme=ns.RK2_PS_RANDOM, precision=ns.FP32, seed=2026) as s:
+        s.set_velocity(u)
+        s.set_forcing(2.0, 3.0, 1.0, 0.5, seed=2026)
+        E0, d0 = s.energy()
+        s.step(dt, 3)
+        E1, d1 = s.energy()
+        S = s.get_state()
+    assert abs(E0 - 1.5) < 0.05 * 1.5
+    # energy budget: dE/dt = eps_inj - eps with eps_inj = 1 (constant-rate forcing)
+    assert abs((E1 - E0) / (3 * dt) - (1.0 - 0.5 * (d0 + d1))) < 0.05
+    assert osp.divergence_ratio(S) < 1e-5
+    assert np.abs(S[:, ~osp.truncation_mask(N, kmax)]).max() == 0.0
+    del S, u
+    # 768^3 RK4 + 2/3 (the comparison leg), unforced Taylor-Green: dE/dt = -eps (the
+    # truncated nonlinear term conserves energy; RK4 in time).  With forcing on a field that
+    # has no energy in the forcing shell, the constant-rate reading (exact for one Euler
+    # step) injects less than eps in later RK4 stages, so the budget is checked unforced.
+    N = 768
+    u = inputs.taylor_green(N)
+    dt = 0.4 / (2.0 / (2 * math.pi / N))
+    with ns.Solver(N, nu, kmax, scheme=ns.RK4, precision=ns.FP32) as s:
+        s.set_velocity(u)
+        E0, d0 = s.energy()
+        s.step(dt, 3)
+        E1, d1 = s.energy()
+    assert abs(E0 - 0.125) < 1e-6
+    assert abs((E1 - E0) / (3 * dt) + 0.5 * (d0 + d1)) < 0.02 * d0
+
+
+def test_config5_adjoint_64_forced_50_steps(ns):
+    N, nsteps, ckpt = 64, 50, 10
+    kmax = N / 2
+    nu = kmax ** (-4.0 / 3.0)
+    u0 = inputs.hit_initial(N, 7)
+    umax = np.abs(u0).reshape(3, -1).max(axis=1)
+    dt = 0.4 / float(np.sum(umax / (2 * math.pi / N)))
+    with ns.Solver(N, nu, kmax, scheme=ns.RK2_PS_RANDOM, precision=ns.FP32, seed=7) as s:
+        s.set_forcing(2.0, 3.0, 1.0, 0.5, seed=7)
+        L32, g32 = s.vjp(u0, nsteps, dt, ckpt_every=ckpt)
+    with ns.Solver(N, nu, kmax, scheme=ns.RK2_PS_RANDOM, precision=ns.FP64, seed=7) as s:
+        s.set_forcing(2.0, 3.0, 1.0, 0.5, seed=7)
+        L64, g64 = s.vjp(u0, nsteps, dt, ckpt_every=ckpt)
+        rs = np.random.default_rng(5)
+        h = 1e-4
+        for _ in range(3):  # central differences in FP64, h = 1e-4
+            v = rs.standard_normal(u0.shape)
+            Lp, _ = s.vjp(u0 + h * v, nsteps, dt, ckpt_every=ckpt)
+            Lm, _ = s.vjp(u0 - h * v, nsteps, dt, ckpt_every=ckpt)
+            fd = (Lp - Lm) / (2 * h)
+            assert abs(fd - float(np.sum(g64 * v))) < 1e-6 * abs(fd)
+    prob = sc.Problem(N, nu, kmax)
+    f = fo.Forcing(N, 2.0, 3.0, 1.0, 0.5, seed=7)
+    Lr, gr = ad.grad_final_dissipation(u0, nsteps, dt, prob, seed=7, forcing=f, ckpt_every=ckpt)
+    assert abs(L64 - Lr) < 1e-11 * Lr and rel(g64, gr) < 1e-9
+    assert abs(L32 - Lr) < 1e-4 * Lr and rel(g32, gr) < 5e-3

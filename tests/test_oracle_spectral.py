@@ -138,3 +138,12 @@ def test_error_index_special_cases():
     one = [tuple(np.where(np.arange(10) == 1, 1.2, 1.0) * a for a in r) for r in ref]
     H8 = sum(1.0 / k for k in range(1, 9))
     assert abs(dg.error_index(one, ref, 9.0) - 20.0 / H8) < 1e-12
+
+
+def test_package_error_index_agrees_with_oracle():
+    from paper_2603_08892_gb300 import analysis
+
+    rs = np.random.default_rng(4)
+    a = [tuple(rs.random(20) + 0.5 for _ in range(3)) for _ in range(4)]
+    b = [tuple(rs.random(20) + 0.5 for _ in range(3)) for _ in range(4)]
+    assert abs(analysis.error_index(a, b, 15.5) - dg.error_index(a, b, 15.5)) < 1e-12
