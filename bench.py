@@ -283,11 +283,14 @@ def main():
     avg_ms = prof[dom][0] / max(1, prof[dom][1])
     achieved = kinds[dom] / (avg_ms / 1000.0) / 1e9
     shares = {k: round(tot[k] / max(1e-9, sum(tot.values())), 4) for k in tot}
+    kernel_ms = {k: round(tot[k] / K, 4) for k in tot}  # event time per step, each kind
     launches = sum(prof[k][2] for k in ("k_pencil", "k_yinv", "k_xrow", "k_yfwd")) + nchunks
     roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
             "frac": achieved / hbm, "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)",
             "algorithmic_bytes_per_launch": kinds[dom], "avg_launch_ms": avg_ms,
             "traffic": ncu_traffic(dom), "kernel_time_shares": shares,
+            "kernel_ms_per_step": kernel_ms,
+            "slab_pass_ms_per_step": round(prof["slab_pass"][0] / K, 4),
             "step_model_bytes": model_bytes,
             "step_frac": (model_bytes / (ms_step / 1000.0) / 1e9) / hbm}
 

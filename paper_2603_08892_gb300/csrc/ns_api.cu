@@ -422,7 +422,7 @@ struct Solver : SolverBase {
   void pencil(const PencilArgs<T>& a) {
     cudaEvent_t e = prof_begin(NS_PROF_PENCIL);
     if (use2)
-      k2.pencil<<<(M / k2.TX) * N, k2.NTP, a.nF > 1 ? k2.smP5 : k2.smP4, st>>>(a);
+      k2.pencil<<<(M / k2.TX) * N, k2.NTP, (a.nF > 1 || a.nOut > 1) ? k2.smP5 : k2.smP4, st>>>(a);
     else
       k_pencil<T><<<(M / TX) * N, bdP, smP, st>>>(a);
     prof_end(e);

@@ -78,8 +78,8 @@ struct BCfg {
   static constexpr size_t sm() {
     using C = K2Cfg<T, N>;
     const size_t cs = sizeof(cpx<T>);
-    const size_t p = 4 * (size_t)N * C::TX * cs, yi = 6 * (size_t)N * C::TYI * cs;
-    const size_t yf = (size_t)N * C::TY * cs, x = 3 * (size_t)C::XBUF * cs;
+    const size_t p = (3 * (size_t)N * C::TX + N) * cs, yi = (6 * (size_t)N * C::TYI + N) * cs;
+    const size_t yf = ((size_t)N * C::TY + N) * cs, x = (2 * (size_t)C::XBUF + N) * cs;
     const size_t a = p > yi ? p : yi, b = yf > x ? yf : x;
     return a > b ? a : b;
   }

@@ -110,7 +110,7 @@ __device__ __forceinline__ void cstage(const Src& src, const Dst& dst, const cpx
       const int base = (j % NS) * TSTEP;
 #pragma unroll
       for (int r = 1; r < R; ++r) {
-        cpx<T> w = ldg(&tw[r * base]);
+        cpx<T> w = tw[r * base];  // twiddle table (shared-memory copy)
         w.y *= -s;
         v[r] = v[r] * w;
       }
@@ -159,7 +159,8 @@ __device__ __forceinline__ void cstage(const Src& src, const Dst& dst, const cpx
   }
 }
 
-template <typename T, int n, int TWS, int NL, int NT, bool LF, int DIR, int S, int NS>
+template <typename T, int n, int TWS, int NL, int NT, bool LF, int DIR, int S, int NS,
+          bool HOLD0 = false>
 struct CStages {
   static constexpr CPlan P = cplan(n);
   template <class Src, class Dst>
@@ -172,9 +173,9 @@ struct CStages {
     if constexpr (first && last) {
       cstage<T, n, R, NS, TWS, NL, NT, LF, DIR, true>(src, dst, tw);
     } else if constexpr (first) {
-      cstage<T, n, R, NS, TWS, NL, NT, LF, DIR, false>(src, W, tw);
+      cstage<T, n, R, NS, TWS, NL, NT, LF, DIR, HOLD0>(src, W, tw);
       __syncthreads();
-      CStages<T, n, TWS, NL, NT, LF, DIR, (first ? S + 1 : S + 1), NS * R>::run(src, dst, work, tw);
+      CStages<T, n, TWS, NL, NT, LF, DIR, S + 1, NS * R>::run(src, dst, work, tw);
     } else if constexpr (last) {
       cstage<T, n, R, NS, TWS, NL, NT, LF, DIR, false>(W, dst, tw);
     } else {
@@ -192,6 +193,47 @@ template <typename T, int n, int TWS, int NL, int NT, bool LF, int DIR, class Sr
 __device__ __forceinline__ void cfft(const Src& src, const Dst& dst, cpx<T>* work,
                                      const cpx<T>* __restrict__ tw) {
   CStages<T, n, TWS, NL, NT, LF, DIR, 0, 1>::run(src, dst, work, tw);
+}
+
+// Same, for a source that reads the work tile itself: stage 0 reads every input before it
+// writes the work tile.
+template <typename T, int n, int TWS, int NL, int NT, bool LF, int DIR, class Src, class Dst>
+__device__ __forceinline__ void cfft_src_in_work(const Src& src, const Dst& dst, cpx<T>* work,
+                                                 const cpx<T>* __restrict__ tw) {
+  CStages<T, n, TWS, NL, NT, LF, DIR, 0, 1, true>::run(src, dst, work, tw);
+}
+
+// In place: stage 0 reads src (ALIAS: src is the tile itself) and writes the tile B; every
+// later stage runs in place on B with its inputs held in registers across a barrier.  The
+// result is left in B in natural order; no separate work tile is needed.
+template <typename T, int n, int TWS, int NL, int NT, bool LF, int DIR, bool ALIAS, int S, int NS>
+struct CStagesIP {
+  static constexpr CPlan P = cplan(n);
+  template <class Src>
+  static __device__ __forceinline__ void run(const Src& src, const WorkTile<T, n, NL, LF>& B,
+                                             const cpx<T>* __restrict__ tw) {
+    constexpr int R = P.r[S];
+    if constexpr (S == 0)
+      cstage<T, n, R, NS, TWS, NL, NT, LF, DIR, ALIAS>(src, B, tw);
+    else
+      cstage<T, n, R, NS, TWS, NL, NT, LF, DIR, true>(B, B, tw);
+    if constexpr (S + 1 < P.nst) {
+      __syncthreads();
+      CStagesIP<T, n, TWS, NL, NT, LF, DIR, ALIAS, S + 1, NS * R>::run(src, B, tw);
+    }
+  }
+};
+
+template <typename T, int n, int TWS, int NL, int NT, bool LF, int DIR, bool ALIAS, class Src>
+__device__ __forceinline__ void cfft_ip(const Src& src, cpx<T>* tile, const cpx<T>* __restrict__ tw) {
+  CStagesIP<T, n, TWS, NL, NT, LF, DIR, ALIAS, 0, 1>::run(src, WorkTile<T, n, NL, LF>{tile}, tw);
+}
+
+// copy of the twiddle table into shared memory (all threads of the block participate)
+template <typename T>
+__device__ __forceinline__ void load_twiddles(cpx<T>* dst, const cpx<T>* __restrict__ tw, int n) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = ldg(&tw[i]);
+  __syncthreads();
 }
 
 }  // namespace ns

@@ -22,6 +22,13 @@ __host__ __device__ constexpr int pick_div(int m, int target, int cap) {
   return 1;
 }
 __host__ __device__ constexpr int round_warps(int t) { return cmin(cmax((t + 31) / 32 * 32, 64), 512); }
+__host__ __device__ constexpr int cgcd(int a, int b) { return b == 0 ? a : cgcd(b, a % b); }
+// thread count: >= t, >= 64, a multiple of the warp size and of w (each thread keeps one line)
+__host__ __device__ constexpr int round_lines(int t, int w) {
+  const int l = 32 / cgcd(32, w) * w;
+  const int v = cmax(t, 64);
+  return (v + l - 1) / l * l;
+}
 
 // Global-memory access policy.  MemNC: data written by earlier launches (read-only path).
 // MemCG: data written by other blocks of the same launch (persistent kernel): loads and
@@ -60,7 +67,9 @@ struct K2Cfg {
   static constexpr int MINW = 32 / CS;  // 32-byte global segments
   // pencil: TX columns of N
   static constexpr int TX = pick_div(M, cmax(16384 / (N * CS), MINW), 16);
-  static constexpr int NTP = round_warps(TX * N / 16);
+  static constexpr int NTP = round_lines(TX * N / 16, TX);
+  // blocks per SM the register budget must allow (at least 128 registers per thread)
+  static constexpr int MINB_P = cmax(1, cmin(4, 65536 / (NTP * 128)));
   // y passes: TY columns of N
   static constexpr int TY = pick_div(M, cmax(32768 / (N * CS), MINW), 16);
   static constexpr int NTY = round_warps(TY * N / 16);
@@ -122,9 +131,8 @@ struct PencilOutSrc {
 // Returns S_next for every component and performs the mode's global writes.
 template <typename T, class MP>
 __device__ __forceinline__ void spectral_point(const PencilArgs<T>& a, int kx, int ky, int kz,
-                                               int iy, int iz, size_t g, size_t fstride,
-                                               cpx<T> nv[3], cpx<T> sn[3]) {
-  const int N = a.N;
+                                               size_t g, size_t fstride, cpx<T> nv[3],
+                                               cpx<T> sn[3], T E1, T Eh) {
   const int D1 = 2 * a.fK + 1;
   const int D = D1 * D1 * (a.fK + 1);
   if (a.nF > 0) {
@@ -154,11 +162,6 @@ __device__ __forceinline__ void spectral_point(const PencilArgs<T>& a, int kx, i
     }
   }
   const T dt = a.dt, hdt = T(0.5) * a.dt;
-  T E1 = 1, Eh = 1;
-  if (a.mode != MODE_INIT && a.mode != MODE_NL && a.mode != MODE_PROJECT) {
-    E1 = a.ifac[kx] * a.ifac[iy] * a.ifac[iz];
-    Eh = a.ifac[N + kx] * a.ifac[N + iy] * a.ifac[N + iz];
-  }
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     const size_t gi = g + c * fstride;
@@ -218,39 +221,51 @@ __device__ __forceinline__ void spectral_point(const PencilArgs<T>& a, int kx, i
 }
 
 // ---- pencil pass --------------------------------------------------------------------
-// One tile: TX consecutive kx at one ky, all kz.  smem: 4 tiles (5 with two inputs).
+// One tile: TX consecutive kx at one ky, all kz.  Shared memory: 3 component tiles (a 4th
+// when there are two inputs or two outputs) and the twiddle table.  Every thread works on
+// one fixed kx (NT is a multiple of TX), so the kx and ky factors of the phase and
+// integrating-factor tables are loaded once per thread.
+template <typename T, int N>
+__host__ __device__ constexpr int pencil_tiles(int nF, int nOut) { return (nF > 1 || nOut > 1) ? 4 : 3; }
+
 template <typename T, int N, class MP>
 __device__ __forceinline__ void pencil_tile(const PencilArgs<T>& a, int tile_id, cpx<T>* buf) {
   using C = K2Cfg<T, N>;
   constexpr int M = N / 2, TX = C::TX, NT = C::NTP, tile = N * TX;
+  static_assert(NT % TX == 0, "every thread keeps one kx");
   cpx<T>* bc[3] = {buf, buf + tile, buf + 2 * tile};
-  cpx<T>* W = buf + 3 * tile;
-  cpx<T>* b3 = buf + 4 * tile;
+  cpx<T>* b3 = buf + 3 * tile;
+  cpx<T>* tws = buf + pencil_tiles<T, N>(a.nF, a.nOut) * tile;
   constexpr int ntx = M / TX;
   const int iy = tile_id / ntx;
   const int x0 = (tile_id % ntx) * TX;
   const size_t fstride = (size_t)N * N * M;
   const int ky = kof(iy, N);
   const bool act = threadIdx.x < NT;
+  const int line = threadIdx.x % TX, kx = x0 + line;
+  load_twiddles(tws, a.tw, N);
 
   if (a.nF > 0) {
+    cpx<T> d0 = mk<T>(1, 0), d1 = mk<T>(1, 0);
+    if (a.dsh[0]) d0 = MP::ld(&a.dsh[0][kx]) * MP::ld(&a.dsh[0][N + iy]);
+    if (a.nF > 1 && a.dsh[1]) d1 = MP::ld(&a.dsh[1][kx]) * MP::ld(&a.dsh[1][N + iy]);
     for (int c = 0; c < 3; ++c) {
-      cfft<T, N, 1, TX, NT, true, -1>(ColIn<T, N, TX, MP>{a.F[0] + c * fstride, iy, x0},
-                                      SmTile<T, TX>{bc[c]}, W, a.tw);
+      cfft_ip<T, N, 1, TX, NT, true, -1, false>(ColIn<T, N, TX, MP>{a.F[0] + c * fstride, iy, x0},
+                                                bc[c], tws);
       __syncthreads();
       if (a.nF > 1) {
-        cfft<T, N, 1, TX, NT, true, -1>(ColIn<T, N, TX, MP>{a.F[1] + c * fstride, iy, x0},
-                                        SmTile<T, TX>{b3}, W, a.tw);
+        cfft_ip<T, N, 1, TX, NT, true, -1, false>(ColIn<T, N, TX, MP>{a.F[1] + c * fstride, iy, x0},
+                                                  b3, tws);
         __syncthreads();
       }
       for (int e = threadIdx.x; act && e < tile; e += NT) {
-        const int iz = e / TX, x = e % TX;
+        const int iz = e / TX;
         cpx<T> v = bc[c][e];
-        if (a.dsh[0]) v = mul_conj(v, phase3p<MP>(a.dsh[0], N, x0 + x, iy, iz));
+        if (a.dsh[0]) v = mul_conj(v, d0 * MP::ld(&a.dsh[0][2 * N + iz]));
         v = a.wF[0] * v;
         if (a.nF > 1) {
           cpx<T> w = b3[e];
-          if (a.dsh[1]) w = mul_conj(w, phase3p<MP>(a.dsh[1], N, x0 + x, iy, iz));
+          if (a.dsh[1]) w = mul_conj(w, d1 * MP::ld(&a.dsh[1][2 * N + iz]));
           v = v + a.wF[1] * w;
         }
         bc[c][e] = v;
@@ -259,9 +274,18 @@ __device__ __forceinline__ void pencil_tile(const PencilArgs<T>& a, int tile_id,
     }
   }
 
+  // stage; with a single shifted output the shift is applied here, once per mode
+  const bool pre = a.nOut == 1 && a.osh[0] != nullptr;
+  cpx<T> oxy = mk<T>(1, 0);
+  if (pre) oxy = MP::ld(&a.osh[0][kx]) * MP::ld(&a.osh[0][N + iy]);
+  const bool useE = a.mode != MODE_INIT && a.mode != MODE_NL && a.mode != MODE_PROJECT;
+  T e1xy = 1, ehxy = 1;
+  if (useE) {
+    e1xy = a.ifac[kx] * a.ifac[iy];
+    ehxy = a.ifac[N + kx] * a.ifac[N + iy];
+  }
   for (int e = threadIdx.x; act && e < tile; e += NT) {
-    const int iz = e / TX, x = e % TX;
-    const int kx = x0 + x, kz = kof(iz, N);
+    const int iz = e / TX, kz = kof(iz, N);
     const size_t g = ((size_t)iz * N + iy) * M + kx;
     cpx<T> nv[3], sn[3];
     if (a.nF > 0) {
@@ -269,25 +293,52 @@ __device__ __forceinline__ void pencil_tile(const PencilArgs<T>& a, int tile_id,
       nv[1] = bc[1][e];
       nv[2] = bc[2][e];
     }
-    spectral_point<T, MP>(a, kx, ky, kz, iy, iz, g, fstride, nv, sn);
+    T E1 = 1, Eh = 1;
+    if (useE) {
+      E1 = e1xy * a.ifac[iz];
+      Eh = ehxy * a.ifac[N + iz];
+    }
+    spectral_point<T, MP>(a, kx, ky, kz, g, fstride, nv, sn, E1, Eh);
+    if (pre) {
+      const cpx<T> ph = oxy * MP::ld(&a.osh[0][2 * N + iz]);
+      sn[0] = sn[0] * ph;
+      sn[1] = sn[1] * ph;
+      sn[2] = sn[2] * ph;
+    }
     bc[0][e] = sn[0];
     bc[1][e] = sn[1];
     bc[2][e] = sn[2];
   }
   __syncthreads();
 
-  for (int o = 0; o < a.nOut; ++o) {
-    for (int f = 0; f < 5; ++f) {
-      const int c = f < 3 ? f : f - 3;
-      cfft<T, N, 1, TX, NT, true, 1>(PencilOutSrc<T, N, TX, MP>{bc[c], a.osh[o], iy, x0, f >= 3},
-                                     ColOut<T, N, TX, MP>{a.out[o] + f * fstride, iy, x0}, W, a.tw);
+  if (a.nOut == 1) {
+    // u_z first (its tile then serves as the work tile), then u_x, d_z u_x, u_y, d_z u_y
+    const cpx<T>* sh = pre ? nullptr : a.osh[0];
+    cfft_src_in_work<T, N, 1, TX, NT, true, 1>(PencilOutSrc<T, N, TX, MP>{bc[2], sh, iy, x0, false},
+                                               ColOut<T, N, TX, MP>{a.out[0] + 2 * fstride, iy, x0},
+                                               bc[2], tws);
+    __syncthreads();
+    const int order[4] = {0, 3, 1, 4};
+    for (int i = 0; i < 4; ++i) {
+      const int f = order[i], c = f < 3 ? f : f - 3;
+      cfft<T, N, 1, TX, NT, true, 1>(PencilOutSrc<T, N, TX, MP>{bc[c], sh, iy, x0, f >= 3},
+                                     ColOut<T, N, TX, MP>{a.out[0] + f * fstride, iy, x0}, bc[2], tws);
       __syncthreads();
+    }
+  } else {
+    for (int o = 0; o < a.nOut; ++o) {
+      for (int f = 0; f < 5; ++f) {
+        const int c = f < 3 ? f : f - 3;
+        cfft<T, N, 1, TX, NT, true, 1>(PencilOutSrc<T, N, TX, MP>{bc[c], a.osh[o], iy, x0, f >= 3},
+                                       ColOut<T, N, TX, MP>{a.out[o] + f * fstride, iy, x0}, b3, tws);
+        __syncthreads();
+      }
     }
   }
 }
 
 template <typename T, int N>
-__global__ void __launch_bounds__(K2Cfg<T, N>::NTP) k2_pencil(PencilArgs<T> a) {
+__global__ void __launch_bounds__(K2Cfg<T, N>::NTP, K2Cfg<T, N>::MINB_P) k2_pencil(PencilArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   pencil_tile<T, N, MemNC>(a, blockIdx.x, reinterpret_cast<cpx<T>*>(smem_raw));
 }
@@ -325,10 +376,10 @@ struct ScrCol {  // one field [plane][y|ky][kx], column tile of a plane (scratch
 
 template <typename T, int N, int F, class MP>
 __device__ __forceinline__ void yinv_field(const SlabArgs<T>& a, const cpx<T>* in, cpx<T>* W,
-                                           int zg, int x0, size_t sstride) {
+                                           int zg, int x0, size_t sstride, const cpx<T>* tws) {
   using C = K2Cfg<T, N>;
   cfft<T, N, 1, C::TYI, C::NTYI, true, 1>(YInvSrc<T, N, F, C::TYI>{in, x0},
-                                          ScrCol<T, N, MP>{a.scr + F * sstride, zg, x0}, W, a.tw);
+                                          ScrCol<T, N, MP>{a.scr + F * sstride, zg, x0}, W, tws);
   __syncthreads();
 }
 
@@ -338,20 +389,22 @@ __device__ __forceinline__ void yinv_tile(const SlabArgs<T>& a, int tx, int zg, 
   using C = K2Cfg<T, N>;
   constexpr int M = N / 2, TY = C::TYI, NT = C::NTYI, tile = N * TY;
   cpx<T>* W = in + 5 * tile;
+  cpx<T>* tws = in + 6 * tile;
   const int x0 = tx * TY, z = a.z0 + zg;
   const size_t sstride = (size_t)a.G * N * M;
   const size_t fs = (size_t)N * N * M;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) tws[i] = ldg(&a.tw[i]);
   for (int i = threadIdx.x; threadIdx.x < NT && i < 5 * tile; i += NT) {
     const int f = i / tile, rem = i % tile, e = rem / TY, line = rem % TY;
     in[i] = MP::ld(&a.mixed[f * fs + ((size_t)z * N + e) * M + x0 + line]);
   }
   __syncthreads();
-  yinv_field<T, N, 0, MP>(a, in, W, zg, x0, sstride);
-  yinv_field<T, N, 1, MP>(a, in, W, zg, x0, sstride);
-  yinv_field<T, N, 2, MP>(a, in, W, zg, x0, sstride);
-  yinv_field<T, N, 3, MP>(a, in, W, zg, x0, sstride);
-  yinv_field<T, N, 4, MP>(a, in, W, zg, x0, sstride);
-  yinv_field<T, N, 5, MP>(a, in, W, zg, x0, sstride);
+  yinv_field<T, N, 0, MP>(a, in, W, zg, x0, sstride, tws);
+  yinv_field<T, N, 1, MP>(a, in, W, zg, x0, sstride, tws);
+  yinv_field<T, N, 2, MP>(a, in, W, zg, x0, sstride, tws);
+  yinv_field<T, N, 3, MP>(a, in, W, zg, x0, sstride, tws);
+  yinv_field<T, N, 4, MP>(a, in, W, zg, x0, sstride, tws);
+  yinv_field<T, N, 5, MP>(a, in, W, zg, x0, sstride, tws);
 }
 
 template <typename T, int N>
@@ -366,9 +419,11 @@ __device__ __forceinline__ void yfwd_tile(const SlabArgs<T>& a, int tx, int zg, 
   const int x0 = tx * C::TY, z = a.z0 + zg;
   const size_t sstride = (size_t)a.G * N * (N / 2);
   const size_t fstride = (size_t)N * N * (N / 2);
+  cpx<T>* tws = W + N * C::TY;
+  load_twiddles(tws, a.tw, N);
   for (int f = 0; f < 3; ++f) {
     cfft<T, N, 1, C::TY, C::NTY, true, -1>(ScrCol<T, N, MP>{a.scr + f * sstride, zg, x0},
-                                           ScrCol<T, N, MP>{a.Ft + f * fstride, z, x0}, W, a.tw);
+                                           ScrCol<T, N, MP>{a.Ft + f * fstride, z, x0}, W, tws);
     __syncthreads();
   }
 }
@@ -387,8 +442,10 @@ __device__ __forceinline__ void xrow_tile(const SlabArgs<T>& a, int tile_id, cpx
   constexpr int M = N / 2, RX = C::RX, NT = C::NTX;
   using RowT = WorkTile<T, M, 3 * RX, false>;
   const RowT U{buf}, V{buf + C::XBUF};
-  cpx<T>* work = buf + 2 * C::XBUF;
+  cpx<T>* tws = buf + 2 * C::XBUF;
   const bool act = threadIdx.x < NT;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) tws[i] = ldg(&a.tw[i]);
+  __syncthreads();  // the pre-processing below reads twiddles written by other threads
   const int rows_total = a.G * N;
   const int r0 = tile_id * RX;
   const int nr = min(RX, rows_total - r0);
@@ -418,7 +475,7 @@ __device__ __forceinline__ void xrow_tile(const SlabArgs<T>& a, int tile_id, cpx
       }
     } else if (k < M - k) {
       const cpx<T> Xk = MP::ld(&src[k]), Xm = MP::ld(&src[M - k]);
-      const cpx<T> tk = ldg(&a.tw[k]);
+      const cpx<T> tk = tws[k];
       const cpx<T> A = Xk + conjg(Xm), Bv = Xk - conjg(Xm);
       B.put(line, k, A + mul_si(conjg(tk) * Bv, T(1)));
       const cpx<T> A2 = Xm + conjg(Xk), B2 = Xm - conjg(Xk);
@@ -426,9 +483,9 @@ __device__ __forceinline__ void xrow_tile(const SlabArgs<T>& a, int tile_id, cpx
     }
   }
   __syncthreads();
-  cfft<T, M, 2, 3 * RX, NT, false, 1>(U, U, work, a.tw);
+  cfft_ip<T, M, 2, 3 * RX, NT, false, 1, true>(U, U.p, tws);
   __syncthreads();
-  cfft<T, M, 2, 3 * RX, NT, false, 1>(V, V, work, a.tw);
+  cfft_ip<T, M, 2, 3 * RX, NT, false, 1, true>(V, V.p, tws);
   __syncthreads();
 
   // u x omega on the packed real rows, written over u
@@ -449,7 +506,7 @@ __device__ __forceinline__ void xrow_tile(const SlabArgs<T>& a, int tile_id, cpx
     U.put(2 * RX + row, k, f2);
   }
   __syncthreads();
-  cfft<T, M, 2, 3 * RX, NT, false, -1>(U, U, work, a.tw);
+  cfft_ip<T, M, 2, 3 * RX, NT, false, -1, true>(U, U.p, tws);
   __syncthreads();
 
   // r2c post-processing and store
@@ -467,7 +524,7 @@ __device__ __forceinline__ void xrow_tile(const SlabArgs<T>& a, int tile_id, cpx
       }
     } else if (k < M - k) {
       const cpx<T> Zk = U.get(line, k), Zm = U.get(line, M - k);
-      const cpx<T> Wk = ldg(&a.tw[k]);
+      const cpx<T> Wk = tws[k];
       const cpx<T> A = Zk + conjg(Zm), B = Zk - conjg(Zm);
       MP::st(&dst[k], T(0.5) * (A - mul_si(Wk * B, T(1))));
       const cpx<T> A2 = Zm + conjg(Zk), B2 = Zm - conjg(Zk);
@@ -505,11 +562,11 @@ K2Entry<T> make_k2_entry() {
   e.xrow = k2_xrow<T, N>;
   e.TX = C::TX; e.NTP = C::NTP; e.TY = C::TY; e.NTY = C::NTY; e.RX = C::RX; e.NTX = C::NTX;
   e.TYI = C::TYI; e.NTYI = C::NTYI;
-  e.smYI = 6 * (size_t)N * C::TYI * sizeof(cpx<T>);
-  e.smP4 = 4 * (size_t)N * C::TX * sizeof(cpx<T>);
-  e.smP5 = 5 * (size_t)N * C::TX * sizeof(cpx<T>);
-  e.smY = (size_t)N * C::TY * sizeof(cpx<T>);
-  e.smX = 3 * (size_t)C::XBUF * sizeof(cpx<T>);
+  e.smYI = (6 * (size_t)N * C::TYI + N) * sizeof(cpx<T>);
+  e.smP4 = (3 * (size_t)N * C::TX + N) * sizeof(cpx<T>);  // 3 tiles + twiddles
+  e.smP5 = (4 * (size_t)N * C::TX + N) * sizeof(cpx<T>);  // 4 tiles + twiddles
+  e.smY = ((size_t)N * C::TY + N) * sizeof(cpx<T>);
+  e.smX = (2 * (size_t)C::XBUF + N) * sizeof(cpx<T>);
   return e;
 }
 
