@@ -10,6 +10,7 @@
 // where X is the slab pass and P the pencil pass of one evaluation, and C = N^3 * sizeof(T)
 // is the size of one half-spectrum complex field.
 #include <cuda_runtime.h>
+#include <sys/stat.h>
 
 #include <cmath>
 #include <cstdio>
@@ -190,7 +191,8 @@ struct Solver : SolverBase {
   size_t smYi, smYf;
   int RX, bdX;
   size_t smX;
-  int G;
+  int G, Gmax;
+  bool tuned = false;
   int nsm = 148;
   K2Entry<T> k2;     // size-specialised kernels, if this N has them
   bool use2 = false;
@@ -284,6 +286,10 @@ struct Solver : SolverBase {
     G = (int)((48ull << 20) / plane6);
     if (G < 1) G = 1;
     if (G > N) G = N;
+    // the scratch holds up to Gmax planes: the autotuner may pick any group size up to it
+    Gmax = (int)((96ull << 20) / plane6);
+    if (Gmax < G) Gmax = G;
+    if (Gmax > N) Gmax = N;
 
     // The attribute belongs to the kernel, not to this context: allow the device maximum so
     // that contexts of different sizes in one process never lower each other's limit.
@@ -315,7 +321,7 @@ struct Solver : SolverBase {
       CUDA_TRY(cudaMalloc(&mixed[1], 5 * F1 * cs));
       CUDA_TRY(cudaMalloc(&Ft[1], 3 * F1 * cs));
     }
-    CUDA_TRY(cudaMalloc(&scr, 6 * (size_t)G * N * M * cs));
+    CUDA_TRY(cudaMalloc(&scr, 6 * (size_t)Gmax * N * M * cs));
     CUDA_TRY(cudaMalloc(&tw, N * cs));
     CUDA_TRY(cudaMalloc(&ifac, 2 * N * sizeof(T)));
     red_blocks = 2 * nsm;
@@ -347,7 +353,7 @@ struct Solver : SolverBase {
   void buffers(double dt, NsCtxBuffers* b) override {
     if (dt > 0) set_dt(dt);
     b->N = N; b->precision = c->p.precision; b->scheme = c->p.scheme; b->truncation = c->p.truncation;
-    b->K2max = c->K2max; b->Kimax = c->Kimax; b->G = G; b->nu = c->p.nu; b->kmax = c->p.kmax;
+    b->K2max = c->K2max; b->Kimax = c->Kimax; b->G = Gmax; b->nu = c->p.nu; b->kmax = c->p.kmax;
     b->state = state; b->mixed = mixed[0]; b->Ft = Ft[0]; b->scr = scr; b->tw = tw; b->ifac = ifac;
     b->err = d_err; b->seed = c->p.seed; b->step = c->step; b->t = c->t;
   }
@@ -558,8 +564,132 @@ struct Solver : SolverBase {
     CUDA_TRY(cudaMemsetAsync(shell, 0, 3 * (size_t)fDn() * sizeof(cpx<T>), st));
   }
 
+  // ---- autotuner of the plane-group size of the slab pass ------------------------------
+  // Candidates G (planes per group of the L2-resident scratch) are timed on the slab pass
+  // with CUDA events; the fastest is kept and cached in a JSON file keyed by device, N and
+  // precision.  Results do not depend on G (every plane is transformed the same way).
+  // NS_AUTOTUNE=0 disables it; NS_AUTOTUNE_CACHE sets the cache file; NS_SLAB_PLANES=g
+  // forces a group size.
+  static std::string cache_path() {
+    const char* e = std::getenv("NS_AUTOTUNE_CACHE");
+    if (e && *e) return e;
+    const char* h = std::getenv("HOME");
+    return std::string(h && *h ? h : "/tmp") + "/.cache/libns_autotune.json";
+  }
+  std::string tune_key() {
+    cudaDeviceProp pr;
+    cudaGetDeviceProperties(&pr, c->p.device);
+    std::string k = std::string(pr.name) + "|N=" + std::to_string(N) + "|" +
+                    (sizeof(T) == 4 ? "fp32" : "fp64") + (use2 ? "|k2" : "|generic");
+    for (auto& ch : k)
+      if (ch == '"' || ch == '\\') ch = '_';
+    return k;
+  }
+  static bool cache_lookup(const std::string& path, const std::string& key, int* val) {
+    FILE* f = std::fopen(path.c_str(), "r");
+    if (!f) return false;
+    std::string txt;
+    char buf[4096];
+    size_t n;
+    while ((n = std::fread(buf, 1, sizeof(buf), f)) > 0) txt.append(buf, n);
+    std::fclose(f);
+    const std::string pat = "\"" + key + "\":";
+    const size_t pos = txt.find(pat);
+    if (pos == std::string::npos) return false;
+    *val = std::atoi(txt.c_str() + pos + pat.size());
+    return *val > 0;
+  }
+  static void cache_store(const std::string& path, const std::string& key, int val) {
+    // read-modify-write of a flat JSON object {"key": value, ...}
+    std::string txt;
+    if (FILE* f = std::fopen(path.c_str(), "r")) {
+      char buf[4096];
+      size_t n;
+      while ((n = std::fread(buf, 1, sizeof(buf), f)) > 0) txt.append(buf, n);
+      std::fclose(f);
+    }
+    std::string body;
+    const size_t a = txt.find('{'), b = txt.rfind('}');
+    if (a != std::string::npos && b != std::string::npos && b > a) body = txt.substr(a + 1, b - a - 1);
+    const std::string pat = "\"" + key + "\":";
+    const size_t pos = body.find(pat);
+    if (pos != std::string::npos) {
+      size_t e = body.find_first_of(",}", pos);
+      body.erase(pos, (e == std::string::npos ? body.size() : e) - pos);
+      while (!body.empty() && (body.back() == ',' || body.back() == ' ' || body.back() == '\n')) body.pop_back();
+      if (!body.empty() && body[0] == ',') body.erase(0, 1);
+    }
+    while (!body.empty() && (body.back() == ' ' || body.back() == '\n')) body.pop_back();
+    if (!body.empty()) body += ",\n ";
+    body += pat + " " + std::to_string(val);
+    const size_t slash = path.rfind('/');
+    if (slash != std::string::npos && slash > 0) mkdir_p(path.substr(0, slash));
+    if (FILE* f = std::fopen(path.c_str(), "w")) {
+      std::fprintf(f, "{%s}\n", body.c_str());
+      std::fclose(f);
+    }
+  }
+  static void mkdir_p(const std::string& d) {
+    std::string cur;
+    for (size_t i = 0; i < d.size(); ++i) {
+      cur += d[i];
+      if (d[i] == '/' && cur.size() > 1) ::mkdir(cur.c_str(), 0755);
+    }
+    ::mkdir(d.c_str(), 0755);
+  }
+
+  void autotune() {
+    tuned = true;
+    if (const char* fg = std::getenv("NS_SLAB_PLANES")) {  // forced group size
+      const int g = std::atoi(fg);
+      if (g >= 1) G = g < Gmax ? g : Gmax;
+      return;
+    }
+    const char* en = std::getenv("NS_AUTOTUNE");
+    if (en && std::string(en) == "0") return;
+    if (Gmax <= 1 || N < 128) return;  // small grids: one group holds every plane
+    const std::string path = cache_path(), key = tune_key();
+    int g = 0;
+    if (cache_lookup(path, key, &g) && g >= 1 && g <= Gmax) {
+      G = g;
+      return;
+    }
+    std::vector<int> cand;
+    for (int q : {8, 12, 16, 19, 24, 28, 32, 38, 43, 48, 57, 64, 76, 96, 128})
+      if (q <= Gmax) cand.push_back(q);
+    if (cand.empty()) return;
+    CUDA_TRY(cudaMemsetAsync(mixed[0], 0, 5 * F1 * sizeof(cpx<T>), st));
+    cudaEvent_t e0, e1;
+    CUDA_TRY(cudaEventCreate(&e0));
+    CUDA_TRY(cudaEventCreate(&e1));
+    const bool pon = prof.on;
+    prof.on = false;
+    float best = 1e30f;
+    int bestG = G;
+    for (int q : cand) {
+      G = q;
+      slab(mixed[0], Ft[0]);  // warm-up
+      CUDA_TRY(cudaEventRecord(e0, st));
+      for (int r = 0; r < 3; ++r) slab(mixed[0], Ft[0]);
+      CUDA_TRY(cudaEventRecord(e1, st));
+      CUDA_TRY(cudaEventSynchronize(e1));
+      float ms = 0;
+      CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+      if (ms < best) {
+        best = ms;
+        bestG = q;
+      }
+    }
+    prof.on = pon;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    G = bestG;
+    cache_store(path, key, G);
+  }
+
   // ---- schemes ------------------------------------------------------------------------
   void step(double dt, int nsteps) override {
+    if (!tuned) autotune();
     set_dt(dt);
     const int sch = c->p.scheme;
     const double dx = 2.0 * M_PI / N;

@@ -60,6 +60,31 @@ struct MemCG {
   }
 };
 
+// Asynchronous 16-byte global -> shared copies (cp.async.cg: through L2 only, so data written
+// by other blocks of a persistent launch is never read from a stale L1 line).
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\ncp.async.wait_all;\n" ::: "memory");
+}
+// Stage a column tile [e][line] (W lines, n elements) of a [z|kz][ky][kx] field from global
+// memory; W * sizeof(cpx<T>) is a multiple of 16 bytes and x0 a multiple of W.
+// PLANE: the tile of a fixed plane p of a [p][e][kx] field (element e = ky or y) instead.
+template <typename T, int N, int W, int NT, bool PLANE = false>
+__device__ __forceinline__ void stage_col_tile(cpx<T>* dst, const cpx<T>* src, int iy, int x0) {
+  constexpr int PER = 16 / (int)sizeof(cpx<T>);  // complex values per 16-byte chunk
+  constexpr int CH = W / PER;                     // chunks per row
+  static_assert(W % PER == 0, "tile rows must be whole 16-byte chunks");
+  if (threadIdx.x >= NT) return;
+  for (int i = threadIdx.x; i < N * CH; i += NT) {
+    const int e = i / CH, xc = (i % CH) * PER;
+    const size_t row = PLANE ? (size_t)iy * N + e : (size_t)e * N + iy;
+    cp_async16(&dst[e * W + xc], &src[row * (N / 2) + x0 + xc]);
+  }
+}
+
 template <typename T, int N>
 struct K2Cfg {
   static constexpr int M = N / 2;
@@ -71,7 +96,7 @@ struct K2Cfg {
   // blocks per SM the register budget must allow (at least 128 registers per thread)
   static constexpr int MINB_P = cmax(1, cmin(4, 65536 / (NTP * 128)));
   // y passes: TY columns of N
-  static constexpr int TY = pick_div(M, cmax(32768 / (N * CS), MINW), 16);
+  static constexpr int TY = pick_div(M, cmax(16384 / (N * CS), MINW), 16);
   static constexpr int NTY = round_warps(TY * N / 16);
   // inverse y pass: the 5 mixed input tiles are staged in shared memory (6 tiles in all)
   static constexpr int TYI = pick_div(M, cmax(110000 / (6 * N * CS), MINW), 16);
@@ -127,96 +152,96 @@ struct PencilOutSrc {
 };
 
 // ---- spectral stage at one mode (Sec. 4.1, 4.2, 6.1) ----------------------------------
-// nv: de-shifted, weighted transform of u x omega at the mode (ignored if nF == 0).
-// Returns S_next for every component and performs the mode's global writes.
-template <typename T, class MP>
-__device__ __forceinline__ void spectral_point(const PencilArgs<T>& a, int kx, int ky, int kz,
-                                               size_t g, size_t fstride, cpx<T> nv[3],
-                                               cpx<T> sn[3], T E1, T Eh) {
-  const int D1 = 2 * a.fK + 1;
-  const int D = D1 * D1 * (a.fK + 1);
-  if (a.nF > 0) {
-    const int k2 = kx * kx + ky * ky + kz * kz;
-    bool keep;
-    if (a.trunc == 1) {
-      keep = max(kx, max(abs(ky), abs(kz))) <= a.Kimax;
-    } else {
-      keep = k2 <= a.K2max;
-    }
-    keep = keep && (k2 != 0);
-    if (keep) {
-      const cpx<T> v0 = nv[0], v1 = nv[1], v2 = nv[2];
-      const T fx = (T)kx, fy = (T)ky, fz = (T)kz;
-      const T ik2 = T(1) / (T)k2;
-      const cpx<T> kd = mk<T>(fx * v0.x + fy * v1.x + fz * v2.x, fx * v0.y + fy * v1.y + fz * v2.y);
-      nv[0] = v0 - (fx * ik2) * kd;
-      nv[1] = v1 - (fy * ik2) * kd;
-      nv[2] = v2 - (fz * ik2) * kd;
-    } else {
-      nv[0] = nv[1] = nv[2] = mk<T>(0, 0);
-    }
-    if (a.force && kx <= a.fK && abs(ky) <= a.fK && abs(kz) <= a.fK) {
-      const int fi = ((kz + a.fK) * D1 + (ky + a.fK)) * (a.fK + 1) + kx;
-#pragma unroll
-      for (int c = 0; c < 3; ++c) nv[c] = nv[c] + a.force[c * D + fi];
-    }
+// nv: de-shifted, weighted transform of u x omega at the mode: N(0) = 0, truncation T,
+// Leray projection P, then the forcing term O (added on the modes of the forcing table).
+template <typename T>
+__device__ __forceinline__ void project_point(const PencilArgs<T>& a, int kx, int ky, int kz,
+                                              cpx<T> nv[3]) {
+  const int k2 = kx * kx + ky * ky + kz * kz;
+  bool keep;
+  if (a.trunc == 1) {
+    keep = max(kx, max(abs(ky), abs(kz))) <= a.Kimax;
+  } else {
+    keep = k2 <= a.K2max;
   }
-  const T dt = a.dt, hdt = T(0.5) * a.dt;
+  keep = keep && (k2 != 0);
+  if (keep) {
+    const cpx<T> v0 = nv[0], v1 = nv[1], v2 = nv[2];
+    const T fx = (T)kx, fy = (T)ky, fz = (T)kz;
+    const T ik2 = T(1) / (T)k2;
+    const cpx<T> kd = mk<T>(fx * v0.x + fy * v1.x + fz * v2.x, fx * v0.y + fy * v1.y + fz * v2.y);
+    nv[0] = v0 - (fx * ik2) * kd;
+    nv[1] = v1 - (fy * ik2) * kd;
+    nv[2] = v2 - (fz * ik2) * kd;
+  } else {
+    nv[0] = nv[1] = nv[2] = mk<T>(0, 0);
+  }
+  if (a.force && kx <= a.fK && abs(ky) <= a.fK && abs(kz) <= a.fK) {
+    const int D1 = 2 * a.fK + 1, D = D1 * D1 * (a.fK + 1);
+    const int fi = ((kz + a.fK) * D1 + (ky + a.fK)) * (a.fK + 1) + kx;
 #pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    const size_t gi = g + c * fstride;
-    cpx<T> s = mk<T>(0, 0);
-    switch (a.mode) {
-      case MODE_INIT:
-        s = MP::ldw(&a.src[gi]);
-        break;
-      case MODE_RK2_1:
-        s = Eh * (MP::ldw(&a.state[gi]) + hdt * nv[c]);
-        break;
-      case MODE_RK2_2:
-        s = E1 * MP::ldw(&a.state[gi]) + (dt * Eh) * nv[c];
-        MP::st(&a.state[gi], s);
-        break;
-      case MODE_RK4_1: {
-        const cpx<T> s0 = MP::ldw(&a.state[gi]);
-        MP::st(&a.acc[gi], E1 * s0 + (dt / T(6) * E1) * nv[c]);
-        s = Eh * (s0 + hdt * nv[c]);
-      } break;
-      case MODE_RK4_2: {
-        const cpx<T> s0 = MP::ldw(&a.state[gi]);
-        MP::st(&a.acc[gi], MP::ldw(&a.acc[gi]) + (dt / T(3) * Eh) * nv[c]);
-        s = Eh * s0 + hdt * nv[c];
-      } break;
-      case MODE_RK4_3: {
-        const cpx<T> s0 = MP::ldw(&a.state[gi]);
-        MP::st(&a.acc[gi], MP::ldw(&a.acc[gi]) + (dt / T(3) * Eh) * nv[c]);
-        s = E1 * s0 + (dt * Eh) * nv[c];
-      } break;
-      case MODE_RK4_4:
-        s = MP::ldw(&a.acc[gi]) + (dt / T(6)) * nv[c];
-        MP::st(&a.state[gi], s);
-        break;
-      case MODE_ROG_1: {
-        const cpx<T> s0 = MP::ldw(&a.state[gi]);
-        MP::st(&a.state[gi], E1 * s0 + (hdt * Eh) * nv[c]);
-        s = E1 * (s0 + dt * nv[c]);
-      } break;
-      case MODE_ROG_2:
-        s = MP::ldw(&a.state[gi]) + (hdt * Eh) * nv[c];
-        MP::st(&a.state[gi], s);
-        break;
-      case MODE_NL:
-        MP::st(&a.acc[gi], nv[c]);
-        break;
-      case MODE_PROJECT:
-        MP::st(&a.state[gi], nv[c]);
-        break;
+    for (int c = 0; c < 3; ++c) nv[c] = nv[c] + a.force[c * D + fi];
+  }
+}
+
+// RK stage combine of component c at one mode (modes of PencilMode).  s0: the value read
+// from src (INIT), acc (RK4_4) or state (all other modes); s1: acc for RK4_2 / RK4_3.
+// Performs the mode's global writes and returns S_next.
+template <typename T, class MP>
+__device__ __forceinline__ cpx<T> stage_combine(const PencilArgs<T>& a, int c, size_t g, cpx<T> n,
+                                                cpx<T> s0, cpx<T> s1, T E1, T Eh) {
+  const T dt = a.dt, hdt = T(0.5) * a.dt;
+  (void)c;
+  switch (a.mode) {
+    case MODE_INIT:
+      return s0;
+    case MODE_RK2_1:
+      return Eh * (s0 + hdt * n);
+    case MODE_RK2_2: {
+      const cpx<T> s = E1 * s0 + (dt * Eh) * n;
+      MP::st(&a.state[g], s);
+      return s;
     }
-    sn[c] = s;
-    if (a.shell && kx <= a.fK && abs(ky) <= a.fK && abs(kz) <= a.fK) {
-      const int fi = ((kz + a.fK) * D1 + (ky + a.fK)) * (a.fK + 1) + kx;
-      MP::st(&a.shell[c * D + fi], s);
+    case MODE_RK4_1:
+      MP::st(&a.acc[g], E1 * s0 + (dt / T(6) * E1) * n);
+      return Eh * (s0 + hdt * n);
+    case MODE_RK4_2:
+      MP::st(&a.acc[g], s1 + (dt / T(3) * Eh) * n);
+      return Eh * s0 + hdt * n;
+    case MODE_RK4_3:
+      MP::st(&a.acc[g], s1 + (dt / T(3) * Eh) * n);
+      return E1 * s0 + (dt * Eh) * n;
+    case MODE_RK4_4: {
+      const cpx<T> s = s0 + (dt / T(6)) * n;
+      MP::st(&a.state[g], s);
+      return s;
     }
+    case MODE_ROG_1:
+      MP::st(&a.state[g], E1 * s0 + (hdt * Eh) * n);
+      return E1 * (s0 + dt * n);
+    case MODE_ROG_2: {
+      const cpx<T> s = s0 + (hdt * Eh) * n;
+      MP::st(&a.state[g], s);
+      return s;
+    }
+    case MODE_NL:
+      MP::st(&a.acc[g], n);
+      return mk<T>(0, 0);
+    default:  // MODE_PROJECT
+      MP::st(&a.state[g], n);
+      return mk<T>(0, 0);
+  }
+}
+
+// S_next of component c at the modes of the forcing table (the forcing amplitude of the
+// next stage needs Re<S_next, f>)
+template <typename T, class MP>
+__device__ __forceinline__ void shell_record(const PencilArgs<T>& a, int c, int kx, int ky, int kz,
+                                             cpx<T> sn) {
+  if (a.shell && kx <= a.fK && abs(ky) <= a.fK && abs(kz) <= a.fK) {
+    const int D1 = 2 * a.fK + 1, D = D1 * D1 * (a.fK + 1);
+    const int fi = ((kz + a.fK) * D1 + (ky + a.fK)) * (a.fK + 1) + kx;
+    MP::st(&a.shell[c * D + fi], sn);
   }
 }
 
@@ -232,6 +257,7 @@ template <typename T, int N, class MP>
 __device__ __forceinline__ void pencil_tile(const PencilArgs<T>& a, int tile_id, cpx<T>* buf) {
   using C = K2Cfg<T, N>;
   constexpr int M = N / 2, TX = C::TX, NT = C::NTP, tile = N * TX;
+  constexpr int PER = (tile + NT - 1) / NT;  // modes per thread (the last may not exist)
   static_assert(NT % TX == 0, "every thread keeps one kx");
   cpx<T>* bc[3] = {buf, buf + tile, buf + 2 * tile};
   cpx<T>* b3 = buf + 3 * tile;
@@ -243,38 +269,63 @@ __device__ __forceinline__ void pencil_tile(const PencilArgs<T>& a, int tile_id,
   const int ky = kof(iy, N);
   const bool act = threadIdx.x < NT;
   const int line = threadIdx.x % TX, kx = x0 + line;
-  load_twiddles(tws, a.tw, N);
+  const int iz0 = threadIdx.x / TX;  // this thread's modes: iz = iz0 + i * (NT / TX)
+  constexpr int DZ = NT / TX;
 
+  // 1) inputs: all three components staged asynchronously, then transformed in place
   if (a.nF > 0) {
+    for (int c = 0; c < 3; ++c) stage_col_tile<T, N, TX, NT>(bc[c], a.F[0] + c * fstride, iy, x0);
+  }
+  load_twiddles(tws, a.tw, N);  // also the barrier after which the staged tiles may be read
+  if (a.nF > 0) {
+    cp_async_wait_all();
+    __syncthreads();
     cpx<T> d0 = mk<T>(1, 0), d1 = mk<T>(1, 0);
     if (a.dsh[0]) d0 = MP::ld(&a.dsh[0][kx]) * MP::ld(&a.dsh[0][N + iy]);
     if (a.nF > 1 && a.dsh[1]) d1 = MP::ld(&a.dsh[1][kx]) * MP::ld(&a.dsh[1][N + iy]);
     for (int c = 0; c < 3; ++c) {
-      cfft_ip<T, N, 1, TX, NT, true, -1, false>(ColIn<T, N, TX, MP>{a.F[0] + c * fstride, iy, x0},
-                                                bc[c], tws);
+      cfft_ip<T, N, 1, TX, NT, true, -1, true>(SmTile<T, TX>{bc[c]}, bc[c], tws);
       __syncthreads();
       if (a.nF > 1) {
-        cfft_ip<T, N, 1, TX, NT, true, -1, false>(ColIn<T, N, TX, MP>{a.F[1] + c * fstride, iy, x0},
-                                                  b3, tws);
+        stage_col_tile<T, N, TX, NT>(b3, a.F[1] + c * fstride, iy, x0);
+        cp_async_wait_all();
+        __syncthreads();
+        cfft_ip<T, N, 1, TX, NT, true, -1, true>(SmTile<T, TX>{b3}, b3, tws);
         __syncthreads();
       }
-      for (int e = threadIdx.x; act && e < tile; e += NT) {
-        const int iz = e / TX;
-        cpx<T> v = bc[c][e];
-        if (a.dsh[0]) v = mul_conj(v, d0 * MP::ld(&a.dsh[0][2 * N + iz]));
-        v = a.wF[0] * v;
-        if (a.nF > 1) {
-          cpx<T> w = b3[e];
-          if (a.dsh[1]) w = mul_conj(w, d1 * MP::ld(&a.dsh[1][2 * N + iz]));
-          v = v + a.wF[1] * w;
+      if (act) {
+#pragma unroll 4
+        for (int i = 0; i < PER; ++i) {
+          const int iz = iz0 + i * DZ, e = iz * TX + line;
+          if (iz >= N) break;
+          cpx<T> v = bc[c][e];
+          if (a.dsh[0]) v = mul_conj(v, d0 * MP::ld(&a.dsh[0][2 * N + iz]));
+          v = a.wF[0] * v;
+          if (a.nF > 1) {
+            cpx<T> w = b3[e];
+            if (a.dsh[1]) w = mul_conj(w, d1 * MP::ld(&a.dsh[1][2 * N + iz]));
+            v = v + a.wF[1] * w;
+          }
+          bc[c][e] = v;
         }
-        bc[c][e] = v;
       }
       __syncthreads();
     }
+    // 2a) N(0) = 0, truncation, projection, forcing (all components of a mode at once)
+    if (act) {
+      for (int i = 0; i < PER; ++i) {
+        const int iz = iz0 + i * DZ, e = iz * TX + line;
+        if (iz >= N) break;
+        cpx<T> nv[3] = {bc[0][e], bc[1][e], bc[2][e]};
+        project_point(a, kx, ky, kof(iz, N), nv);
+        bc[0][e] = nv[0];
+        bc[1][e] = nv[1];
+        bc[2][e] = nv[2];
+      }
+    }
   }
 
-  // stage; with a single shifted output the shift is applied here, once per mode
+  // 2b) stage combine per component, the state of the thread's modes loaded together
   const bool pre = a.nOut == 1 && a.osh[0] != nullptr;
   cpx<T> oxy = mk<T>(1, 0);
   if (pre) oxy = MP::ld(&a.osh[0][kx]) * MP::ld(&a.osh[0][N + iy]);
@@ -284,30 +335,42 @@ __device__ __forceinline__ void pencil_tile(const PencilArgs<T>& a, int tile_id,
     e1xy = a.ifac[kx] * a.ifac[iy];
     ehxy = a.ifac[N + kx] * a.ifac[N + iy];
   }
-  for (int e = threadIdx.x; act && e < tile; e += NT) {
-    const int iz = e / TX, kz = kof(iz, N);
-    const size_t g = ((size_t)iz * N + iy) * M + kx;
-    cpx<T> nv[3], sn[3];
-    if (a.nF > 0) {
-      nv[0] = bc[0][e];
-      nv[1] = bc[1][e];
-      nv[2] = bc[2][e];
+  if (act) {
+    constexpr int CHK = PER < 8 ? PER : 8;  // modes whose state loads are in flight together
+    const bool rd0 = a.mode != MODE_NL && a.mode != MODE_PROJECT;
+    const bool rd1 = a.mode == MODE_RK4_2 || a.mode == MODE_RK4_3;
+    const cpx<T>* base0 = a.mode == MODE_INIT ? a.src : (a.mode == MODE_RK4_4 ? a.acc : a.state);
+    for (int c = 0; c < 3; ++c)
+    for (int i0 = 0; i0 < PER; i0 += CHK) {
+      const size_t gc = c * fstride + (size_t)iy * M + kx;
+      cpx<T> s0[CHK], s1[CHK];
+#pragma unroll
+      for (int j = 0; j < CHK; ++j) {
+        const int iz = iz0 + (i0 + j) * DZ;
+        const size_t g = gc + (size_t)iz * N * M;
+        s0[j] = s1[j] = mk<T>(0, 0);
+        if (iz < N && i0 + j < PER) {
+          if (rd0) s0[j] = MP::ldw(&base0[g]);
+          if (rd1) s1[j] = MP::ldw(&a.acc[g]);
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < CHK; ++j) {
+        const int iz = iz0 + (i0 + j) * DZ, e = iz * TX + line;
+        if (iz >= N || i0 + j >= PER) break;
+        const size_t g = gc + (size_t)iz * N * M;
+        T E1 = 1, Eh = 1;
+        if (useE) {
+          E1 = e1xy * a.ifac[iz];
+          Eh = ehxy * a.ifac[N + iz];
+        }
+        const cpx<T> n = a.nF > 0 ? bc[c][e] : mk<T>(0, 0);
+        cpx<T> sn = stage_combine<T, MP>(a, c, g, n, s0[j], s1[j], E1, Eh);
+        shell_record<T, MP>(a, c, kx, ky, kof(iz, N), sn);
+        if (pre) sn = sn * (oxy * MP::ld(&a.osh[0][2 * N + iz]));
+        bc[c][e] = sn;
+      }
     }
-    T E1 = 1, Eh = 1;
-    if (useE) {
-      E1 = e1xy * a.ifac[iz];
-      Eh = ehxy * a.ifac[N + iz];
-    }
-    spectral_point<T, MP>(a, kx, ky, kz, g, fstride, nv, sn, E1, Eh);
-    if (pre) {
-      const cpx<T> ph = oxy * MP::ld(&a.osh[0][2 * N + iz]);
-      sn[0] = sn[0] * ph;
-      sn[1] = sn[1] * ph;
-      sn[2] = sn[2] * ph;
-    }
-    bc[0][e] = sn[0];
-    bc[1][e] = sn[1];
-    bc[2][e] = sn[2];
   }
   __syncthreads();
 
@@ -393,11 +456,9 @@ __device__ __forceinline__ void yinv_tile(const SlabArgs<T>& a, int tx, int zg, 
   const int x0 = tx * TY, z = a.z0 + zg;
   const size_t sstride = (size_t)a.G * N * M;
   const size_t fs = (size_t)N * N * M;
+  for (int f = 0; f < 5; ++f) stage_col_tile<T, N, TY, NT, true>(in + f * tile, a.mixed + f * fs, z, x0);
   for (int i = threadIdx.x; i < N; i += blockDim.x) tws[i] = ldg(&a.tw[i]);
-  for (int i = threadIdx.x; threadIdx.x < NT && i < 5 * tile; i += NT) {
-    const int f = i / tile, rem = i % tile, e = rem / TY, line = rem % TY;
-    in[i] = MP::ld(&a.mixed[f * fs + ((size_t)z * N + e) * M + x0 + line]);
-  }
+  cp_async_wait_all();
   __syncthreads();
   yinv_field<T, N, 0, MP>(a, in, W, zg, x0, sstride, tws);
   yinv_field<T, N, 1, MP>(a, in, W, zg, x0, sstride, tws);

@@ -297,3 +297,22 @@ def test_specialised_and_generic_kernels_agree(ns, prec, code, monkeypatch):
             s.step(0.01, 3)
             out.append(s.get_state())
     assert rel(out[0], out[1]) < (1e-13 if prec else 3e-6)
+
+
+def test_results_do_not_depend_on_slab_group_size(ns, monkeypatch, tmp_path):
+    # the autotuner only changes how many planes share the L2-resident scratch
+    N = 128
+    u = field(N, seed=31)
+    out = []
+    monkeypatch.setenv("NS_AUTOTUNE_CACHE", str(tmp_path / "tune.json"))
+    for g in ("5", "128", None):
+        if g is None:
+            monkeypatch.delenv("NS_SLAB_PLANES", raising=False)
+        else:
+            monkeypatch.setenv("NS_SLAB_PLANES", g)
+        with ns.Solver(N, 0.001, N / 2, scheme=4, precision=0, seed=3) as s:
+            s.set_velocity(u)
+            s.step(0.005, 2)
+            out.append(s.get_state())
+    assert np.array_equal(out[0], out[1]) and np.array_equal(out[0], out[2])
+    assert (tmp_path / "tune.json").exists()
