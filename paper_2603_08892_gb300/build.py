@@ -15,6 +15,8 @@ LIB = os.path.join(HERE, "libns.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I" + os.path.join(ROOT, "include")]
+# extra nvcc flags (tuning experiments, e.g. NS_NVCC_FLAGS="-DNS_MAX_RADIX=8")
+FLAGS += os.environ.get("NS_NVCC_FLAGS", "").split()
 
 
 def _nvcc():

@@ -21,14 +21,23 @@ struct CPlan {
   int r[8];
 };
 
+// Largest radix of the register butterflies (16 or 8; 8 measured faster on GB300): 8 halves
+// the values a thread holds
+// and doubles the threads that share a tile (more warps to hide latency), at the cost of
+// one more shared-memory pass for n = 256.
+#ifndef NS_MAX_RADIX
+#define NS_MAX_RADIX 8
+#endif
+
 __host__ __device__ constexpr CPlan cplan(int n) {
   CPlan p{0, {0, 0, 0, 0, 0, 0, 0, 0}};
   int m = n, a2 = 0, a3 = 0;
   while (m % 2 == 0) { m /= 2; ++a2; }
   while (m % 3 == 0) { m /= 3; ++a3; }
-  while (a2 >= 4) { p.r[p.nst++] = 16; a2 -= 4; }
-  if (a2 == 3) p.r[p.nst++] = 8;
-  else if (a2 == 2) p.r[p.nst++] = 4;
+  if (NS_MAX_RADIX >= 16)
+    while (a2 >= 4) { p.r[p.nst++] = 16; a2 -= 4; }
+  while (a2 >= 3) { p.r[p.nst++] = 8; a2 -= 3; }
+  if (a2 == 2) p.r[p.nst++] = 4;
   else if (a2 == 1) p.r[p.nst++] = 2;
   for (int i = 0; i < a3; ++i) p.r[p.nst++] = 3;
   return p;

@@ -92,18 +92,18 @@ struct K2Cfg {
   static constexpr int MINW = 32 / CS;  // 32-byte global segments
   // pencil: TX columns of N
   static constexpr int TX = pick_div(M, cmax(16384 / (N * CS), MINW), 16);
-  static constexpr int NTP = round_lines(TX * N / 16, TX);
+  static constexpr int NTP = round_lines(TX * N / NS_MAX_RADIX, TX);
   // blocks per SM the register budget must allow (at least 128 registers per thread)
   static constexpr int MINB_P = cmax(1, cmin(4, 65536 / (NTP * 128)));
   // y passes: TY columns of N
   static constexpr int TY = pick_div(M, cmax(16384 / (N * CS), MINW), 16);
-  static constexpr int NTY = round_warps(TY * N / 16);
+  static constexpr int NTY = round_warps(TY * N / NS_MAX_RADIX);
   // inverse y pass: the 5 mixed input tiles are staged in shared memory (6 tiles in all)
   static constexpr int TYI = pick_div(M, cmax(110000 / (6 * N * CS), MINW), 16);
-  static constexpr int NTYI = round_warps(TYI * N / 16);
+  static constexpr int NTYI = round_warps(TYI * N / NS_MAX_RADIX);
   // x rows: RX rows of M, processed three fields at a time
   static constexpr int RX = cmin(cmax(8192 / (M * CS), 1), 16);
-  static constexpr int NTX = round_warps(3 * RX * M / 16);
+  static constexpr int NTX = round_warps(3 * RX * M / NS_MAX_RADIX);
   static constexpr int XLS = WorkTile<T, M, 3 * RX, false>::LS;
   static constexpr int XBUF = 3 * RX * XLS;  // elements of one 3-field row buffer
   static __host__ __device__ constexpr int pencil_tiles(int nF) { return nF > 1 ? 5 : 4; }
