@@ -22,9 +22,8 @@ struct CPlan {
 };
 
 // Largest radix of the register butterflies (16 or 8; 8 measured faster on GB300): 8 halves
-// the values a thread holds
-// and doubles the threads that share a tile (more warps to hide latency), at the cost of
-// one more shared-memory pass for n = 256.
+// the values a thread holds and doubles the threads that share a tile (more warps to hide
+// latency), at the cost of one more shared-memory pass for n = 256.
 #ifndef NS_MAX_RADIX
 #define NS_MAX_RADIX 8
 #endif
