@@ -93,8 +93,12 @@ struct K2Cfg {
   // pencil: TX columns of N
   static constexpr int TX = pick_div(M, cmax(16384 / (N * CS), MINW), 16);
   static constexpr int NTP = round_lines(TX * N / NS_MAX_RADIX, TX);
-  // blocks per SM the register budget must allow (at least 128 registers per thread)
-  static constexpr int MINB_P = cmax(1, cmin(4, 65536 / (NTP * 128)));
+  // blocks per SM the register budget must allow (NS_PENCIL_REGS registers per thread;
+  // 80 measured best at 256^3 FP32 on GB300 against 96 and 128)
+#ifndef NS_PENCIL_REGS
+#define NS_PENCIL_REGS 80
+#endif
+  static constexpr int MINB_P = cmax(1, cmin(8, 65536 / (NTP * NS_PENCIL_REGS)));
   // y passes: TY columns of N
   static constexpr int TY = pick_div(M, cmax(16384 / (N * CS), MINW), 16);
   static constexpr int NTY = round_warps(TY * N / NS_MAX_RADIX);
