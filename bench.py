@@ -270,27 +270,37 @@ def main():
     ms_step = ms_max / K
     hbm, peak_kind = peaks()
 
-    # dominant kernel and its algorithmic bytes per launch
+    # Roofline units.  The pencil pass is one launch (INIT + 2 per step; the last has no
+    # output): 14C per launch.  The slab pass is one HBM pass made of three kernels per plane
+    # group (y inverse, x rows, y forward) whose intermediates stay in L2 by design: it reads
+    # the 5 mixed fields (5C) and writes the 3 transformed products (3C), 8C per pass.
     nchunks = (K + 255) // 256
-    pencil_bytes = (8.0 + 28.0 * K - 5.0) * C  # INIT + 2 pencil passes/step, last has no output
-    G_planes = max(1, min(N_PS, int((48 << 20) // (6 * N_PS * (N_PS // 2) * 8))))
-    kinds = {"k_pencil": pencil_bytes / prof["k_pencil"][2],
-             "k_yinv": 5.0 * C * G_planes / N_PS,
-             "k_yfwd": 3.0 * C * G_planes / N_PS,
-             "k_xrow": 0.0}
-    tot = {k: prof[k][0] for k in kinds}
-    dom = max(tot, key=tot.get)
-    avg_ms = prof[dom][0] / max(1, prof[dom][1])
-    achieved = kinds[dom] / (avg_ms / 1000.0) / 1e9
+    pencil_bytes = (8.0 + 28.0 * K - 5.0) * C
+    units = {
+        "k_pencil": (pencil_bytes / max(1, prof["k_pencil"][2]), prof["k_pencil"][0],
+                     prof["k_pencil"][1]),
+        "slab_pass": (8.0 * C, prof["slab_pass"][0], prof["slab_pass"][1]),
+    }
+    roof_units = {}
+    for name, (nbytes, tot_ms, n) in units.items():
+        avg = tot_ms / max(1, n)
+        ach = nbytes / (avg / 1000.0) / 1e9
+        roof_units[name] = {"algorithmic_bytes_per_launch": nbytes, "avg_launch_ms": avg,
+                            "achieved": ach, "frac": ach / hbm, "ms_per_step": tot_ms / K}
+    dom = max(roof_units, key=lambda k: roof_units[k]["ms_per_step"])
+    kern = ("k_pencil", "k_yinv", "k_xrow", "k_yfwd")
+    tot = {k: prof[k][0] for k in kern}
     shares = {k: round(tot[k] / max(1e-9, sum(tot.values())), 4) for k in tot}
     kernel_ms = {k: round(tot[k] / K, 4) for k in tot}  # event time per step, each kind
-    launches = sum(prof[k][2] for k in ("k_pencil", "k_yinv", "k_xrow", "k_yfwd")) + nchunks
-    roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
-            "frac": achieved / hbm, "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)",
-            "algorithmic_bytes_per_launch": kinds[dom], "avg_launch_ms": avg_ms,
-            "traffic": ncu_traffic(dom), "kernel_time_shares": shares,
-            "kernel_ms_per_step": kernel_ms,
-            "slab_pass_ms_per_step": round(prof["slab_pass"][0] / K, 4),
+    launches = sum(prof[k][2] for k in kern) + nchunks
+    ru = roof_units[dom]
+    roof = {"bound": "hbm",
+            "kernel": dom if dom == "k_pencil" else "slab_pass (k_yinv + k_xrow + k_yfwd)",
+            "achieved": ru["achieved"], "peak": hbm, "unit": "GB/s", "frac": ru["frac"],
+            "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)",
+            "algorithmic_bytes_per_launch": ru["algorithmic_bytes_per_launch"],
+            "avg_launch_ms": ru["avg_launch_ms"], "traffic": ncu_traffic(dom),
+            "units": roof_units, "kernel_time_shares": shares, "kernel_ms_per_step": kernel_ms,
             "step_model_bytes": model_bytes,
             "step_frac": (model_bytes / (ms_step / 1000.0) / 1e9) / hbm}
 

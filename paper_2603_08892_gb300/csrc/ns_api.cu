@@ -306,6 +306,7 @@ struct Solver : SolverBase {
       if ((int)k2.smP5 > optin || (int)k2.smX > optin || (int)k2.smY > optin || (int)k2.smYI > optin)
         throw NsError{NS_ERR_INTERNAL, "specialised tile shapes exceed the shared memory of the device"};
       CUDA_TRY(cudaFuncSetAttribute(k2.pencil, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+      CUDA_TRY(cudaFuncSetAttribute(k2.pencil1, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
       CUDA_TRY(cudaFuncSetAttribute(k2.yinv, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
       CUDA_TRY(cudaFuncSetAttribute(k2.yfwd, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
       CUDA_TRY(cudaFuncSetAttribute(k2.xrow, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
@@ -428,7 +429,8 @@ struct Solver : SolverBase {
   void pencil(const PencilArgs<T>& a) {
     cudaEvent_t e = prof_begin(NS_PROF_PENCIL);
     if (use2)
-      k2.pencil<<<(M / k2.TX) * N, k2.NTP, (a.nF > 1 || a.nOut > 1) ? k2.smP5 : k2.smP4, st>>>(a);
+      (a.nF == 1 && a.nOut == 1 ? k2.pencil1 : k2.pencil)<<<(M / k2.TX) * N, k2.NTP,
+                                                          (a.nF > 1 || a.nOut > 1) ? k2.smP5 : k2.smP4, st>>>(a);
     else
       k_pencil<T><<<(M / TX) * N, bdP, smP, st>>>(a);
     prof_end(e);

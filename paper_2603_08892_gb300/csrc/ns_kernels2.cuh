@@ -257,15 +257,19 @@ __device__ __forceinline__ void shell_record(const PencilArgs<T>& a, int c, int 
 template <typename T, int N>
 __host__ __device__ constexpr int pencil_tiles(int nF, int nOut) { return (nF > 1 || nOut > 1) ? 4 : 3; }
 
-template <typename T, int N, class MP>
+// ONE: the tile has one input and one output (a.nF == 1, a.nOut == 1) -- every RK2, Rogallo
+// and RK4 stage -- known at compile time, which keeps the kernel free of register spills.
+template <typename T, int N, class MP, bool ONE = false>
 __device__ __forceinline__ void pencil_tile(const PencilArgs<T>& a, int tile_id, cpx<T>* buf) {
   using C = K2Cfg<T, N>;
+  const int nF = ONE ? 1 : a.nF, nOut = ONE ? 1 : a.nOut;
   constexpr int M = N / 2, TX = C::TX, NT = C::NTP, tile = N * TX;
   constexpr int PER = (tile + NT - 1) / NT;  // modes per thread (the last may not exist)
   static_assert(NT % TX == 0, "every thread keeps one kx");
-  cpx<T>* bc[3] = {buf, buf + tile, buf + 2 * tile};
+  // component tile c is buf + c * tile (pointer arithmetic, not an array: no local memory)
+  auto bc = [&](int c) { return buf + c * tile; };
   cpx<T>* b3 = buf + 3 * tile;
-  cpx<T>* tws = buf + pencil_tiles<T, N>(a.nF, a.nOut) * tile;
+  cpx<T>* tws = buf + pencil_tiles<T, N>(nF, nOut) * tile;
   constexpr int ntx = M / TX;
   const int iy = tile_id / ntx;
   const int x0 = (tile_id % ntx) * TX;
@@ -277,20 +281,20 @@ __device__ __forceinline__ void pencil_tile(const PencilArgs<T>& a, int tile_id,
   constexpr int DZ = NT / TX;
 
   // 1) inputs: all three components staged asynchronously, then transformed in place
-  if (a.nF > 0) {
-    for (int c = 0; c < 3; ++c) stage_col_tile<T, N, TX, NT>(bc[c], a.F[0] + c * fstride, iy, x0);
+  if (nF > 0) {
+    for (int c = 0; c < 3; ++c) stage_col_tile<T, N, TX, NT>(bc(c), a.F[0] + c * fstride, iy, x0);
   }
   load_twiddles(tws, a.tw, N);  // also the barrier after which the staged tiles may be read
-  if (a.nF > 0) {
+  if (nF > 0) {
     cp_async_wait_all();
     __syncthreads();
     cpx<T> d0 = mk<T>(1, 0), d1 = mk<T>(1, 0);
     if (a.dsh[0]) d0 = MP::ld(&a.dsh[0][kx]) * MP::ld(&a.dsh[0][N + iy]);
-    if (a.nF > 1 && a.dsh[1]) d1 = MP::ld(&a.dsh[1][kx]) * MP::ld(&a.dsh[1][N + iy]);
+    if (nF > 1 && a.dsh[1]) d1 = MP::ld(&a.dsh[1][kx]) * MP::ld(&a.dsh[1][N + iy]);
     for (int c = 0; c < 3; ++c) {
-      cfft_ip<T, N, 1, TX, NT, true, -1, true>(SmTile<T, TX>{bc[c]}, bc[c], tws);
+      cfft_ip<T, N, 1, TX, NT, true, -1, true>(SmTile<T, TX>{bc(c)}, bc(c), tws);
       __syncthreads();
-      if (a.nF > 1) {
+      if (nF > 1) {
         stage_col_tile<T, N, TX, NT>(b3, a.F[1] + c * fstride, iy, x0);
         cp_async_wait_all();
         __syncthreads();
@@ -302,15 +306,15 @@ __device__ __forceinline__ void pencil_tile(const PencilArgs<T>& a, int tile_id,
         for (int i = 0; i < PER; ++i) {
           const int iz = iz0 + i * DZ, e = iz * TX + line;
           if (iz >= N) break;
-          cpx<T> v = bc[c][e];
+          cpx<T> v = bc(c)[e];
           if (a.dsh[0]) v = mul_conj(v, d0 * MP::ld(&a.dsh[0][2 * N + iz]));
           v = a.wF[0] * v;
-          if (a.nF > 1) {
+          if (nF > 1) {
             cpx<T> w = b3[e];
             if (a.dsh[1]) w = mul_conj(w, d1 * MP::ld(&a.dsh[1][2 * N + iz]));
             v = v + a.wF[1] * w;
           }
-          bc[c][e] = v;
+          bc(c)[e] = v;
         }
       }
       __syncthreads();
@@ -320,17 +324,17 @@ __device__ __forceinline__ void pencil_tile(const PencilArgs<T>& a, int tile_id,
       for (int i = 0; i < PER; ++i) {
         const int iz = iz0 + i * DZ, e = iz * TX + line;
         if (iz >= N) break;
-        cpx<T> nv[3] = {bc[0][e], bc[1][e], bc[2][e]};
+        cpx<T> nv[3] = {bc(0)[e], bc(1)[e], bc(2)[e]};
         project_point(a, kx, ky, kof(iz, N), nv);
-        bc[0][e] = nv[0];
-        bc[1][e] = nv[1];
-        bc[2][e] = nv[2];
+        bc(0)[e] = nv[0];
+        bc(1)[e] = nv[1];
+        bc(2)[e] = nv[2];
       }
     }
   }
 
   // 2b) stage combine per component, the state of the thread's modes loaded together
-  const bool pre = a.nOut == 1 && a.osh[0] != nullptr;
+  const bool pre = nOut == 1 && a.osh[0] != nullptr;
   cpx<T> oxy = mk<T>(1, 0);
   if (pre) oxy = MP::ld(&a.osh[0][kx]) * MP::ld(&a.osh[0][N + iy]);
   const bool useE = a.mode != MODE_INIT && a.mode != MODE_NL && a.mode != MODE_PROJECT;
@@ -368,35 +372,34 @@ __device__ __forceinline__ void pencil_tile(const PencilArgs<T>& a, int tile_id,
           E1 = e1xy * a.ifac[iz];
           Eh = ehxy * a.ifac[N + iz];
         }
-        const cpx<T> n = a.nF > 0 ? bc[c][e] : mk<T>(0, 0);
+        const cpx<T> n = nF > 0 ? bc(c)[e] : mk<T>(0, 0);
         cpx<T> sn = stage_combine<T, MP>(a, c, g, n, s0[j], s1[j], E1, Eh);
         shell_record<T, MP>(a, c, kx, ky, kof(iz, N), sn);
         if (pre) sn = sn * (oxy * MP::ld(&a.osh[0][2 * N + iz]));
-        bc[c][e] = sn;
+        bc(c)[e] = sn;
       }
     }
   }
   __syncthreads();
 
-  if (a.nOut == 1) {
+  if (nOut == 1) {
     // u_z first (its tile then serves as the work tile), then u_x, d_z u_x, u_y, d_z u_y
     const cpx<T>* sh = pre ? nullptr : a.osh[0];
-    cfft_src_in_work<T, N, 1, TX, NT, true, 1>(PencilOutSrc<T, N, TX, MP>{bc[2], sh, iy, x0, false},
+    cfft_src_in_work<T, N, 1, TX, NT, true, 1>(PencilOutSrc<T, N, TX, MP>{bc(2), sh, iy, x0, false},
                                                ColOut<T, N, TX, MP>{a.out[0] + 2 * fstride, iy, x0},
-                                               bc[2], tws);
+                                               bc(2), tws);
     __syncthreads();
-    const int order[4] = {0, 3, 1, 4};
     for (int i = 0; i < 4; ++i) {
-      const int f = order[i], c = f < 3 ? f : f - 3;
-      cfft<T, N, 1, TX, NT, true, 1>(PencilOutSrc<T, N, TX, MP>{bc[c], sh, iy, x0, f >= 3},
-                                     ColOut<T, N, TX, MP>{a.out[0] + f * fstride, iy, x0}, bc[2], tws);
+      const int f = (i & 1) ? 3 + (i >> 1) : (i >> 1), c = f < 3 ? f : f - 3;  // 0, 3, 1, 4
+      cfft<T, N, 1, TX, NT, true, 1>(PencilOutSrc<T, N, TX, MP>{bc(c), sh, iy, x0, f >= 3},
+                                     ColOut<T, N, TX, MP>{a.out[0] + f * fstride, iy, x0}, bc(2), tws);
       __syncthreads();
     }
   } else {
-    for (int o = 0; o < a.nOut; ++o) {
+    for (int o = 0; o < nOut; ++o) {
       for (int f = 0; f < 5; ++f) {
         const int c = f < 3 ? f : f - 3;
-        cfft<T, N, 1, TX, NT, true, 1>(PencilOutSrc<T, N, TX, MP>{bc[c], a.osh[o], iy, x0, f >= 3},
+        cfft<T, N, 1, TX, NT, true, 1>(PencilOutSrc<T, N, TX, MP>{bc(c), a.osh[o], iy, x0, f >= 3},
                                        ColOut<T, N, TX, MP>{a.out[o] + f * fstride, iy, x0}, b3, tws);
         __syncthreads();
       }
@@ -404,10 +407,10 @@ __device__ __forceinline__ void pencil_tile(const PencilArgs<T>& a, int tile_id,
   }
 }
 
-template <typename T, int N>
+template <typename T, int N, bool ONE>
 __global__ void __launch_bounds__(K2Cfg<T, N>::NTP, K2Cfg<T, N>::MINB_P) k2_pencil(PencilArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  pencil_tile<T, N, MemNC>(a, blockIdx.x, reinterpret_cast<cpx<T>*>(smem_raw));
+  pencil_tile<T, N, MemNC, ONE>(a, blockIdx.x, reinterpret_cast<cpx<T>*>(smem_raw));
 }
 
 // ---- slab pass: y transforms --------------------------------------------------------
@@ -608,7 +611,8 @@ __global__ void __launch_bounds__(K2Cfg<T, N>::NTX) k2_xrow(SlabArgs<T> a) {
 template <typename T>
 struct K2Entry {
   int N = 0;
-  void (*pencil)(PencilArgs<T>) = nullptr;
+  void (*pencil)(PencilArgs<T>) = nullptr;   // any number of inputs / outputs
+  void (*pencil1)(PencilArgs<T>) = nullptr;  // one input, one output
   void (*yinv)(SlabArgs<T>) = nullptr;
   void (*yfwd)(SlabArgs<T>) = nullptr;
   void (*xrow)(SlabArgs<T>) = nullptr;
@@ -621,7 +625,8 @@ K2Entry<T> make_k2_entry() {
   using C = K2Cfg<T, N>;
   K2Entry<T> e;
   e.N = N;
-  e.pencil = k2_pencil<T, N>;
+  e.pencil = k2_pencil<T, N, false>;
+  e.pencil1 = k2_pencil<T, N, true>;
   e.yinv = k2_yinv<T, N>;
   e.yfwd = k2_yfwd<T, N>;
   e.xrow = k2_xrow<T, N>;
