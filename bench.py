@@ -301,6 +301,7 @@ def main():
             "algorithmic_bytes_per_launch": ru["algorithmic_bytes_per_launch"],
             "avg_launch_ms": ru["avg_launch_ms"], "traffic": ncu_traffic(dom),
             "units": roof_units, "kernel_time_shares": shares, "kernel_ms_per_step": kernel_ms,
+            "slab_groups_per_pass": prof["k_yinv"][2] / max(1, prof["slab_pass"][2]),
             "step_model_bytes": model_bytes,
             "step_frac": (model_bytes / (ms_step / 1000.0) / 1e9) / hbm}
 

@@ -307,6 +307,7 @@ struct Solver : SolverBase {
         throw NsError{NS_ERR_INTERNAL, "specialised tile shapes exceed the shared memory of the device"};
       CUDA_TRY(cudaFuncSetAttribute(k2.pencil, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
       CUDA_TRY(cudaFuncSetAttribute(k2.pencil1, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+      CUDA_TRY(cudaFuncSetAttribute(k2.pencil2, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
       CUDA_TRY(cudaFuncSetAttribute(k2.yinv, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
       CUDA_TRY(cudaFuncSetAttribute(k2.yfwd, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
       CUDA_TRY(cudaFuncSetAttribute(k2.xrow, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
@@ -429,8 +430,10 @@ struct Solver : SolverBase {
   void pencil(const PencilArgs<T>& a) {
     cudaEvent_t e = prof_begin(NS_PROF_PENCIL);
     if (use2)
-      (a.nF == 1 && a.nOut == 1 ? k2.pencil1 : k2.pencil)<<<(M / k2.TX) * N, k2.NTP,
-                                                          (a.nF > 1 || a.nOut > 1) ? k2.smP5 : k2.smP4, st>>>(a);
+      (a.nF == 1 && a.nOut == 1   ? k2.pencil1
+       : a.nF == 2 && a.nOut == 2 ? k2.pencil2
+                                  : k2.pencil)<<<(M / k2.TX) * N, k2.NTP,
+                                                  (a.nF > 1 || a.nOut > 1) ? k2.smP5 : k2.smP4, st>>>(a);
     else
       k_pencil<T><<<(M / TX) * N, bdP, smP, st>>>(a);
     prof_end(e);
@@ -583,6 +586,9 @@ struct Solver : SolverBase {
     cudaGetDeviceProperties(&pr, c->p.device);
     std::string k = std::string(pr.name) + "|N=" + std::to_string(N) + "|" +
                     (sizeof(T) == 4 ? "fp32" : "fp64") + (use2 ? "|k2" : "|generic");
+    if (use2)  // the slab kernels' tiles and thread counts: a change of kernels re-tunes
+      k += "|" + std::to_string(k2.TYI) + "," + std::to_string(k2.NTYI) + "," + std::to_string(k2.TY) +
+           "," + std::to_string(k2.NTY) + "," + std::to_string(k2.RX) + "," + std::to_string(k2.NTX);
     for (auto& ch : k)
       if (ch == '"' || ch == '\\') ch = '_';
     return k;
@@ -672,7 +678,7 @@ struct Solver : SolverBase {
       G = q;
       slab(mixed[0], Ft[0]);  // warm-up
       CUDA_TRY(cudaEventRecord(e0, st));
-      for (int r = 0; r < 3; ++r) slab(mixed[0], Ft[0]);
+      for (int r = 0; r < 8; ++r) slab(mixed[0], Ft[0]);
       CUDA_TRY(cudaEventRecord(e1, st));
       CUDA_TRY(cudaEventSynchronize(e1));
       float ms = 0;

@@ -21,19 +21,19 @@ struct CPlan {
   int r[8];
 };
 
-// Largest radix of the register butterflies (16 or 8; 8 measured faster on GB300): 8 halves
-// the values a thread holds and doubles the threads that share a tile (more warps to hide
-// latency), at the cost of one more shared-memory pass for n = 256.
+// Largest radix of the register butterflies (16 or 8).  8 halves the values a thread holds
+// and doubles the threads that share a tile (more warps to hide latency), at the cost of one
+// more shared-memory pass for n = 256; every kernel can pick its own cap (template MR).
 #ifndef NS_MAX_RADIX
 #define NS_MAX_RADIX 8
 #endif
 
-__host__ __device__ constexpr CPlan cplan(int n) {
+__host__ __device__ constexpr CPlan cplan(int n, int mr = NS_MAX_RADIX) {
   CPlan p{0, {0, 0, 0, 0, 0, 0, 0, 0}};
   int m = n, a2 = 0, a3 = 0;
   while (m % 2 == 0) { m /= 2; ++a2; }
   while (m % 3 == 0) { m /= 3; ++a3; }
-  if (NS_MAX_RADIX >= 16)
+  if (mr >= 16)
     while (a2 >= 4) { p.r[p.nst++] = 16; a2 -= 4; }
   while (a2 >= 3) { p.r[p.nst++] = 8; a2 -= 3; }
   if (a2 == 2) p.r[p.nst++] = 4;
@@ -168,9 +168,9 @@ __device__ __forceinline__ void cstage(const Src& src, const Dst& dst, const cpx
 }
 
 template <typename T, int n, int TWS, int NL, int NT, bool LF, int DIR, int S, int NS,
-          bool HOLD0 = false>
+          bool HOLD0 = false, int MR = NS_MAX_RADIX>
 struct CStages {
-  static constexpr CPlan P = cplan(n);
+  static constexpr CPlan P = cplan(n, MR);
   template <class Src, class Dst>
   static __device__ __forceinline__ void run(const Src& src, const Dst& dst, cpx<T>* work,
                                              const cpx<T>* __restrict__ tw) {
@@ -183,13 +183,13 @@ struct CStages {
     } else if constexpr (first) {
       cstage<T, n, R, NS, TWS, NL, NT, LF, DIR, HOLD0>(src, W, tw);
       __syncthreads();
-      CStages<T, n, TWS, NL, NT, LF, DIR, S + 1, NS * R>::run(src, dst, work, tw);
+      CStages<T, n, TWS, NL, NT, LF, DIR, S + 1, NS * R, false, MR>::run(src, dst, work, tw);
     } else if constexpr (last) {
       cstage<T, n, R, NS, TWS, NL, NT, LF, DIR, false>(W, dst, tw);
     } else {
       cstage<T, n, R, NS, TWS, NL, NT, LF, DIR, true>(W, W, tw);
       __syncthreads();
-      CStages<T, n, TWS, NL, NT, LF, DIR, S + 1, NS * R>::run(src, dst, work, tw);
+      CStages<T, n, TWS, NL, NT, LF, DIR, S + 1, NS * R, false, MR>::run(src, dst, work, tw);
     }
   }
 };
@@ -197,44 +197,63 @@ struct CStages {
 // Transform of NL lines of length n: src -> dst through the shared work tile `work`
 // (WorkTile<T, n, NL, LF>::elems() values).  DIR = -1 forward, +1 inverse.  TWS = table
 // length / n.  The caller places a barrier after it before dst is read by other threads.
-template <typename T, int n, int TWS, int NL, int NT, bool LF, int DIR, class Src, class Dst>
+template <typename T, int n, int TWS, int NL, int NT, bool LF, int DIR, int MR = NS_MAX_RADIX,
+          class Src, class Dst>
 __device__ __forceinline__ void cfft(const Src& src, const Dst& dst, cpx<T>* work,
                                      const cpx<T>* __restrict__ tw) {
-  CStages<T, n, TWS, NL, NT, LF, DIR, 0, 1>::run(src, dst, work, tw);
+  CStages<T, n, TWS, NL, NT, LF, DIR, 0, 1, false, MR>::run(src, dst, work, tw);
 }
 
 // Same, for a source that reads the work tile itself: stage 0 reads every input before it
 // writes the work tile.
-template <typename T, int n, int TWS, int NL, int NT, bool LF, int DIR, class Src, class Dst>
+template <typename T, int n, int TWS, int NL, int NT, bool LF, int DIR, int MR = NS_MAX_RADIX,
+          class Src, class Dst>
 __device__ __forceinline__ void cfft_src_in_work(const Src& src, const Dst& dst, cpx<T>* work,
                                                  const cpx<T>* __restrict__ tw) {
-  CStages<T, n, TWS, NL, NT, LF, DIR, 0, 1, true>::run(src, dst, work, tw);
+  CStages<T, n, TWS, NL, NT, LF, DIR, 0, 1, true, MR>::run(src, dst, work, tw);
 }
 
 // In place: stage 0 reads src (ALIAS: src is the tile itself) and writes the tile B; every
 // later stage runs in place on B with its inputs held in registers across a barrier.  The
-// result is left in B in natural order; no separate work tile is needed.
-template <typename T, int n, int TWS, int NL, int NT, bool LF, int DIR, bool ALIAS, int S, int NS>
+// last stage writes through dst (an accessor over the same tile, e.g. applying a pointwise
+// factor); the result is left in natural order.  No separate work tile is needed.
+template <typename T, int n, int TWS, int NL, int NT, bool LF, int DIR, bool ALIAS, int S, int NS,
+          int MR = NS_MAX_RADIX>
 struct CStagesIP {
-  static constexpr CPlan P = cplan(n);
-  template <class Src>
+  static constexpr CPlan P = cplan(n, MR);
+  template <class Src, class Dst>
   static __device__ __forceinline__ void run(const Src& src, const WorkTile<T, n, NL, LF>& B,
-                                             const cpx<T>* __restrict__ tw) {
+                                             const Dst& dst, const cpx<T>* __restrict__ tw) {
     constexpr int R = P.r[S];
-    if constexpr (S == 0)
+    constexpr bool last = S + 1 == P.nst;
+    if constexpr (S == 0 && last)
+      cstage<T, n, R, NS, TWS, NL, NT, LF, DIR, ALIAS>(src, dst, tw);
+    else if constexpr (S == 0)
       cstage<T, n, R, NS, TWS, NL, NT, LF, DIR, ALIAS>(src, B, tw);
+    else if constexpr (last)
+      cstage<T, n, R, NS, TWS, NL, NT, LF, DIR, true>(B, dst, tw);
     else
       cstage<T, n, R, NS, TWS, NL, NT, LF, DIR, true>(B, B, tw);
-    if constexpr (S + 1 < P.nst) {
+    if constexpr (!last) {
       __syncthreads();
-      CStagesIP<T, n, TWS, NL, NT, LF, DIR, ALIAS, S + 1, NS * R>::run(src, B, tw);
+      CStagesIP<T, n, TWS, NL, NT, LF, DIR, ALIAS, S + 1, NS * R, MR>::run(src, B, dst, tw);
     }
   }
 };
 
-template <typename T, int n, int TWS, int NL, int NT, bool LF, int DIR, bool ALIAS, class Src>
+template <typename T, int n, int TWS, int NL, int NT, bool LF, int DIR, bool ALIAS,
+          int MR = NS_MAX_RADIX, class Src>
 __device__ __forceinline__ void cfft_ip(const Src& src, cpx<T>* tile, const cpx<T>* __restrict__ tw) {
-  CStagesIP<T, n, TWS, NL, NT, LF, DIR, ALIAS, 0, 1>::run(src, WorkTile<T, n, NL, LF>{tile}, tw);
+  const WorkTile<T, n, NL, LF> B{tile};
+  CStagesIP<T, n, TWS, NL, NT, LF, DIR, ALIAS, 0, 1, MR>::run(src, B, B, tw);
+}
+
+// Same, the last stage writing through dst (which must address the same tile)
+template <typename T, int n, int TWS, int NL, int NT, bool LF, int DIR, bool ALIAS,
+          int MR = NS_MAX_RADIX, class Src, class Dst>
+__device__ __forceinline__ void cfft_ip_to(const Src& src, cpx<T>* tile, const Dst& dst,
+                                           const cpx<T>* __restrict__ tw) {
+  CStagesIP<T, n, TWS, NL, NT, LF, DIR, ALIAS, 0, 1, MR>::run(src, WorkTile<T, n, NL, LF>{tile}, dst, tw);
 }
 
 // copy of the twiddle table into shared memory (all threads of the block participate)

@@ -85,14 +85,38 @@ __device__ __forceinline__ void stage_col_tile(cpx<T>* dst, const cpx<T>* src, i
   }
 }
 
+// Radix cap of each kernel's transforms (pencil z, inverse y, forward y, x rows); 0 = the
+// measured default: in FP32 radix 16 for the forward y and the x rows (one shared-memory pass
+// fewer), radix 8 for the pencil and the inverse y (more threads per tile); 8 in FP64.
+#ifndef NS_RADIX_Z
+#define NS_RADIX_Z 0
+#endif
+#ifndef NS_RADIX_YI
+#define NS_RADIX_YI 0
+#endif
+#ifndef NS_RADIX_YF
+#define NS_RADIX_YF 0
+#endif
+#ifndef NS_RADIX_X
+#define NS_RADIX_X 0
+#endif
+__host__ __device__ constexpr int radix_cap(int set, int f32_default, bool f32) {
+  return set > 0 ? set : (f32 ? f32_default : NS_MAX_RADIX);
+}
+
 template <typename T, int N>
 struct K2Cfg {
   static constexpr int M = N / 2;
   static constexpr int CS = (int)sizeof(cpx<T>);
   static constexpr int MINW = 32 / CS;  // 32-byte global segments
+  static constexpr bool F32 = sizeof(T) == 4;
+  static constexpr int RZ = radix_cap(NS_RADIX_Z, NS_MAX_RADIX, F32);
+  static constexpr int RYI = radix_cap(NS_RADIX_YI, NS_MAX_RADIX, F32);
+  static constexpr int RYF = radix_cap(NS_RADIX_YF, 16, F32);
+  static constexpr int RXR = radix_cap(NS_RADIX_X, 16, F32);
   // pencil: TX columns of N
   static constexpr int TX = pick_div(M, cmax(16384 / (N * CS), MINW), 16);
-  static constexpr int NTP = round_lines(TX * N / NS_MAX_RADIX, TX);
+  static constexpr int NTP = round_lines(TX * N / RZ, TX);
   // blocks per SM the register budget must allow (NS_PENCIL_REGS registers per thread;
   // 80 measured best at 256^3 FP32 on GB300 against 96 and 128)
 #ifndef NS_PENCIL_REGS
@@ -101,13 +125,18 @@ struct K2Cfg {
   static constexpr int MINB_P = cmax(1, cmin(8, 65536 / (NTP * NS_PENCIL_REGS)));
   // y passes: TY columns of N
   static constexpr int TY = pick_div(M, cmax(16384 / (N * CS), MINW), 16);
-  static constexpr int NTY = round_warps(TY * N / NS_MAX_RADIX);
+  static constexpr int NTY = round_warps(TY * N / RYF);
   // inverse y pass: the 5 mixed input tiles are staged in shared memory (6 tiles in all)
-  static constexpr int TYI = pick_div(M, cmax(110000 / (6 * N * CS), MINW), 16);
-  static constexpr int NTYI = round_warps(TYI * N / NS_MAX_RADIX);
+#ifndef NS_YI_LINES
+#define NS_YI_LINES 0
+#endif
+  static constexpr int TYI = (NS_YI_LINES > 0 && M % NS_YI_LINES == 0 && NS_YI_LINES % MINW == 0)
+                                 ? NS_YI_LINES
+                                 : pick_div(M, cmax(110000 / (6 * N * CS), MINW), 16);
+  static constexpr int NTYI = round_warps(TYI * N / RYI);
   // x rows: RX rows of M, processed three fields at a time
   static constexpr int RX = cmin(cmax(8192 / (M * CS), 1), 16);
-  static constexpr int NTX = round_warps(3 * RX * M / NS_MAX_RADIX);
+  static constexpr int NTX = round_warps(3 * RX * M / RXR);
   static constexpr int XLS = WorkTile<T, M, 3 * RX, false>::LS;
   static constexpr int XBUF = 3 * RX * XLS;  // elements of one 3-field row buffer
   static __host__ __device__ constexpr int pencil_tiles(int nF) { return nF > 1 ? 5 : 4; }
@@ -257,12 +286,115 @@ __device__ __forceinline__ void shell_record(const PencilArgs<T>& a, int c, int 
 template <typename T, int N>
 __host__ __device__ constexpr int pencil_tiles(int nF, int nOut) { return (nF > 1 || nOut > 1) ? 4 : 3; }
 
-// ONE: the tile has one input and one output (a.nF == 1, a.nOut == 1) -- every RK2, Rogallo
-// and RK4 stage -- known at compile time, which keeps the kernel free of register spills.
-template <typename T, int N, class MP, bool ONE = false>
+// Last-stage output of a forward z transform of one input component: de-shift by
+// e^{-i k.delta} (the kx, ky factor cxy is the thread's own: the thread's line is fixed) and
+// the weight w.
+template <typename T, int W, class MP>
+struct DeshiftOut {
+  cpx<T>* p;
+  cpx<T> cxy;
+  const cpx<T>* dz;  // z factors of the shift table, or null (no shift)
+  T w;
+  __device__ __forceinline__ void put(int line, int e, cpx<T> v) const {
+    if (dz) v = mul_conj(v, cxy * MP::ld(&dz[e]));
+    p[e * W + line] = w * v;
+  }
+};
+
+// Spectral stage of a pencil tile with one input: the three components of F are staged,
+// transformed in place (the last stage de-shifting and weighting), then one pass per mode
+// applies N(0) = 0, truncation, projection and forcing and the RK stage combine of all three
+// components, leaving S_next (shifted for the output when there is one output) in the tiles.
+template <typename T, int N, class MP>
+__device__ __forceinline__ void pencil_spectral_one(const PencilArgs<T>& a, cpx<T>* buf, cpx<T>* tws,
+                                                    int iy, int x0, int nOut) {
+  using C = K2Cfg<T, N>;
+  constexpr int M = N / 2, TX = C::TX, NT = C::NTP, tile = N * TX;
+  constexpr int PER = (tile + NT - 1) / NT;
+  constexpr int DZ = NT / TX;
+  const size_t fstride = (size_t)N * N * M;
+  const int ky = kof(iy, N);
+  const bool act = threadIdx.x < NT;
+  const int line = threadIdx.x % TX, kx = x0 + line;
+  const int iz0 = threadIdx.x / TX;
+  for (int c = 0; c < 3; ++c) stage_col_tile<T, N, TX, NT>(buf + c * tile, a.F[0] + c * fstride, iy, x0);
+  load_twiddles(tws, a.tw, N);
+  cp_async_wait_all();
+  __syncthreads();
+  const cpx<T>* dz = a.dsh[0] ? a.dsh[0] + 2 * N : nullptr;
+  cpx<T> d0 = mk<T>(1, 0);
+  if (dz) d0 = MP::ld(&a.dsh[0][kx]) * MP::ld(&a.dsh[0][N + iy]);
+  for (int c = 0; c < 3; ++c) {
+    cpx<T>* t = buf + c * tile;
+    cfft_ip_to<T, N, 1, TX, NT, true, -1, true, C::RZ>(SmTile<T, TX>{t}, t,
+                                                       DeshiftOut<T, TX, MP>{t, d0, dz, a.wF[0]}, tws);
+  }
+  __syncthreads();
+
+  const bool pre = nOut == 1 && a.osh[0] != nullptr;
+  cpx<T> oxy = mk<T>(1, 0);
+  if (pre) oxy = MP::ld(&a.osh[0][kx]) * MP::ld(&a.osh[0][N + iy]);
+  const bool useE = a.mode != MODE_INIT && a.mode != MODE_NL && a.mode != MODE_PROJECT;
+  T e1xy = 1, ehxy = 1;
+  if (useE) {
+    e1xy = a.ifac[kx] * a.ifac[iy];
+    ehxy = a.ifac[N + kx] * a.ifac[N + iy];
+  }
+  if (act) {
+    constexpr int CHK = PER < 4 ? PER : 4;  // modes whose state loads are in flight together
+    const bool rd0 = a.mode != MODE_NL && a.mode != MODE_PROJECT;
+    const bool rd1 = a.mode == MODE_RK4_2 || a.mode == MODE_RK4_3;
+    const cpx<T>* base0 = a.mode == MODE_RK4_4 ? a.acc : a.state;
+    const size_t gxy = (size_t)iy * M + kx;
+    for (int i0 = 0; i0 < PER; i0 += CHK) {
+      cpx<T> s0[3][CHK];  // (the RK4 accumulator, read by two modes only, is loaded on use)
+#pragma unroll
+      for (int j = 0; j < CHK; ++j) {
+        const int iz = iz0 + (i0 + j) * DZ;
+        const size_t g = gxy + (size_t)iz * N * M;
+        const bool ok = iz < N && i0 + j < PER;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          s0[c][j] = mk<T>(0, 0);
+          if (ok && rd0) s0[c][j] = MP::ldw(&base0[c * fstride + g]);
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < CHK; ++j) {
+        const int iz = iz0 + (i0 + j) * DZ, e = iz * TX + line;
+        if (iz >= N || i0 + j >= PER) break;
+        const size_t g = gxy + (size_t)iz * N * M;
+        const int kz = kof(iz, N);
+        cpx<T> nv[3] = {buf[e], buf[tile + e], buf[2 * tile + e]};
+        project_point(a, kx, ky, kz, nv);
+        T E1 = 1, Eh = 1;
+        if (useE) {
+          E1 = e1xy * a.ifac[iz];
+          Eh = ehxy * a.ifac[N + iz];
+        }
+        cpx<T> shz = oxy;
+        if (pre) shz = oxy * MP::ld(&a.osh[0][2 * N + iz]);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const cpx<T> s1 = rd1 ? MP::ldw(&a.acc[c * fstride + g]) : mk<T>(0, 0);
+          cpx<T> sn = stage_combine<T, MP>(a, c, c * fstride + g, nv[c], s0[c][j], s1, E1, Eh);
+          shell_record<T, MP>(a, c, kx, ky, kz, sn);
+          if (pre) sn = sn * shz;
+          buf[c * tile + e] = sn;
+        }
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// NFC, NOC: the number of inputs and outputs known at compile time (-1: read from the
+// arguments).  (1, 1) is every RK2, Rogallo and RK4 stage, (2, 2) the exact scheme's stage;
+// fixing them keeps those kernels free of register spills.
+template <typename T, int N, class MP, int NFC = -1, int NOC = -1>
 __device__ __forceinline__ void pencil_tile(const PencilArgs<T>& a, int tile_id, cpx<T>* buf) {
   using C = K2Cfg<T, N>;
-  const int nF = ONE ? 1 : a.nF, nOut = ONE ? 1 : a.nOut;
+  const int nF = NFC >= 0 ? NFC : a.nF, nOut = NOC >= 0 ? NOC : a.nOut;
   constexpr int M = N / 2, TX = C::TX, NT = C::NTP, tile = N * TX;
   constexpr int PER = (tile + NT - 1) / NT;  // modes per thread (the last may not exist)
   static_assert(NT % TX == 0, "every thread keeps one kx");
@@ -280,118 +412,122 @@ __device__ __forceinline__ void pencil_tile(const PencilArgs<T>& a, int tile_id,
   const int iz0 = threadIdx.x / TX;  // this thread's modes: iz = iz0 + i * (NT / TX)
   constexpr int DZ = NT / TX;
 
-  // 1) inputs: all three components staged asynchronously, then transformed in place
-  if (nF > 0) {
-    for (int c = 0; c < 3; ++c) stage_col_tile<T, N, TX, NT>(bc(c), a.F[0] + c * fstride, iy, x0);
-  }
-  load_twiddles(tws, a.tw, N);  // also the barrier after which the staged tiles may be read
-  if (nF > 0) {
-    cp_async_wait_all();
-    __syncthreads();
-    cpx<T> d0 = mk<T>(1, 0), d1 = mk<T>(1, 0);
-    if (a.dsh[0]) d0 = MP::ld(&a.dsh[0][kx]) * MP::ld(&a.dsh[0][N + iy]);
-    if (nF > 1 && a.dsh[1]) d1 = MP::ld(&a.dsh[1][kx]) * MP::ld(&a.dsh[1][N + iy]);
-    for (int c = 0; c < 3; ++c) {
-      cfft_ip<T, N, 1, TX, NT, true, -1, true>(SmTile<T, TX>{bc(c)}, bc(c), tws);
+  const bool pre = nOut == 1 && a.osh[0] != nullptr;  // S_next is shifted in the tiles
+  if constexpr (NFC == 1) {
+    pencil_spectral_one<T, N, MP>(a, buf, tws, iy, x0, nOut);
+  } else {
+    // 1) inputs: all three components staged asynchronously, then transformed in place
+    if (nF > 0) {
+      for (int c = 0; c < 3; ++c) stage_col_tile<T, N, TX, NT>(bc(c), a.F[0] + c * fstride, iy, x0);
+    }
+    load_twiddles(tws, a.tw, N);  // also the barrier after which the staged tiles may be read
+    if (nF > 0) {
+      cp_async_wait_all();
       __syncthreads();
-      if (nF > 1) {
-        stage_col_tile<T, N, TX, NT>(b3, a.F[1] + c * fstride, iy, x0);
-        cp_async_wait_all();
+      cpx<T> d0 = mk<T>(1, 0), d1 = mk<T>(1, 0);
+      if (a.dsh[0]) d0 = MP::ld(&a.dsh[0][kx]) * MP::ld(&a.dsh[0][N + iy]);
+      if (nF > 1 && a.dsh[1]) d1 = MP::ld(&a.dsh[1][kx]) * MP::ld(&a.dsh[1][N + iy]);
+      for (int c = 0; c < 3; ++c) {
+        cfft_ip<T, N, 1, TX, NT, true, -1, true, C::RZ>(SmTile<T, TX>{bc(c)}, bc(c), tws);
         __syncthreads();
-        cfft_ip<T, N, 1, TX, NT, true, -1, true>(SmTile<T, TX>{b3}, b3, tws);
+        if (nF > 1) {
+          stage_col_tile<T, N, TX, NT>(b3, a.F[1] + c * fstride, iy, x0);
+          cp_async_wait_all();
+          __syncthreads();
+          cfft_ip<T, N, 1, TX, NT, true, -1, true, C::RZ>(SmTile<T, TX>{b3}, b3, tws);
+          __syncthreads();
+        }
+        if (act) {
+  #pragma unroll 4
+          for (int i = 0; i < PER; ++i) {
+            const int iz = iz0 + i * DZ, e = iz * TX + line;
+            if (iz >= N) break;
+            cpx<T> v = bc(c)[e];
+            if (a.dsh[0]) v = mul_conj(v, d0 * MP::ld(&a.dsh[0][2 * N + iz]));
+            v = a.wF[0] * v;
+            if (nF > 1) {
+              cpx<T> w = b3[e];
+              if (a.dsh[1]) w = mul_conj(w, d1 * MP::ld(&a.dsh[1][2 * N + iz]));
+              v = v + a.wF[1] * w;
+            }
+            bc(c)[e] = v;
+          }
+        }
         __syncthreads();
       }
+      // 2a) N(0) = 0, truncation, projection, forcing (all components of a mode at once)
       if (act) {
-#pragma unroll 4
         for (int i = 0; i < PER; ++i) {
           const int iz = iz0 + i * DZ, e = iz * TX + line;
           if (iz >= N) break;
-          cpx<T> v = bc(c)[e];
-          if (a.dsh[0]) v = mul_conj(v, d0 * MP::ld(&a.dsh[0][2 * N + iz]));
-          v = a.wF[0] * v;
-          if (nF > 1) {
-            cpx<T> w = b3[e];
-            if (a.dsh[1]) w = mul_conj(w, d1 * MP::ld(&a.dsh[1][2 * N + iz]));
-            v = v + a.wF[1] * w;
-          }
-          bc(c)[e] = v;
+          cpx<T> nv[3] = {bc(0)[e], bc(1)[e], bc(2)[e]};
+          project_point(a, kx, ky, kof(iz, N), nv);
+          bc(0)[e] = nv[0];
+          bc(1)[e] = nv[1];
+          bc(2)[e] = nv[2];
         }
       }
-      __syncthreads();
     }
-    // 2a) N(0) = 0, truncation, projection, forcing (all components of a mode at once)
-    if (act) {
-      for (int i = 0; i < PER; ++i) {
-        const int iz = iz0 + i * DZ, e = iz * TX + line;
-        if (iz >= N) break;
-        cpx<T> nv[3] = {bc(0)[e], bc(1)[e], bc(2)[e]};
-        project_point(a, kx, ky, kof(iz, N), nv);
-        bc(0)[e] = nv[0];
-        bc(1)[e] = nv[1];
-        bc(2)[e] = nv[2];
-      }
-    }
-  }
 
-  // 2b) stage combine per component, the state of the thread's modes loaded together
-  const bool pre = nOut == 1 && a.osh[0] != nullptr;
-  cpx<T> oxy = mk<T>(1, 0);
-  if (pre) oxy = MP::ld(&a.osh[0][kx]) * MP::ld(&a.osh[0][N + iy]);
-  const bool useE = a.mode != MODE_INIT && a.mode != MODE_NL && a.mode != MODE_PROJECT;
-  T e1xy = 1, ehxy = 1;
-  if (useE) {
-    e1xy = a.ifac[kx] * a.ifac[iy];
-    ehxy = a.ifac[N + kx] * a.ifac[N + iy];
-  }
-  if (act) {
-    constexpr int CHK = PER < 8 ? PER : 8;  // modes whose state loads are in flight together
-    const bool rd0 = a.mode != MODE_NL && a.mode != MODE_PROJECT;
-    const bool rd1 = a.mode == MODE_RK4_2 || a.mode == MODE_RK4_3;
-    const cpx<T>* base0 = a.mode == MODE_INIT ? a.src : (a.mode == MODE_RK4_4 ? a.acc : a.state);
-    for (int c = 0; c < 3; ++c)
-    for (int i0 = 0; i0 < PER; i0 += CHK) {
-      const size_t gc = c * fstride + (size_t)iy * M + kx;
-      cpx<T> s0[CHK], s1[CHK];
-#pragma unroll
-      for (int j = 0; j < CHK; ++j) {
-        const int iz = iz0 + (i0 + j) * DZ;
-        const size_t g = gc + (size_t)iz * N * M;
-        s0[j] = s1[j] = mk<T>(0, 0);
-        if (iz < N && i0 + j < PER) {
-          if (rd0) s0[j] = MP::ldw(&base0[g]);
-          if (rd1) s1[j] = MP::ldw(&a.acc[g]);
+    // 2b) stage combine per component, the state of the thread's modes loaded together
+    cpx<T> oxy = mk<T>(1, 0);
+    if (pre) oxy = MP::ld(&a.osh[0][kx]) * MP::ld(&a.osh[0][N + iy]);
+    const bool useE = a.mode != MODE_INIT && a.mode != MODE_NL && a.mode != MODE_PROJECT;
+    T e1xy = 1, ehxy = 1;
+    if (useE) {
+      e1xy = a.ifac[kx] * a.ifac[iy];
+      ehxy = a.ifac[N + kx] * a.ifac[N + iy];
+    }
+    if (act) {
+      constexpr int CHK = PER < 8 ? PER : 8;  // modes whose state loads are in flight together
+      const bool rd0 = a.mode != MODE_NL && a.mode != MODE_PROJECT;
+      const bool rd1 = a.mode == MODE_RK4_2 || a.mode == MODE_RK4_3;
+      const cpx<T>* base0 = a.mode == MODE_INIT ? a.src : (a.mode == MODE_RK4_4 ? a.acc : a.state);
+      for (int c = 0; c < 3; ++c)
+      for (int i0 = 0; i0 < PER; i0 += CHK) {
+        const size_t gc = c * fstride + (size_t)iy * M + kx;
+        cpx<T> s0[CHK], s1[CHK];
+  #pragma unroll
+        for (int j = 0; j < CHK; ++j) {
+          const int iz = iz0 + (i0 + j) * DZ;
+          const size_t g = gc + (size_t)iz * N * M;
+          s0[j] = s1[j] = mk<T>(0, 0);
+          if (iz < N && i0 + j < PER) {
+            if (rd0) s0[j] = MP::ldw(&base0[g]);
+            if (rd1) s1[j] = MP::ldw(&a.acc[g]);
+          }
         }
-      }
-#pragma unroll
-      for (int j = 0; j < CHK; ++j) {
-        const int iz = iz0 + (i0 + j) * DZ, e = iz * TX + line;
-        if (iz >= N || i0 + j >= PER) break;
-        const size_t g = gc + (size_t)iz * N * M;
-        T E1 = 1, Eh = 1;
-        if (useE) {
-          E1 = e1xy * a.ifac[iz];
-          Eh = ehxy * a.ifac[N + iz];
+  #pragma unroll
+        for (int j = 0; j < CHK; ++j) {
+          const int iz = iz0 + (i0 + j) * DZ, e = iz * TX + line;
+          if (iz >= N || i0 + j >= PER) break;
+          const size_t g = gc + (size_t)iz * N * M;
+          T E1 = 1, Eh = 1;
+          if (useE) {
+            E1 = e1xy * a.ifac[iz];
+            Eh = ehxy * a.ifac[N + iz];
+          }
+          const cpx<T> n = nF > 0 ? bc(c)[e] : mk<T>(0, 0);
+          cpx<T> sn = stage_combine<T, MP>(a, c, g, n, s0[j], s1[j], E1, Eh);
+          shell_record<T, MP>(a, c, kx, ky, kof(iz, N), sn);
+          if (pre) sn = sn * (oxy * MP::ld(&a.osh[0][2 * N + iz]));
+          bc(c)[e] = sn;
         }
-        const cpx<T> n = nF > 0 ? bc(c)[e] : mk<T>(0, 0);
-        cpx<T> sn = stage_combine<T, MP>(a, c, g, n, s0[j], s1[j], E1, Eh);
-        shell_record<T, MP>(a, c, kx, ky, kof(iz, N), sn);
-        if (pre) sn = sn * (oxy * MP::ld(&a.osh[0][2 * N + iz]));
-        bc(c)[e] = sn;
       }
     }
+    __syncthreads();
   }
-  __syncthreads();
 
   if (nOut == 1) {
     // u_z first (its tile then serves as the work tile), then u_x, d_z u_x, u_y, d_z u_y
     const cpx<T>* sh = pre ? nullptr : a.osh[0];
-    cfft_src_in_work<T, N, 1, TX, NT, true, 1>(PencilOutSrc<T, N, TX, MP>{bc(2), sh, iy, x0, false},
+    cfft_src_in_work<T, N, 1, TX, NT, true, 1, C::RZ>(PencilOutSrc<T, N, TX, MP>{bc(2), sh, iy, x0, false},
                                                ColOut<T, N, TX, MP>{a.out[0] + 2 * fstride, iy, x0},
                                                bc(2), tws);
     __syncthreads();
     for (int i = 0; i < 4; ++i) {
       const int f = (i & 1) ? 3 + (i >> 1) : (i >> 1), c = f < 3 ? f : f - 3;  // 0, 3, 1, 4
-      cfft<T, N, 1, TX, NT, true, 1>(PencilOutSrc<T, N, TX, MP>{bc(c), sh, iy, x0, f >= 3},
+      cfft<T, N, 1, TX, NT, true, 1, C::RZ>(PencilOutSrc<T, N, TX, MP>{bc(c), sh, iy, x0, f >= 3},
                                      ColOut<T, N, TX, MP>{a.out[0] + f * fstride, iy, x0}, bc(2), tws);
       __syncthreads();
     }
@@ -399,7 +535,7 @@ __device__ __forceinline__ void pencil_tile(const PencilArgs<T>& a, int tile_id,
     for (int o = 0; o < nOut; ++o) {
       for (int f = 0; f < 5; ++f) {
         const int c = f < 3 ? f : f - 3;
-        cfft<T, N, 1, TX, NT, true, 1>(PencilOutSrc<T, N, TX, MP>{bc(c), a.osh[o], iy, x0, f >= 3},
+        cfft<T, N, 1, TX, NT, true, 1, C::RZ>(PencilOutSrc<T, N, TX, MP>{bc(c), a.osh[o], iy, x0, f >= 3},
                                        ColOut<T, N, TX, MP>{a.out[o] + f * fstride, iy, x0}, b3, tws);
         __syncthreads();
       }
@@ -407,10 +543,13 @@ __device__ __forceinline__ void pencil_tile(const PencilArgs<T>& a, int tile_id,
   }
 }
 
-template <typename T, int N, bool ONE>
-__global__ void __launch_bounds__(K2Cfg<T, N>::NTP, K2Cfg<T, N>::MINB_P) k2_pencil(PencilArgs<T> a) {
+// the two-input variant holds 4 shared tiles (3 blocks per SM at most): it is given the
+// registers of 2 resident blocks rather than spill
+template <typename T, int N, int NFC, int NOC>
+__global__ void __launch_bounds__(K2Cfg<T, N>::NTP, NFC == 2 ? cmin(2, K2Cfg<T, N>::MINB_P) : K2Cfg<T, N>::MINB_P)
+    k2_pencil(PencilArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  pencil_tile<T, N, MemNC, ONE>(a, blockIdx.x, reinterpret_cast<cpx<T>*>(smem_raw));
+  pencil_tile<T, N, MemNC, NFC, NOC>(a, blockIdx.x, reinterpret_cast<cpx<T>*>(smem_raw));
 }
 
 // ---- slab pass: y transforms --------------------------------------------------------
@@ -448,7 +587,7 @@ template <typename T, int N, int F, class MP>
 __device__ __forceinline__ void yinv_field(const SlabArgs<T>& a, const cpx<T>* in, cpx<T>* W,
                                            int zg, int x0, size_t sstride, const cpx<T>* tws) {
   using C = K2Cfg<T, N>;
-  cfft<T, N, 1, C::TYI, C::NTYI, true, 1>(YInvSrc<T, N, F, C::TYI>{in, x0},
+  cfft<T, N, 1, C::TYI, C::NTYI, true, 1, C::RYI>(YInvSrc<T, N, F, C::TYI>{in, x0},
                                           ScrCol<T, N, MP>{a.scr + F * sstride, zg, x0}, W, tws);
   __syncthreads();
 }
@@ -490,7 +629,7 @@ __device__ __forceinline__ void yfwd_tile(const SlabArgs<T>& a, int tx, int zg, 
   cpx<T>* tws = W + N * C::TY;
   load_twiddles(tws, a.tw, N);
   for (int f = 0; f < 3; ++f) {
-    cfft<T, N, 1, C::TY, C::NTY, true, -1>(ScrCol<T, N, MP>{a.scr + f * sstride, zg, x0},
+    cfft<T, N, 1, C::TY, C::NTY, true, -1, C::RYF>(ScrCol<T, N, MP>{a.scr + f * sstride, zg, x0},
                                            ScrCol<T, N, MP>{a.Ft + f * fstride, z, x0}, W, tws);
     __syncthreads();
   }
@@ -518,42 +657,50 @@ __device__ __forceinline__ void xrow_tile(const SlabArgs<T>& a, int tile_id, cpx
   const int r0 = tile_id * RX;
   const int nr = min(RX, rows_total - r0);
   const size_t sstride = (size_t)a.G * N * M;
-  constexpr int NP = M / 2 + 1;  // pairs (k, M-k), k = 0..M/2
 
-  // load the 6 fields with the c2r pre-processing (Hermitian half row -> packed Z')
-  for (int i = threadIdx.x; act && i < 6 * RX * NP; i += NT) {
-    const int f = i / (RX * NP), rem = i % (RX * NP), row = rem / NP, k = rem % NP;
-    const RowT& B = f < 3 ? U : V;
-    const int line = (f % 3) * RX + row;
-    if (row >= nr) {
-      if (k == 0 || k < M - k) {
-        B.put(line, k, mk<T>(0, 0));
-        if (k != 0) B.put(line, M - k, mk<T>(0, 0));
-        if (k == 0 && M % 2 == 0 && M > 1) B.put(line, M / 2, mk<T>(0, 0));
+  // load the 6 fields with the c2r pre-processing (Hermitian half row -> packed Z'): item
+  // (f, row, k) handles k = 0 with M/2, or the pair (k, M - k); each thread issues all of its
+  // loads before any arithmetic.  Rows past the end of the group are zero-filled.
+  static_assert(M % 2 == 0, "x rows of even length");
+  constexpr int H = M / 2;
+  constexpr int NI = 6 * RX * H, KI = (NI + NT - 1) / NT;
+  cpx<T> xa[KI], xb[KI];
+#pragma unroll
+  for (int c = 0; c < KI; ++c) {
+    const int i = threadIdx.x + c * NT;
+    xa[c] = xb[c] = mk<T>(0, 0);
+    if (act && (NI % NT == 0 || i < NI)) {
+      const int f = i / (RX * H), row = (i / H) % RX, k = i % H;
+      if (row < nr) {
+        const cpx<T>* src = a.scr + f * sstride + (size_t)(r0 + row) * M;
+        xa[c] = MP::ld(&src[k]);
+        xb[c] = MP::ld(&src[k == 0 ? H : M - k]);
       }
-      continue;
     }
-    const cpx<T>* src = a.scr + f * sstride + (size_t)(r0 + row) * M;
-    if (k == 0) {
-      const T r = MP::ld(&src[0]).x;
-      B.put(line, 0, mk<T>(r, r));
-      if (M % 2 == 0 && M > 1) {
-        const cpx<T> X = MP::ld(&src[M / 2]);
-        B.put(line, M / 2, (X + conjg(X)) - (X - conjg(X)));
+  }
+#pragma unroll
+  for (int c = 0; c < KI; ++c) {
+    const int i = threadIdx.x + c * NT;
+    if (act && (NI % NT == 0 || i < NI)) {
+      const int f = i / (RX * H), row = (i / H) % RX, k = i % H;
+      const int line = f * RX + row;
+      const WorkTile<T, M, 6 * RX, false> B{buf};  // U then V: field f, row r is line f RX + r
+      if (k == 0) {
+        B.put(line, 0, mk<T>(xa[c].x, xa[c].x));
+        B.put(line, H, (xb[c] + conjg(xb[c])) - (xb[c] - conjg(xb[c])));
+      } else {
+        const cpx<T> Xk = xa[c], Xm = xb[c];
+        const cpx<T> tk = tws[k];
+        const cpx<T> A = Xk + conjg(Xm), Bv = Xk - conjg(Xm);
+        B.put(line, k, A + mul_si(conjg(tk) * Bv, T(1)));
+        const cpx<T> A2 = Xm + conjg(Xk), B2 = Xm - conjg(Xk);
+        B.put(line, M - k, A2 - mul_si(tk * B2, T(1)));
       }
-    } else if (k < M - k) {
-      const cpx<T> Xk = MP::ld(&src[k]), Xm = MP::ld(&src[M - k]);
-      const cpx<T> tk = tws[k];
-      const cpx<T> A = Xk + conjg(Xm), Bv = Xk - conjg(Xm);
-      B.put(line, k, A + mul_si(conjg(tk) * Bv, T(1)));
-      const cpx<T> A2 = Xm + conjg(Xk), B2 = Xm - conjg(Xk);
-      B.put(line, M - k, A2 - mul_si(tk * B2, T(1)));
     }
   }
   __syncthreads();
-  cfft_ip<T, M, 2, 3 * RX, NT, false, 1, true>(U, U.p, tws);
-  __syncthreads();
-  cfft_ip<T, M, 2, 3 * RX, NT, false, 1, true>(V, V.p, tws);
+  // the six inverse transforms in one in-place call (lines 0 .. 6 RX - 1)
+  cfft_ip<T, M, 2, 6 * RX, NT, false, 1, true, C::RXR>(WorkTile<T, M, 6 * RX, false>{buf}, buf, tws);
   __syncthreads();
 
   // u x omega on the packed real rows, written over u
@@ -574,23 +721,23 @@ __device__ __forceinline__ void xrow_tile(const SlabArgs<T>& a, int tile_id, cpx
     U.put(2 * RX + row, k, f2);
   }
   __syncthreads();
-  cfft_ip<T, M, 2, 3 * RX, NT, false, -1, true>(U, U.p, tws);
+  cfft_ip<T, M, 2, 3 * RX, NT, false, -1, true, C::RXR>(U, U.p, tws);
   __syncthreads();
 
-  // r2c post-processing and store
-  for (int i = threadIdx.x; act && i < 3 * RX * NP; i += NT) {
-    const int f = i / (RX * NP), rem = i % (RX * NP), row = rem / NP, k = rem % NP;
+  // r2c post-processing and store: item (f, row, k) writes k = 0 with M/2, or the pair
+  // (k, M - k)
+  constexpr int NO = 3 * RX * H;
+  for (int i = threadIdx.x; act && i < NO; i += NT) {
+    const int f = i / (RX * H), row = (i / H) % RX, k = i % H;
     if (row >= nr) continue;
     const int line = f * RX + row;
     cpx<T>* dst = a.scr + f * sstride + (size_t)(r0 + row) * M;
     if (k == 0) {
       const cpx<T> Z = U.get(line, 0);
       MP::st(&dst[0], mk<T>(Z.x + Z.y, T(0)));
-      if (M % 2 == 0 && M > 1) {
-        const cpx<T> Zk = U.get(line, M / 2);
-        MP::st(&dst[M / 2], T(0.5) * ((Zk + conjg(Zk)) - (Zk - conjg(Zk))));
-      }
-    } else if (k < M - k) {
+      const cpx<T> Zk = U.get(line, H);
+      MP::st(&dst[H], T(0.5) * ((Zk + conjg(Zk)) - (Zk - conjg(Zk))));
+    } else {
       const cpx<T> Zk = U.get(line, k), Zm = U.get(line, M - k);
       const cpx<T> Wk = tws[k];
       const cpx<T> A = Zk + conjg(Zm), B = Zk - conjg(Zm);
@@ -613,6 +760,7 @@ struct K2Entry {
   int N = 0;
   void (*pencil)(PencilArgs<T>) = nullptr;   // any number of inputs / outputs
   void (*pencil1)(PencilArgs<T>) = nullptr;  // one input, one output
+  void (*pencil2)(PencilArgs<T>) = nullptr;  // two inputs, two outputs
   void (*yinv)(SlabArgs<T>) = nullptr;
   void (*yfwd)(SlabArgs<T>) = nullptr;
   void (*xrow)(SlabArgs<T>) = nullptr;
@@ -625,8 +773,13 @@ K2Entry<T> make_k2_entry() {
   using C = K2Cfg<T, N>;
   K2Entry<T> e;
   e.N = N;
-  e.pencil = k2_pencil<T, N, false>;
-  e.pencil1 = k2_pencil<T, N, true>;
+  e.pencil = k2_pencil<T, N, -1, -1>;
+#ifndef NS_PENCIL_VARIANTS
+#define NS_PENCIL_VARIANTS 1
+#endif
+  // NS_PENCIL_VARIANTS=0 routes every pencil pass through the generic kernel (comparisons)
+  e.pencil1 = NS_PENCIL_VARIANTS ? k2_pencil<T, N, 1, 1> : e.pencil;
+  e.pencil2 = NS_PENCIL_VARIANTS ? k2_pencil<T, N, 2, 2> : e.pencil;
   e.yinv = k2_yinv<T, N>;
   e.yfwd = k2_yfwd<T, N>;
   e.xrow = k2_xrow<T, N>;
