@@ -69,6 +69,12 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
 __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.commit_group;\ncp.async.wait_all;\n" ::: "memory");
 }
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+// wait until at most P of this thread's committed groups are still in flight
+template <int P>
+__device__ __forceinline__ void cp_async_wait_pending() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(P) : "memory");
+}
 // Stage a column tile [e][line] (W lines, n elements) of a [z|kz][ky][kx] field from global
 // memory; W * sizeof(cpx<T>) is a multiple of 16 bytes and x0 a multiple of W.
 // PLANE: the tile of a fixed plane p of a [p][e][kx] field (element e = ky or y) instead.
@@ -286,6 +292,34 @@ __device__ __forceinline__ void shell_record(const PencilArgs<T>& a, int c, int 
 template <typename T, int N>
 __host__ __device__ constexpr int pencil_tiles(int nF, int nOut) { return (nF > 1 || nOut > 1) ? 4 : 3; }
 
+// True when every mode of a pencil tile (kx in [x0, x0 + TX), this ky, every kz) lies outside
+// the truncation and none is in the forcing table: the truncated nonlinear term and the
+// forcing vanish there, so the tile's forward transforms are skipped (Sec. 2, truncation).
+template <typename T, int TX>
+__device__ __forceinline__ bool pencil_tile_truncated(const PencilArgs<T>& a, int x0, int ky) {
+  bool out;
+  if (a.trunc == 1)
+    out = x0 > a.Kimax || abs(ky) > a.Kimax;
+  else
+    out = (long long)x0 * x0 + (long long)ky * ky > (long long)a.K2max;
+  const bool forced = (a.force != nullptr || a.shell != nullptr) && x0 <= a.fK && abs(ky) <= a.fK;
+  return out && !forced;
+}
+
+// Zero columns of the outputs of a tile whose S_next vanishes (the inverse transforms of zero)
+template <typename T, int N, int TX, int NT, class MP>
+__device__ __forceinline__ void pencil_zero_outputs(const PencilArgs<T>& a, int nOut, int iy, int x0) {
+  constexpr int M = N / 2;
+  const size_t fstride = (size_t)N * N * M;
+  if (threadIdx.x >= NT) return;
+  for (int o = 0; o < nOut; ++o)
+    for (int f = 0; f < 5; ++f)
+      for (int i = threadIdx.x; i < N * TX; i += NT) {
+        const int iz = i / TX, line = i % TX;
+        MP::st(&a.out[o][f * fstride + ((size_t)iz * N + iy) * M + x0 + line], mk<T>(0, 0));
+      }
+}
+
 // Last-stage output of a forward z transform of one input component: de-shift by
 // e^{-i k.delta} (the kx, ky factor cxy is the thread's own: the thread's line is fixed) and
 // the weight w.
@@ -307,7 +341,7 @@ struct DeshiftOut {
 // components, leaving S_next (shifted for the output when there is one output) in the tiles.
 template <typename T, int N, class MP>
 __device__ __forceinline__ void pencil_spectral_one(const PencilArgs<T>& a, cpx<T>* buf, cpx<T>* tws,
-                                                    int iy, int x0, int nOut) {
+                                                    int iy, int x0, int nOut, bool tz) {
   using C = K2Cfg<T, N>;
   constexpr int M = N / 2, TX = C::TX, NT = C::NTP, tile = N * TX;
   constexpr int PER = (tile + NT - 1) / NT;
@@ -317,19 +351,22 @@ __device__ __forceinline__ void pencil_spectral_one(const PencilArgs<T>& a, cpx<
   const bool act = threadIdx.x < NT;
   const int line = threadIdx.x % TX, kx = x0 + line;
   const int iz0 = threadIdx.x / TX;
-  for (int c = 0; c < 3; ++c) stage_col_tile<T, N, TX, NT>(buf + c * tile, a.F[0] + c * fstride, iy, x0);
+  if (!tz)
+    for (int c = 0; c < 3; ++c) stage_col_tile<T, N, TX, NT>(buf + c * tile, a.F[0] + c * fstride, iy, x0);
   load_twiddles(tws, a.tw, N);
-  cp_async_wait_all();
-  __syncthreads();
-  const cpx<T>* dz = a.dsh[0] ? a.dsh[0] + 2 * N : nullptr;
-  cpx<T> d0 = mk<T>(1, 0);
-  if (dz) d0 = MP::ld(&a.dsh[0][kx]) * MP::ld(&a.dsh[0][N + iy]);
-  for (int c = 0; c < 3; ++c) {
-    cpx<T>* t = buf + c * tile;
-    cfft_ip_to<T, N, 1, TX, NT, true, -1, true, C::RZ>(SmTile<T, TX>{t}, t,
-                                                       DeshiftOut<T, TX, MP>{t, d0, dz, a.wF[0]}, tws);
+  if (!tz) {
+    cp_async_wait_all();
+    __syncthreads();
+    const cpx<T>* dz = a.dsh[0] ? a.dsh[0] + 2 * N : nullptr;
+    cpx<T> d0 = mk<T>(1, 0);
+    if (dz) d0 = MP::ld(&a.dsh[0][kx]) * MP::ld(&a.dsh[0][N + iy]);
+    for (int c = 0; c < 3; ++c) {
+      cpx<T>* t = buf + c * tile;
+      cfft_ip_to<T, N, 1, TX, NT, true, -1, true, C::RZ>(SmTile<T, TX>{t}, t,
+                                                         DeshiftOut<T, TX, MP>{t, d0, dz, a.wF[0]}, tws);
+    }
+    __syncthreads();
   }
-  __syncthreads();
 
   const bool pre = nOut == 1 && a.osh[0] != nullptr;
   cpx<T> oxy = mk<T>(1, 0);
@@ -365,8 +402,13 @@ __device__ __forceinline__ void pencil_spectral_one(const PencilArgs<T>& a, cpx<
         if (iz >= N || i0 + j >= PER) break;
         const size_t g = gxy + (size_t)iz * N * M;
         const int kz = kof(iz, N);
-        cpx<T> nv[3] = {buf[e], buf[tile + e], buf[2 * tile + e]};
-        project_point(a, kx, ky, kz, nv);
+        cpx<T> nv[3] = {mk<T>(0, 0), mk<T>(0, 0), mk<T>(0, 0)};
+        if (!tz) {
+          nv[0] = buf[e];
+          nv[1] = buf[tile + e];
+          nv[2] = buf[2 * tile + e];
+          project_point(a, kx, ky, kz, nv);
+        }
         T E1 = 1, Eh = 1;
         if (useE) {
           E1 = e1xy * a.ifac[iz];
@@ -413,15 +455,18 @@ __device__ __forceinline__ void pencil_tile(const PencilArgs<T>& a, int tile_id,
   constexpr int DZ = NT / TX;
 
   const bool pre = nOut == 1 && a.osh[0] != nullptr;  // S_next is shifted in the tiles
+  const bool tt = pencil_tile_truncated<T, TX>(a, x0, ky);  // N = 0 on the whole tile
+  const bool tz = nF > 0 && tt;                               // so its inputs are not transformed
   if constexpr (NFC == 1) {
-    pencil_spectral_one<T, N, MP>(a, buf, tws, iy, x0, nOut);
+    pencil_spectral_one<T, N, MP>(a, buf, tws, iy, x0, nOut, tz);
   } else {
+    const int nFe = tz ? 0 : nF;  // inputs that are transformed
     // 1) inputs: all three components staged asynchronously, then transformed in place
-    if (nF > 0) {
+    if (nFe > 0) {
       for (int c = 0; c < 3; ++c) stage_col_tile<T, N, TX, NT>(bc(c), a.F[0] + c * fstride, iy, x0);
     }
     load_twiddles(tws, a.tw, N);  // also the barrier after which the staged tiles may be read
-    if (nF > 0) {
+    if (nFe > 0) {
       cp_async_wait_all();
       __syncthreads();
       cpx<T> d0 = mk<T>(1, 0), d1 = mk<T>(1, 0);
@@ -507,7 +552,7 @@ __device__ __forceinline__ void pencil_tile(const PencilArgs<T>& a, int tile_id,
             E1 = e1xy * a.ifac[iz];
             Eh = ehxy * a.ifac[N + iz];
           }
-          const cpx<T> n = nF > 0 ? bc(c)[e] : mk<T>(0, 0);
+          const cpx<T> n = nFe > 0 ? bc(c)[e] : mk<T>(0, 0);
           cpx<T> sn = stage_combine<T, MP>(a, c, g, n, s0[j], s1[j], E1, Eh);
           shell_record<T, MP>(a, c, kx, ky, kof(iz, N), sn);
           if (pre) sn = sn * (oxy * MP::ld(&a.osh[0][2 * N + iz]));
@@ -518,6 +563,22 @@ __device__ __forceinline__ void pencil_tile(const PencilArgs<T>& a, int tile_id,
     __syncthreads();
   }
 
+  if (tt) {  // S_next vanishing on the whole tile (a truncated state): zero outputs, no transforms
+    bool nz = false;
+    if (act)
+      for (int i = 0; i < PER; ++i) {
+        const int iz = iz0 + i * DZ, e = iz * TX + line;
+        if (iz >= N) break;
+        for (int c = 0; c < 3; ++c) {
+          const cpx<T> v = bc(c)[e];
+          nz = nz || v.x != T(0) || v.y != T(0);
+        }
+      }
+    if (!__syncthreads_or(nz)) {
+      pencil_zero_outputs<T, N, TX, NT, MP>(a, nOut, iy, x0);
+      return;
+    }
+  }
   if (nOut == 1) {
     // u_z first (its tile then serves as the work tile), then u_x, d_z u_x, u_y, d_z u_y
     const cpx<T>* sh = pre ? nullptr : a.osh[0];
@@ -602,16 +663,22 @@ __device__ __forceinline__ void yinv_tile(const SlabArgs<T>& a, int tx, int zg, 
   const int x0 = tx * TY, z = a.z0 + zg;
   const size_t sstride = (size_t)a.G * N * M;
   const size_t fs = (size_t)N * N * M;
-  for (int f = 0; f < 5; ++f) stage_col_tile<T, N, TY, NT, true>(in + f * tile, a.mixed + f * fs, z, x0);
+  // two copy groups: u (fields 0-2) first, d_z u_x and d_z u_y (3-4) in flight meanwhile
+  for (int f = 0; f < 3; ++f) stage_col_tile<T, N, TY, NT, true>(in + f * tile, a.mixed + f * fs, z, x0);
+  cp_async_commit();
+  for (int f = 3; f < 5; ++f) stage_col_tile<T, N, TY, NT, true>(in + f * tile, a.mixed + f * fs, z, x0);
+  cp_async_commit();
   for (int i = threadIdx.x; i < N; i += blockDim.x) tws[i] = ldg(&a.tw[i]);
-  cp_async_wait_all();
+  cp_async_wait_pending<1>();
   __syncthreads();
   yinv_field<T, N, 0, MP>(a, in, W, zg, x0, sstride, tws);
   yinv_field<T, N, 1, MP>(a, in, W, zg, x0, sstride, tws);
   yinv_field<T, N, 2, MP>(a, in, W, zg, x0, sstride, tws);
+  yinv_field<T, N, 5, MP>(a, in, W, zg, x0, sstride, tws);  // omega_z: u_x, u_y only
+  cp_async_wait_pending<0>();
+  __syncthreads();
   yinv_field<T, N, 3, MP>(a, in, W, zg, x0, sstride, tws);
   yinv_field<T, N, 4, MP>(a, in, W, zg, x0, sstride, tws);
-  yinv_field<T, N, 5, MP>(a, in, W, zg, x0, sstride, tws);
 }
 
 template <typename T, int N>
