@@ -76,19 +76,76 @@ struct DFT<T, 16> {
   }
 };
 
-// Shared work tile of NL lines of length n.  LF (line-fast) layout [e][line]; otherwise
-// [line][e] with one pad element per 16 to spread the stride-R writes of a stage.
+// Line-fast tiles [e][line] of W lines.  When a row is narrower than the 32 banks of shared
+// memory, rows 8 apart share banks (the radix-8 first stage writes rows 8 j + r); NS_LF_PAD=1
+// inserts one empty row after every 8 (element row e at row lf_row(e) of lf_rows(n)).  Off by
+// default: on GB300 at 256^3 the index arithmetic cost more than the conflicts it removed.
+#ifndef NS_LF_PAD
+#define NS_LF_PAD 0
+#endif
+template <typename T, int W>
+__host__ __device__ constexpr bool lf_padded() { return NS_LF_PAD && W * (int)sizeof(cpx<T>) < 128; }
+template <typename T, int W>
+__host__ __device__ constexpr int lf_rows(int n) { return lf_padded<T, W>() ? n + (n - 1) / 8 : n; }
+template <typename T, int W>
+__host__ __device__ __forceinline__ int lf_row(int e) { return lf_padded<T, W>() ? e + (e >> 3) : e; }
+template <typename T, int W>
+__host__ __device__ __forceinline__ int lf_idx(int e, int line) { return lf_row<T, W>(e) * W + line; }
+
+// Shared work tile of NL lines of length n.  LF (line-fast) layout [e][line] as above;
+// otherwise [line][e] with one pad element per 16 to spread the stride-R writes of a stage.
 template <typename T, int n, int NL, bool LF>
 struct WorkTile {
   cpx<T>* p;
   static constexpr int LS = n + n / 16 + 1;
-  static __host__ __device__ constexpr int elems() { return LF ? n * NL : NL * LS; }
+  static __host__ __device__ constexpr int elems() { return LF ? lf_rows<T, NL>(n) * NL : NL * LS; }
   __device__ __forceinline__ int idx(int line, int e) const {
-    return LF ? e * NL + line : line * LS + e + (e >> 4);
+    return LF ? lf_idx<T, NL>(e, line) : line * LS + e + (e >> 4);
   }
   __device__ __forceinline__ cpx<T> get(int line, int e) const { return p[idx(line, e)]; }
   __device__ __forceinline__ void put(int line, int e, cpx<T> v) const { p[idx(line, e)] = v; }
 };
+
+// Twiddles w[r] = W^(r base) (conjugated when cs = -1), r = 1 .. R-1, of one butterfly.  Only
+// the powers r = 1, 2, 4, 8 are read from the (shared-memory) table; the others are their
+// products, which moves work from the shared-memory pipe to the FMA pipe.
+#ifndef NS_TW_PRODUCTS
+#define NS_TW_PRODUCTS 1
+#endif
+template <typename T, int R>
+__device__ __forceinline__ void stage_twiddles(cpx<T>* w, const cpx<T>* __restrict__ tw, int base, T cs) {
+  auto ld = [&](int r) {
+    cpx<T> v = tw[r * base];
+    v.y *= cs;
+    return v;
+  };
+  if constexpr (R == 2) {
+    w[1] = ld(1);
+  } else if constexpr (R == 3) {
+    w[1] = ld(1);
+    w[2] = ld(2);
+  } else if constexpr (R == 4) {
+    w[1] = ld(1);
+    w[2] = ld(2);
+    w[3] = w[1] * w[2];
+  } else if constexpr ((R == 8 || R == 16) && NS_TW_PRODUCTS) {
+    w[1] = ld(1);
+    w[2] = ld(2);
+    w[4] = ld(4);
+    w[3] = w[1] * w[2];
+    w[5] = w[1] * w[4];
+    w[6] = w[2] * w[4];
+    w[7] = w[3] * w[4];
+    if constexpr (R == 16) {
+      w[8] = ld(8);
+#pragma unroll
+      for (int r = 9; r < 16; ++r) w[r] = w[r - 8] * w[8];
+    }
+  } else {
+#pragma unroll
+    for (int r = 1; r < R; ++r) w[r] = ld(r);
+  }
+}
 
 // One Stockham stage: butterfly j of a line reads elements j + r n/R, applies the
 // twiddles W_{NS R}^{p r} (p = j mod NS), a radix-R DFT, and writes q NS R + p + r NS.
@@ -116,12 +173,10 @@ __device__ __forceinline__ void cstage(const Src& src, const Dst& dst, const cpx
     for (int r = 0; r < R; ++r) v[r] = src.get(line, j + r * NB);
     if (NS > 1) {
       const int base = (j % NS) * TSTEP;
+      cpx<T> w[R];
+      stage_twiddles<T, R>(w, tw, base, -s);
 #pragma unroll
-      for (int r = 1; r < R; ++r) {
-        cpx<T> w = tw[r * base];  // twiddle table (shared-memory copy)
-        w.y *= -s;
-        v[r] = v[r] * w;
-      }
+      for (int r = 1; r < R; ++r) v[r] = v[r] * w[r];
     }
     DFT<T, R>::run(v, s);
   };

@@ -87,7 +87,7 @@ __device__ __forceinline__ void stage_col_tile(cpx<T>* dst, const cpx<T>* src, i
   for (int i = threadIdx.x; i < N * CH; i += NT) {
     const int e = i / CH, xc = (i % CH) * PER;
     const size_t row = PLANE ? (size_t)iy * N + e : (size_t)e * N + iy;
-    cp_async16(&dst[e * W + xc], &src[row * (N / 2) + x0 + xc]);
+    cp_async16(&dst[lf_idx<T, W>(e, xc)], &src[row * (N / 2) + x0 + xc]);
   }
 }
 
@@ -168,8 +168,8 @@ struct ColOut {
 template <typename T, int W>
 struct SmTile {  // shared [e][line]
   cpx<T>* p;
-  __device__ __forceinline__ cpx<T> get(int line, int e) const { return p[e * W + line]; }
-  __device__ __forceinline__ void put(int line, int e, cpx<T> v) const { p[e * W + line] = v; }
+  __device__ __forceinline__ cpx<T> get(int line, int e) const { return p[lf_idx<T, W>(e, line)]; }
+  __device__ __forceinline__ void put(int line, int e, cpx<T> v) const { p[lf_idx<T, W>(e, line)] = v; }
 };
 template <class MP, typename T>
 __device__ __forceinline__ cpx<T> phase3p(const cpx<T>* tab, int N, int ix, int iy, int iz) {
@@ -183,7 +183,7 @@ struct PencilOutSrc {
   int iy, x0;
   bool deriv;
   __device__ __forceinline__ cpx<T> get(int line, int e) const {
-    cpx<T> v = s[e * W + line];
+    cpx<T> v = s[lf_idx<T, W>(e, line)];
     if (sh) v = v * phase3p<MP>(sh, N, x0 + line, iy, e);
     if (deriv) v = mul_si(v, (T)kof(e, N));
     return v;
@@ -331,7 +331,7 @@ struct DeshiftOut {
   T w;
   __device__ __forceinline__ void put(int line, int e, cpx<T> v) const {
     if (dz) v = mul_conj(v, cxy * MP::ld(&dz[e]));
-    p[e * W + line] = w * v;
+    p[lf_idx<T, W>(e, line)] = w * v;
   }
 };
 
@@ -343,7 +343,7 @@ template <typename T, int N, class MP>
 __device__ __forceinline__ void pencil_spectral_one(const PencilArgs<T>& a, cpx<T>* buf, cpx<T>* tws,
                                                     int iy, int x0, int nOut, bool tz) {
   using C = K2Cfg<T, N>;
-  constexpr int M = N / 2, TX = C::TX, NT = C::NTP, tile = N * TX;
+  constexpr int M = N / 2, TX = C::TX, NT = C::NTP, tile = lf_rows<T, C::TX>(N) * TX;
   constexpr int PER = (tile + NT - 1) / NT;
   constexpr int DZ = NT / TX;
   const size_t fstride = (size_t)N * N * M;
@@ -398,7 +398,7 @@ __device__ __forceinline__ void pencil_spectral_one(const PencilArgs<T>& a, cpx<
       }
 #pragma unroll
       for (int j = 0; j < CHK; ++j) {
-        const int iz = iz0 + (i0 + j) * DZ, e = iz * TX + line;
+        const int iz = iz0 + (i0 + j) * DZ, e = lf_idx<T, TX>(iz, line);
         if (iz >= N || i0 + j >= PER) break;
         const size_t g = gxy + (size_t)iz * N * M;
         const int kz = kof(iz, N);
@@ -437,7 +437,7 @@ template <typename T, int N, class MP, int NFC = -1, int NOC = -1>
 __device__ __forceinline__ void pencil_tile(const PencilArgs<T>& a, int tile_id, cpx<T>* buf) {
   using C = K2Cfg<T, N>;
   const int nF = NFC >= 0 ? NFC : a.nF, nOut = NOC >= 0 ? NOC : a.nOut;
-  constexpr int M = N / 2, TX = C::TX, NT = C::NTP, tile = N * TX;
+  constexpr int M = N / 2, TX = C::TX, NT = C::NTP, tile = lf_rows<T, C::TX>(N) * TX;
   constexpr int PER = (tile + NT - 1) / NT;  // modes per thread (the last may not exist)
   static_assert(NT % TX == 0, "every thread keeps one kx");
   // component tile c is buf + c * tile (pointer arithmetic, not an array: no local memory)
@@ -485,7 +485,7 @@ __device__ __forceinline__ void pencil_tile(const PencilArgs<T>& a, int tile_id,
         if (act) {
   #pragma unroll 4
           for (int i = 0; i < PER; ++i) {
-            const int iz = iz0 + i * DZ, e = iz * TX + line;
+            const int iz = iz0 + i * DZ, e = lf_idx<T, TX>(iz, line);
             if (iz >= N) break;
             cpx<T> v = bc(c)[e];
             if (a.dsh[0]) v = mul_conj(v, d0 * MP::ld(&a.dsh[0][2 * N + iz]));
@@ -503,7 +503,7 @@ __device__ __forceinline__ void pencil_tile(const PencilArgs<T>& a, int tile_id,
       // 2a) N(0) = 0, truncation, projection, forcing (all components of a mode at once)
       if (act) {
         for (int i = 0; i < PER; ++i) {
-          const int iz = iz0 + i * DZ, e = iz * TX + line;
+          const int iz = iz0 + i * DZ, e = lf_idx<T, TX>(iz, line);
           if (iz >= N) break;
           cpx<T> nv[3] = {bc(0)[e], bc(1)[e], bc(2)[e]};
           project_point(a, kx, ky, kof(iz, N), nv);
@@ -544,7 +544,7 @@ __device__ __forceinline__ void pencil_tile(const PencilArgs<T>& a, int tile_id,
         }
   #pragma unroll
         for (int j = 0; j < CHK; ++j) {
-          const int iz = iz0 + (i0 + j) * DZ, e = iz * TX + line;
+          const int iz = iz0 + (i0 + j) * DZ, e = lf_idx<T, TX>(iz, line);
           if (iz >= N || i0 + j >= PER) break;
           const size_t g = gc + (size_t)iz * N * M;
           T E1 = 1, Eh = 1;
@@ -567,7 +567,7 @@ __device__ __forceinline__ void pencil_tile(const PencilArgs<T>& a, int tile_id,
     bool nz = false;
     if (act)
       for (int i = 0; i < PER; ++i) {
-        const int iz = iz0 + i * DZ, e = iz * TX + line;
+        const int iz = iz0 + i * DZ, e = lf_idx<T, TX>(iz, line);
         if (iz >= N) break;
         for (int c = 0; c < 3; ++c) {
           const cpx<T> v = bc(c)[e];
@@ -621,8 +621,8 @@ struct YInvSrc {
   const cpx<T>* m;
   int x0;
   __device__ __forceinline__ cpx<T> get(int line, int e) const {
-    constexpr int fs = N * TY;
-    const int i = e * TY + line;
+    constexpr int fs = lf_rows<T, TY>(N) * TY;
+    const int i = lf_idx<T, TY>(e, line);
     const T kx = (T)(x0 + line), ky = (T)kof(e, N);
     if (F == 0) return m[i];
     if (F == 1) return m[i + fs];
@@ -657,7 +657,7 @@ __device__ __forceinline__ void yinv_field(const SlabArgs<T>& a, const cpx<T>* i
 template <typename T, int N, class MP>
 __device__ __forceinline__ void yinv_tile(const SlabArgs<T>& a, int tx, int zg, cpx<T>* in) {
   using C = K2Cfg<T, N>;
-  constexpr int M = N / 2, TY = C::TYI, NT = C::NTYI, tile = N * TY;
+  constexpr int M = N / 2, TY = C::TYI, NT = C::NTYI, tile = lf_rows<T, TY>(N) * TY;
   cpx<T>* W = in + 5 * tile;
   cpx<T>* tws = in + 6 * tile;
   const int x0 = tx * TY, z = a.z0 + zg;
@@ -693,7 +693,7 @@ __device__ __forceinline__ void yfwd_tile(const SlabArgs<T>& a, int tx, int zg, 
   const int x0 = tx * C::TY, z = a.z0 + zg;
   const size_t sstride = (size_t)a.G * N * (N / 2);
   const size_t fstride = (size_t)N * N * (N / 2);
-  cpx<T>* tws = W + N * C::TY;
+  cpx<T>* tws = W + lf_rows<T, C::TY>(N) * C::TY;
   load_twiddles(tws, a.tw, N);
   for (int f = 0; f < 3; ++f) {
     cfft<T, N, 1, C::TY, C::NTY, true, -1, C::RYF>(ScrCol<T, N, MP>{a.scr + f * sstride, zg, x0},
@@ -852,10 +852,10 @@ K2Entry<T> make_k2_entry() {
   e.xrow = k2_xrow<T, N>;
   e.TX = C::TX; e.NTP = C::NTP; e.TY = C::TY; e.NTY = C::NTY; e.RX = C::RX; e.NTX = C::NTX;
   e.TYI = C::TYI; e.NTYI = C::NTYI;
-  e.smYI = (6 * (size_t)N * C::TYI + N) * sizeof(cpx<T>);
-  e.smP4 = (3 * (size_t)N * C::TX + N) * sizeof(cpx<T>);  // 3 tiles + twiddles
-  e.smP5 = (4 * (size_t)N * C::TX + N) * sizeof(cpx<T>);  // 4 tiles + twiddles
-  e.smY = ((size_t)N * C::TY + N) * sizeof(cpx<T>);
+  e.smYI = (6 * (size_t)lf_rows<T, C::TYI>(N) * C::TYI + N) * sizeof(cpx<T>);
+  e.smP4 = (3 * (size_t)lf_rows<T, C::TX>(N) * C::TX + N) * sizeof(cpx<T>);  // 3 tiles + twiddles
+  e.smP5 = (4 * (size_t)lf_rows<T, C::TX>(N) * C::TX + N) * sizeof(cpx<T>);  // 4 tiles + twiddles
+  e.smY = ((size_t)lf_rows<T, C::TY>(N) * C::TY + N) * sizeof(cpx<T>);
   e.smX = (2 * (size_t)C::XBUF + N) * sizeof(cpx<T>);
   return e;
 }
