@@ -305,6 +305,17 @@ def main():
             "step_model_bytes": model_bytes,
             "step_frac": (model_bytes / (ms_step / 1000.0) / 1e9) / hbm}
 
+    # secondary roofline: FP32 CUDA-core arithmetic, 130 N^3 log2 N flop per RK2-family step
+    # (radix-2 operation count of the step's 3D transforms) against the measured FMA peak
+    fma32 = ns.fma_peak(ns.FP32, device=local)
+    fma64 = ns.fma_peak(ns.FP64, device=local)
+    step_flops = 130.0 * N_PS ** 3 * math.log2(N_PS)
+    alu = {"bound": "alu", "flops_per_step": step_flops,
+           "achieved": step_flops / (ms_step / 1000.0) / 1e12, "peak": fma32 / 1e12,
+           "unit": "TFLOP/s", "frac": step_flops / (ms_step / 1000.0) / fma32,
+           "peak_source": "measured (ns_fma_peak, FP32 FMA chains on every SM)",
+           "fp64_fma_peak_tflops": fma64 / 1e12}
+
     line = {
         "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": K,
         "warmup": W, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
@@ -316,7 +327,7 @@ def main():
         "gcells_per_s": value * N_PS ** 3 / 1e9,
         "sim_time_per_s": value * dt / world,
         "energy_at_end": E, "dissipation_at_end": eps,
-        "roofline": roof, "gpu_launches": launches, "clocks": clk,
+        "roofline": roof, "alu_roofline": alu, "gpu_launches": launches, "clocks": clk,
     }
 
     # RK4 + 2/3 truncation at 384^3, same kmax (comparison leg)
@@ -366,6 +377,7 @@ def main():
             "gcells_per_s": world * sum(n ** 3 for n in Ns) * Kb / (msb / 1000.0) / 1e9,
             "model_bytes_per_step": model,
             "frac_hbm": (model / (msb / Kb / 1000.0) / 1e9) / hbm,
+            "frac_alu": sum(130.0 * n ** 3 * math.log2(n) for n in Ns) / (msb / Kb / 1000.0) / fma32,
             "finite": bool(np.all(np.isfinite(Eb)))}
         b.close()
 

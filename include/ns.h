@@ -210,6 +210,14 @@ int ns_nonlinear_noalloc(const void* state, void* out, int N, double kmax, int t
  * one pencil pass per evaluation), for roofline reporting. */
 double ns_model_bytes_per_step(ns_ctx* ctx);
 
+/* Measured CUDA-core FMA throughput of `device` in flop/s (2 flops per FMA) for precision
+ * NS_FP32 or NS_FP64: one timed launch of independent FMA chains filling every SM (a few ms
+ * in FP32, tens of ms in FP64).  It is the peak of the secondary, arithmetic roofline of the
+ * FFT passes; the paper has no counterpart.  Allocates and frees one scalar; synchronises the
+ * device's default stream.  Returns NS_ERR_INVALID_ARG for a null pointer or another
+ * precision, NS_ERR_CUDA on a CUDA failure.  The current device is restored. */
+int ns_fma_peak(int device, int precision, double* flops_per_s);
+
 #ifdef __cplusplus
 }
 #endif

@@ -71,6 +71,7 @@ _set_time = _sig("ns_set_time", ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_in
 _device_state = _sig("ns_device_state", ctypes.c_int,
                      [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(ctypes.c_int)])
 _model_bytes = _sig("ns_model_bytes_per_step", ctypes.c_double, [_vp])
+_fma_peak = _sig("ns_fma_peak", ctypes.c_int, [ctypes.c_int, ctypes.c_int, _dp])
 _profile = _sig("ns_profile", ctypes.c_int, [_vp, ctypes.c_int])
 _profile_read = _sig("ns_profile_read", ctypes.c_int,
                      [_vp, ctypes.c_int, _dp, ctypes.POINTER(ctypes.c_int64),
@@ -99,7 +100,7 @@ EXPORTED = ["ns_init", "ns_init_ex", "ns_init_error", "ns_destroy", "ns_last_err
             "ns_set_velocity", "ns_get_velocity", "ns_get_state", "ns_set_state",
             "ns_set_forcing", "ns_step", "ns_set_shifts", "ns_nonlinear", "ns_energy",
             "ns_energy_spectrum", "ns_time", "ns_set_time", "ns_device_state",
-            "ns_model_bytes_per_step", "ns_profile", "ns_profile_read", "ns_nonlinear_noalloc", "ns_vjp", "ns_batch_init", "ns_batch_destroy", "ns_batch_last_error",
+            "ns_model_bytes_per_step", "ns_fma_peak", "ns_profile", "ns_profile_read", "ns_nonlinear_noalloc", "ns_vjp", "ns_batch_init", "ns_batch_destroy", "ns_batch_last_error",
             "ns_batch_member", "ns_batch_set_velocity", "ns_batch_get_state", "ns_batch_step",
             "ns_batch_energy", "ns_batch_set_spin_limit", "ns_batch_test_stall", "ns_batch_grid"]
 
@@ -246,6 +247,15 @@ class Solver:
             self._check(_profile_read(self._h, k, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(nl)))
             out[name] = (ms.value, n.value, nl.value)
         return out
+
+
+def fma_peak(precision=None, device=0):
+    """Measured CUDA-core FMA throughput of the device in flop/s (ns_fma_peak)."""
+    out = ctypes.c_double()
+    rc = _fma_peak(device, FP32 if precision is None else precision, ctypes.byref(out))
+    if rc != NS_OK:
+        raise NSError(rc, "ns_fma_peak failed")
+    return out.value
 
 
 def nonlinear_noalloc(state_ptr, out_ptr, N, kmax, delta, truncation=TRUNC_SPHERICAL, stream=None):

@@ -82,12 +82,16 @@ ns_ctx* ns_batch_member(ns_batch* b, int i) {
 
 int ns_batch_set_velocity(ns_batch* b, int i, const double* u) {
   if (!b || i < 0 || i >= b->count) return NS_ERR_INVALID_ARG;
-  return ns_set_velocity(b->mem[i], u);
+  const int rc = ns_set_velocity(b->mem[i], u);
+  if (rc != NS_OK) b->err = ns_last_error(b->mem[i]);
+  return rc;
 }
 
 int ns_batch_get_state(ns_batch* b, int i, double* re_im) {
   if (!b || i < 0 || i >= b->count) return NS_ERR_INVALID_ARG;
-  return ns_get_state(b->mem[i], re_im);
+  const int rc = ns_get_state(b->mem[i], re_im);
+  if (rc != NS_OK) b->err = ns_last_error(b->mem[i]);
+  return rc;
 }
 
 int ns_batch_step(ns_batch* b, const double* dt, int nsteps) {

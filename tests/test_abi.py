@@ -65,3 +65,14 @@ def test_init_rejects_bad_arguments_before_touching_a_device(lib):
     with pytest.raises(ns.NSError) as e:
         ns.Solver(16, 0.01, 8.0, scheme=9)
     assert e.value.code == 1
+
+
+def test_fma_peak_argument_checks():
+    # rejected before any CUDA call, so this runs without a GPU
+    import ctypes
+
+    from paper_2603_08892_gb300 import binding as b
+
+    out = ctypes.c_double()
+    assert b._fma_peak(0, 7, ctypes.byref(out)) == 1  # NS_ERR_INVALID_ARG
+    assert b._fma_peak(0, b.FP32, None) == 1

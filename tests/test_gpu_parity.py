@@ -316,3 +316,11 @@ def test_results_do_not_depend_on_slab_group_size(ns, monkeypatch, tmp_path):
             out.append(s.get_state())
     assert np.array_equal(out[0], out[1]) and np.array_equal(out[0], out[2])
     assert (tmp_path / "tune.json").exists()
+
+
+def test_fma_peak_measures_the_device(ns):
+    f32 = ns.fma_peak(ns.FP32)
+    f64 = ns.fma_peak(ns.FP64)
+    # 152 SMs x 128 FP32 lanes x 2 flop x ~2 GHz is ~80 TFLOP/s; FP64 is a small fraction
+    assert 20e12 < f32 < 200e12
+    assert 0 < f64 < f32
