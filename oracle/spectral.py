@@ -8,7 +8,9 @@ Paper passages followed:
   the 1/N factor per direction, the inverse none; wavenumbers k in [-N/2, N/2-1].
 * Domain size 2*pi so that wavenumbers are integers -- Section 2 (numerical methods).
 * Truncations -- Section 3.2, Fig. truncation:common: "cubic" zeroes modes with any
-  |k_i| >= kmax, "spherical" zeroes modes with |k| >= kmax, kmax = C_t k_N.
+  |k_i| >= kmax, "spherical" zeroes modes with |k| >= kmax, kmax = C_t k_N.  "No double
+  aliases" (Section 4.2, Fig. truncation:spherical:double:aliases(b); supplementary alias
+  classes): the spherical truncation minus every mode that a double alias can reach.
 * Leray projection onto divergence-free fields -- Section 4.1 below Eq. (base-eq): the
   nonlinear term is the projection of the advective term onto the divergence-free space.
 * Phase-shift operator -- Section 4.2, Eq. (shift_operator_3d): P_Delta(X) = exp(i k.Delta) X,
@@ -18,6 +20,7 @@ import numpy as np
 
 TRUNC_SPHERICAL = 0
 TRUNC_CUBIC = 1
+TRUNC_NO_DOUBLE_ALIAS = 2
 
 
 def wavenumbers(N):
@@ -90,14 +93,46 @@ def kmax_int_threshold(kmax):
     return m
 
 
+def double_alias_shifts():
+    """The 12 vectors e in {-1, 0, 1}^3 with exactly one zero component: the alias classes
+    called double aliases (supplementary material, classification of e)."""
+    out = []
+    for ez in (-1, 0, 1):
+        for ey in (-1, 0, 1):
+            for ex in (-1, 0, 1):
+                if (ex == 0) + (ey == 0) + (ez == 0) == 1:
+                    out.append((ex, ey, ez))
+    return out
+
+
+def double_alias_reach(N, kmax):
+    """Modes k that a double alias can reach from the spherically retained modes.
+
+    A product of retained modes kn + km with |kn|^2, |km|^2 <= m (m = kmax2_threshold) lands on
+    k = kn + km - N e (2 k_N = N); for a double-alias class e this needs
+    |k + N e| <= |kn| + |km| <= 2 sqrt(m), i.e. |k + N e|^2 <= 4 m.  The set returned is every k
+    meeting that bound for some double-alias e: it contains every mode a double alias reaches
+    (reading of the paper: the removed region is this bound, not the exact lattice set).
+    """
+    KX, KY, KZ = wavenumbers(N)
+    m4 = 4 * kmax2_threshold(kmax)
+    reach = np.zeros(KX.shape, dtype=bool)
+    for ex, ey, ez in double_alias_shifts():
+        d2 = (KX + N * ex) ** 2 + (KY + N * ey) ** 2 + (KZ + N * ez) ** 2
+        reach |= d2 <= m4
+    return reach
+
+
 def truncation_mask(N, kmax, kind=TRUNC_SPHERICAL):
     """Boolean mask of retained modes (Section 3.2, Fig. truncation:common).
 
-    spherical: keep |k| < kmax; cubic: keep max_i |k_i| < kmax.
+    spherical: keep |k| < kmax; cubic: keep max_i |k_i| < kmax; no double aliases: the
+    spherical mask without double_alias_reach (which is empty when 3 sqrt(m) < sqrt(2) N,
+    the discrete form of kmax <= (2 sqrt 2 / 3) k_N).
     Every admissible kmax (<= N/2) zeroes the Nyquist rows ky = -N/2, kz = -N/2.
     """
     KX, KY, KZ = wavenumbers(N)
-    if kind not in (TRUNC_SPHERICAL, TRUNC_CUBIC):
+    if kind not in (TRUNC_SPHERICAL, TRUNC_CUBIC, TRUNC_NO_DOUBLE_ALIAS):
         raise ValueError("unknown truncation kind")
     if kind == TRUNC_CUBIC:
         m = kmax_int_threshold(kmax)
@@ -105,6 +140,8 @@ def truncation_mask(N, kmax, kind=TRUNC_SPHERICAL):
     else:
         K2 = KX * KX + KY * KY + KZ * KZ
         keep = K2 <= kmax2_threshold(kmax)
+        if kind == TRUNC_NO_DOUBLE_ALIAS:
+            keep &= ~double_alias_reach(N, kmax)
     return keep
 
 
