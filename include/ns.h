@@ -44,7 +44,14 @@ typedef enum {
   NS_ERR_INTERNAL = 9      /* a device-side consistency check failed (bad launch shape) */
 } ns_status;
 
-enum { NS_TRUNC_SPHERICAL = 0, NS_TRUNC_CUBIC = 1 };
+/* Truncations (Sec. 3.2, Fig. truncation:common; Sec. 4.2, Fig.
+ * truncation:spherical:double:aliases(b)): spherical keeps |k| < kmax, cubic keeps every
+ * |k_i| < kmax, no-double-alias keeps the spherical set minus the modes that a double alias
+ * (an aliased product with exactly two out-of-range components) can reach: every k with
+ * |k + N e|^2 <= 4 m for some e in {-1,0,1}^3 with exactly one zero component, m the largest
+ * integer below kmax^2.  It equals the spherical set for kmax <= (2 sqrt 2 / 3) N/2; with the
+ * exact phase-shift scheme it makes the nonlinear term alias-free at any kmax <= N/2. */
+enum { NS_TRUNC_SPHERICAL = 0, NS_TRUNC_CUBIC = 1, NS_TRUNC_NO_DOUBLE_ALIAS = 2 };
 enum { NS_RK2 = 0, NS_RK4 = 1, NS_RK2_PS_EXACT = 2, NS_RK2_PS_APPROX = 3, NS_RK2_PS_RANDOM = 4 };
 enum { NS_FP32 = 0, NS_FP64 = 1 };
 enum { NS_FORCE_NONE = 0, NS_FORCE_TCRANDOM_CONST_EPS = 1 };
@@ -57,7 +64,7 @@ typedef struct {
   double L;          /* domain size, must be 2*pi                                       */
   double nu;         /* kinematic viscosity >= 0                                        */
   double kmax;       /* truncation wavenumber, 0 < kmax <= N/2 (Sec. 3.2: kmax = C_t k_N) */
-  int truncation;    /* NS_TRUNC_SPHERICAL (keep |k| < kmax) or NS_TRUNC_CUBIC (all |k_i| < kmax) */
+  int truncation;    /* NS_TRUNC_SPHERICAL, NS_TRUNC_CUBIC or NS_TRUNC_NO_DOUBLE_ALIAS (above) */
   int scheme;        /* NS_RK2 ... NS_RK2_PS_RANDOM                                     */
   int precision;     /* NS_FP32 (FP32 butterflies and products, FP64 tables/reductions) or NS_FP64 */
   int device;        /* CUDA device ordinal                                             */

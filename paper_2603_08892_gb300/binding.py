@@ -26,7 +26,7 @@ NS_OK = 0
 ERRORS = {1: "NS_ERR_INVALID_ARG", 2: "NS_ERR_UNSUPPORTED_N", 3: "NS_ERR_KMAX", 4: "NS_ERR_CUDA",
           5: "NS_ERR_OOM", 6: "NS_ERR_NONFINITE", 7: "NS_ERR_TIMEOUT", 8: "NS_ERR_STATE",
           9: "NS_ERR_INTERNAL"}
-TRUNC_SPHERICAL, TRUNC_CUBIC = 0, 1
+TRUNC_SPHERICAL, TRUNC_CUBIC, TRUNC_NO_DOUBLE_ALIAS = 0, 1, 2
 RK2, RK4, RK2_PS_EXACT, RK2_PS_APPROX, RK2_PS_RANDOM = 0, 1, 2, 3, 4
 FP32, FP64 = 0, 1
 FORCE_NONE, FORCE_TCRANDOM_CONST_EPS = 0, 1

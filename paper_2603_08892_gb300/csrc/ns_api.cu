@@ -1222,7 +1222,8 @@ int ns_init_ex(ns_ctx** out, const ns_params* prm) {
     g_init_error = "kmax must satisfy 0 < kmax <= N/2";
     return NS_ERR_KMAX;
   }
-  if (p.truncation != NS_TRUNC_SPHERICAL && p.truncation != NS_TRUNC_CUBIC) {
+  if (p.truncation != NS_TRUNC_SPHERICAL && p.truncation != NS_TRUNC_CUBIC &&
+      p.truncation != NS_TRUNC_NO_DOUBLE_ALIAS) {
     g_init_error = "unknown truncation";
     return NS_ERR_INVALID_ARG;
   }
@@ -1498,7 +1499,9 @@ extern "C" int ns_nonlinear_noalloc(const void* state, void* out, int N, double 
   if (!state || !out || !delta) return NS_ERR_INVALID_ARG;
   if (N < 8 || N > kNoallocMaxN || N % 2 != 0 || !is_2a3b(N)) return NS_ERR_UNSUPPORTED_N;
   if (!(kmax > 0.0) || kmax > 0.5 * N) return NS_ERR_KMAX;
-  if (truncation != NS_TRUNC_SPHERICAL && truncation != NS_TRUNC_CUBIC) return NS_ERR_INVALID_ARG;
+  if (truncation != NS_TRUNC_SPHERICAL && truncation != NS_TRUNC_CUBIC &&
+      truncation != NS_TRUNC_NO_DOUBLE_ALIAS)
+    return NS_ERR_INVALID_ARG;
   cudaStream_t st = (cudaStream_t)stream_p;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return NS_ERR_CUDA;

@@ -44,6 +44,19 @@ __device__ __forceinline__ int kof(int i, int N) { return i < (N >> 1) ? i : i -
 // ----------------------------------------------------------------------------------------
 // Tables (FP64 arithmetic, rounded to T)
 // ----------------------------------------------------------------------------------------
+// Truncation mask T at mode k (Sec. 3.2; Sec. 4.2 for the double aliases).  trunc 1, cubic:
+// max_i |k_i| <= Kimax.  Otherwise spherical: |k|^2 <= K2max; trunc 2 also drops the modes a
+// double alias can reach: |k + N e|^2 <= 4 K2max for some e with exactly one zero component,
+// whose closest member gives (N - |k_i|)^2 + (N - |k_j|)^2 + k_l^2 for the pair (i, j).
+__device__ __forceinline__ bool trunc_keep(int trunc, int kx, int ky, int kz, int N, int K2max, int Kimax) {
+  if (trunc == 1) return max(abs(kx), max(abs(ky), abs(kz))) <= Kimax;
+  const long long x2 = (long long)kx * kx, y2 = (long long)ky * ky, z2 = (long long)kz * kz;
+  if (x2 + y2 + z2 > (long long)K2max) return false;
+  if (trunc != 2) return true;
+  const long long ax = N - abs(kx), ay = N - abs(ky), az = N - abs(kz), m4 = 4LL * K2max;
+  return ax * ax + ay * ay + z2 > m4 && ax * ax + az * az + y2 > m4 && ay * ay + az * az + x2 > m4;
+}
+
 template <typename T>
 __global__ void k_twiddle(cpx<T>* tw, int N) {
   int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -179,14 +192,7 @@ __global__ void __launch_bounds__(512) k_pencil(PencilArgs<T> a) {
     cpx<T> nv[3];
     if (a.nF > 0) {
       const int k2 = kx * kx + ky * ky + kz * kz;
-      bool keep;
-      if (a.trunc == 1) {
-        int m = max(kx, max(abs(ky), abs(kz)));
-        keep = m <= a.Kimax;
-      } else {
-        keep = k2 <= a.K2max;
-      }
-      keep = keep && (k2 != 0);
+      const bool keep = trunc_keep(a.trunc, kx, ky, kz, N, a.K2max, a.Kimax) && (k2 != 0);
       if (keep) {
         cpx<T> v0 = b[0][e], v1 = b[1][e], v2 = b[2][e];
         const T fx = (T)kx, fy = (T)ky, fz = (T)kz;

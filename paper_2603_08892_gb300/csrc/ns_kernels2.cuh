@@ -197,13 +197,7 @@ template <typename T>
 __device__ __forceinline__ void project_point(const PencilArgs<T>& a, int kx, int ky, int kz,
                                               cpx<T> nv[3]) {
   const int k2 = kx * kx + ky * ky + kz * kz;
-  bool keep;
-  if (a.trunc == 1) {
-    keep = max(kx, max(abs(ky), abs(kz))) <= a.Kimax;
-  } else {
-    keep = k2 <= a.K2max;
-  }
-  keep = keep && (k2 != 0);
+  const bool keep = trunc_keep(a.trunc, kx, ky, kz, a.N, a.K2max, a.Kimax) && (k2 != 0);
   if (keep) {
     const cpx<T> v0 = nv[0], v1 = nv[1], v2 = nv[2];
     const T fx = (T)kx, fy = (T)ky, fz = (T)kz;
@@ -297,7 +291,7 @@ __host__ __device__ constexpr int pencil_tiles(int nF, int nOut) { return (nF > 
 // forcing vanish there, so the tile's forward transforms are skipped (Sec. 2, truncation).
 template <typename T, int TX>
 __device__ __forceinline__ bool pencil_tile_truncated(const PencilArgs<T>& a, int x0, int ky) {
-  bool out;
+  bool out;  // the no-double-alias mask lies inside the sphere: the spherical test is safe
   if (a.trunc == 1)
     out = x0 > a.Kimax || abs(ky) > a.Kimax;
   else
