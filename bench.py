@@ -58,6 +58,8 @@ def parse():
     ap.add_argument("--no-rk4", action="store_true")
     ap.add_argument("--batch-steps", type=int, default=200,
                     help="steps of the 64-member ensemble leg (0: skip)")
+    ap.add_argument("--quality", action="store_true",
+                    help="run the accuracy study at kmax = 108 instead (spectral error vs speedup)")
     return ap.parse_args()
 
 
@@ -212,6 +214,57 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def run_quality(local):
+    """Accuracy / speed study at kmax = 108 (Sec. 5, Fig. quality, supplementary Table
+    tab:quality): Taylor-Green Re = 1600 to t = 12 with the spectral error index (Eq. quality)
+    of the 1D spectra over the window t = 7 .. 12 around the dissipation peak (t_end = t_start
+    + 5), sampled at integer times, against RK4 at N = 324, C_t = 2/3.  FP32, time step
+    1 / ceil(1 / (0.25 dx)) (CFL 0.5 reading, integer times on steps).  Speedup = GPU time of
+    the reference run / GPU time of the run (stepping only, CUDA events)."""
+    import torch
+
+    from paper_2603_08892_gb300 import analysis
+    from paper_2603_08892_gb300 import binding as ns
+    from paper_2603_08892_gb300 import inputs
+
+    torch.cuda.set_device(local)
+    kmax, T, t0 = 108.0, 12, 7
+    cases = [("RK4 C_t=2/3 (reference)", 324, ns.RK4, ns.TRUNC_SPHERICAL),
+             ("RK2 PS exact C_t=1 spherical", 216, ns.RK2_PS_EXACT, ns.TRUNC_SPHERICAL),
+             ("RK2 PS random C_t=1 spherical", 216, ns.RK2_PS_RANDOM, ns.TRUNC_SPHERICAL),
+             ("RK2 PS exact C_t=1 no double aliases", 216, ns.RK2_PS_EXACT, ns.TRUNC_NO_DOUBLE_ALIAS),
+             ("RK2 PS random C_t=1 no double aliases", 216, ns.RK2_PS_RANDOM, ns.TRUNC_NO_DOUBLE_ALIAS),
+             ("RK4 C_t=1 spherical (aliased)", 216, ns.RK4, ns.TRUNC_SPHERICAL)]
+    out, ref_spec, ref_ms = [], None, None
+    for name, N, scheme, trunc in cases:
+        dt = 1.0 / math.ceil(1.0 / (0.25 * 2 * math.pi / N))
+        per = int(round(1.0 / dt))
+        stream = torch.cuda.Stream()
+        with ns.Solver(N, 1.0 / 1600, kmax, scheme=scheme, truncation=trunc, precision=ns.FP32,
+                       stream=stream.cuda_stream, seed=12345) as s:
+            s.set_velocity(inputs.taylor_green(N))
+            spec, ms = [], 0.0
+            for j in range(1, T + 1):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                e0.record(stream)
+                s.step(dt, per)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms += e0.elapsed_time(e1)
+                if j >= t0:
+                    spec.append(tuple(s.spectrum(k, 112) for k in (1, 2, 3)))
+            E, eps = s.energy()
+        if ref_spec is None:
+            ref_spec, ref_ms = spec, ms
+        out.append({"run": name, "N": N, "steps": T * per, "dt": dt, "gpu_s": ms / 1000.0,
+                    "speedup": ref_ms / ms, "error_pct": analysis.error_index(spec, ref_spec, kmax),
+                    "E_end": E, "eps_end": eps})
+        print(json.dumps(out[-1]), flush=True)
+    print(json.dumps({"study": "quality", "kmax": kmax, "Re": 1600, "window": [t0, T], "runs": out}))
+
+
 def timed_steps(ns, s, dt, K, stream):
     import torch
 
@@ -230,6 +283,10 @@ def main():
     rank, world, local = dist_env()
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.quality:
+        if rank == 0:
+            run_quality(local)
         return
     import numpy as np
     import torch
