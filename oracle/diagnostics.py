@@ -9,7 +9,14 @@ Paper passages followed:
   convention of supplementary Eq. dft_def), eps = nu <|omega|^2> = nu sum_k k^2 |uh|^2;
 * one-dimensional spectra E(k_x), E(k_y), E(k_z) and their use in the error index
   (Section 3.4, Eq. quality; Appendix A, Eq. quality-i-disc);
-* shell spectrum E(k) on integer bins.
+* shell spectrum E(k) on integer bins;
+* nonlinear energy flux and cumulative dissipation (Section 3.4, Fig. spectra:192): the running
+  sums over shells of the nonlinear transfer T(k) = sum_shell Re(uh* . Nh) and of the
+  dissipation spectrum 2 nu k^2 E(k); flux Pi(k) = -sum_{k' <= k} T(k') (positive for a
+  transfer towards small scales), cumulative dissipation D(k) = sum_{k' <= k} 2 nu k'^2 E(k');
+* windowed error metrics (Section 6, Table tab:960): Err_early and Err_late are the error index
+  over the first and second half of the output times, Err(Ebar) the relative error of the
+  time-averaged spectra with the same weights.
 
 Readings: half-spectrum sums use the Hermitian weights w (1 at kx = 0, 2 elsewhere);
 shell bin = floor(|k| + 1/2); 1D spectra fold +/-k_i onto |k_i|; the discrete error index
@@ -94,3 +101,59 @@ def error_index(spectra, spectra_ref, kmax):
             tot += float(np.sum(wk * 100.0 * np.abs(Er - E) / Er))
         errs.append(tot / (Nt * float(np.sum(wk))))
     return float(np.mean(errs))
+
+
+def _shell_sum(N, values, nbins):
+    """Sum of half-spectrum values (already weighted) over shell bins 0..nbins-1."""
+    KX, KY, KZ = sp.wavenumbers(N)
+    b = shell_bin(KX * KX + KY * KY + KZ * KZ)
+    out = np.zeros(nbins)
+    ok = b < nbins
+    np.add.at(out, b[ok], values[ok])
+    return out
+
+
+def transfer_spectrum(S, Nl, nbins):
+    """T(k): energy change rate of shell k due to the nonlinear term Nl (both [3][N][N][N/2]).
+
+    d/dt (1/2)|uh|^2 = Re(uh* . duh/dt) over the full spectrum, Hermitian weights w on the
+    half spectrum.
+    """
+    N = S.shape[-2]
+    w = sp.hermitian_weights(N)
+    t = w * np.sum(np.real(np.conj(S) * Nl), axis=0)
+    return _shell_sum(N, t, nbins)
+
+
+def energy_flux(S, Nl, nbins):
+    """Pi(k) = -sum_{k' <= k} T(k')."""
+    return -np.cumsum(transfer_spectrum(S, Nl, nbins))
+
+
+def dissipation_spectrum(S, nu, nbins):
+    N = S.shape[-2]
+    KX, KY, KZ = sp.wavenumbers(N)
+    w = sp.hermitian_weights(N)
+    K2 = KX * KX + KY * KY + KZ * KZ
+    return _shell_sum(N, nu * w * K2 * np.sum(np.abs(S) ** 2, axis=0), nbins)
+
+
+def cumulative_dissipation(S, nu, nbins):
+    """D(k) = sum_{k' <= k} 2 nu k'^2 E(k') (tends to eps at the last shell)."""
+    return np.cumsum(dissipation_spectrum(S, nu, nbins))
+
+
+def error_index_windows(spectra, spectra_ref, kmax):
+    """(Err_early, Err_late, Err(Ebar)) over a sequence of output times (Table tab:960).
+
+    The first half of the samples is the early window, the second half the late one (an odd
+    count puts the middle sample in both); Err(Ebar) compares the spectra averaged over all
+    samples with the error index's weights.
+    """
+    Nt = len(spectra)
+    h = (Nt + 1) // 2
+    early = error_index(spectra[:h], spectra_ref[:h], kmax)
+    late = error_index(spectra[Nt - h:], spectra_ref[Nt - h:], kmax)
+    mean = [tuple(np.mean([np.asarray(s[d]) for s in spectra], axis=0) for d in range(3))]
+    mean_ref = [tuple(np.mean([np.asarray(s[d]) for s in spectra_ref], axis=0) for d in range(3))]
+    return early, late, error_index(mean, mean_ref, kmax)

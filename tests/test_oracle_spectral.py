@@ -147,3 +147,14 @@ def test_package_error_index_agrees_with_oracle():
     a = [tuple(rs.random(20) + 0.5 for _ in range(3)) for _ in range(4)]
     b = [tuple(rs.random(20) + 0.5 for _ in range(3)) for _ in range(4)]
     assert abs(analysis.error_index(a, b, 15.5) - dg.error_index(a, b, 15.5)) < 1e-12
+
+
+def test_package_windowed_error_metrics_agree_with_oracle():
+    from paper_2603_08892_gb300 import analysis
+
+    rs = np.random.default_rng(6)
+    a = [tuple(rs.random(20) + 0.5 for _ in range(3)) for _ in range(5)]
+    b = [tuple(rs.random(20) + 0.5 for _ in range(3)) for _ in range(5)]
+    got = analysis.error_index_windows(a, b, 15.5)
+    ref = dg.error_index_windows(a, b, 15.5)
+    assert max(abs(x - y) for x, y in zip(got, ref)) < 1e-12
