@@ -234,7 +234,8 @@ def run_quality(local):
              ("RK2 PS random C_t=1 spherical", 216, ns.RK2_PS_RANDOM, ns.TRUNC_SPHERICAL),
              ("RK2 PS exact C_t=1 no double aliases", 216, ns.RK2_PS_EXACT, ns.TRUNC_NO_DOUBLE_ALIAS),
              ("RK2 PS random C_t=1 no double aliases", 216, ns.RK2_PS_RANDOM, ns.TRUNC_NO_DOUBLE_ALIAS),
-             ("RK4 C_t=1 spherical (aliased)", 216, ns.RK4, ns.TRUNC_SPHERICAL)]
+             ("RK4 C_t=1 spherical (aliased)", 216, ns.RK4, ns.TRUNC_SPHERICAL),
+             ("RK2 C_t=2/3 (time-step error only)", 324, ns.RK2, ns.TRUNC_SPHERICAL)]
     out, ref_spec, ref_ms = [], None, None
     for name, N, scheme, trunc in cases:
         dt = 1.0 / math.ceil(1.0 / (0.25 * 2 * math.pi / N))
@@ -318,6 +319,13 @@ def main():
     prof = s.profile_read()
     s.profile(False)
     E, eps = s.energy()
+    # diagnostic cost: flux and cumulative dissipation with the two-shift average (ns_energy_flux)
+    dxq = 2 * math.pi / N_PS
+    s.energy_flux(200, [[0, 0, 0], [dxq / 2] * 3])
+    torch.cuda.synchronize()
+    tf0 = time.perf_counter()
+    s.energy_flux(200, [[0, 0, 0], [dxq / 2] * 3])
+    flux_ms = (time.perf_counter() - tf0) * 1000.0
     ms_max = reduce_max(ms, world)
     barrier(world)
 
@@ -385,6 +393,7 @@ def main():
         "sim_time_per_s": value * dt / world,
         "energy_at_end": E, "dissipation_at_end": eps,
         "roofline": roof, "alu_roofline": alu, "gpu_launches": launches, "clocks": clk,
+        "diagnostics_ms": {"energy_flux_two_shifts": flux_ms},
     }
 
     # RK4 + 2/3 truncation at 384^3, same kmax (comparison leg)

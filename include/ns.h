@@ -141,6 +141,18 @@ int ns_energy(ns_ctx* ctx, double* E, double* eps);
 /* Energy spectrum, FP64 bins k = 0..nbins-1: NS_SPEC_SHELL bins floor(|k| + 1/2),
  * NS_SPEC_X/Y/Z fold +-k_i onto |k_i| (Sec. 3.4, Eq. quality uses the 1D spectra). */
 int ns_energy_spectrum(ns_ctx* ctx, int kind, double* out, int nbins);
+/* Nonlinear energy flux and cumulative dissipation of the current state on shell bins
+ * k = 0 .. nbins-1, bin floor(|k| + 1/2) (Sec. 3.4, Fig. spectra:192).  N is the mean over
+ * nshift shift vectors delta[3 s .. 3 s + 2] (radians) of the shifted, truncated, projected
+ * nonlinear term (nshift = 0: the unshifted term; the exact scheme's term is the mean over
+ * {0, (dx/2)(1,1,1)}).  T(k) = sum over the shell of Re(uh* . Nh) over the full spectrum,
+ * flux[k] = -sum_{k' <= k} T(k') (it vanishes at the last shell: the truncated rotational term
+ * conserves energy), cumdiss[k] = sum_{k' <= k} 2 nu k'^2 E(k') (eps at the last shell).
+ * Either output may be NULL.  The state is unchanged; the first call allocates one or two
+ * work fields of the state's size; synchronises the context's stream.  Returns
+ * NS_ERR_INVALID_ARG for nbins outside 1..4096, nshift outside 0..8 or a non-finite shift. */
+int ns_energy_flux(ns_ctx* ctx, const double* delta, int nshift, double* flux, double* cumdiss, int nbins);
+
 /* Simulated time and number of steps done since the last ns_set_velocity. */
 int ns_time(ns_ctx* ctx, double* t, int64_t* step);
 /* Overrides time and step counter (checkpoint resume). */

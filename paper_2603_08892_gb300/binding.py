@@ -66,6 +66,7 @@ _set_shifts = _sig("ns_set_shifts", ctypes.c_int, [_vp, _dp, ctypes.c_int])
 _nonlinear = _sig("ns_nonlinear", ctypes.c_int, [_vp, _dp, _dp, _dp])
 _energy = _sig("ns_energy", ctypes.c_int, [_vp, _dp, _dp])
 _spectrum = _sig("ns_energy_spectrum", ctypes.c_int, [_vp, ctypes.c_int, _dp, ctypes.c_int])
+_flux = _sig("ns_energy_flux", ctypes.c_int, [_vp, _dp, ctypes.c_int, _dp, _dp, ctypes.c_int])
 _time = _sig("ns_time", ctypes.c_int, [_vp, _dp, ctypes.POINTER(ctypes.c_int64)])
 _set_time = _sig("ns_set_time", ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_int64])
 _device_state = _sig("ns_device_state", ctypes.c_int,
@@ -99,7 +100,7 @@ PROF_KINDS = {"k_pencil": 0, "k_yinv": 1, "k_xrow": 2, "k_yfwd": 3, "slab_pass":
 EXPORTED = ["ns_init", "ns_init_ex", "ns_init_error", "ns_destroy", "ns_last_error",
             "ns_set_velocity", "ns_get_velocity", "ns_get_state", "ns_set_state",
             "ns_set_forcing", "ns_step", "ns_set_shifts", "ns_nonlinear", "ns_energy",
-            "ns_energy_spectrum", "ns_time", "ns_set_time", "ns_device_state",
+            "ns_energy_spectrum", "ns_energy_flux", "ns_time", "ns_set_time", "ns_device_state",
             "ns_model_bytes_per_step", "ns_fma_peak", "ns_profile", "ns_profile_read", "ns_nonlinear_noalloc", "ns_vjp", "ns_batch_init", "ns_batch_destroy", "ns_batch_last_error",
             "ns_batch_member", "ns_batch_set_velocity", "ns_batch_get_state", "ns_batch_step",
             "ns_batch_energy", "ns_batch_set_spin_limit", "ns_batch_test_stall", "ns_batch_grid"]
@@ -206,6 +207,19 @@ class Solver:
         out = np.empty(nbins)
         self._check(_spectrum(self._h, kind, _ptr(out), nbins))
         return out
+
+    def energy_flux(self, nbins=None, shifts=None):
+        """(flux Pi(k), cumulative dissipation D(k)) on shell bins (ns_energy_flux).
+
+        shifts: list of shift vectors whose shifted nonlinear terms are averaged (None: the
+        unshifted term)."""
+        nbins = int(math.ceil(math.sqrt(3) * self.N / 2)) + 1 if nbins is None else nbins
+        d = np.ascontiguousarray(np.asarray(shifts if shifts else [[0.0, 0.0, 0.0]], dtype=np.float64))
+        ns_ = len(shifts) if shifts else 0
+        flux = np.empty(nbins)
+        cum = np.empty(nbins)
+        self._check(_flux(self._h, _ptr(d), ns_, _ptr(flux), _ptr(cum), nbins))
+        return flux, cum
 
     def time(self):
         t = ctypes.c_double()

@@ -125,6 +125,7 @@ struct SolverBase {
   virtual void nonlinear(const double* in, const double* delta, double* out) = 0;
   virtual void energy(double* E, double* eps) = 0;
   virtual void spectrum(int kind, double* out, int nbins) = 0;
+  virtual void energy_flux(const double* delta, int nshift, double* flux, double* cumd, int nbins) = 0;
   virtual void set_forcing(int kind, double kfmin, double kfmax, double eps, double tcorr,
                            uint64_t seed) = 0;
   virtual void* state_ptr() = 0;
@@ -338,6 +339,7 @@ struct Solver : SolverBase {
 
   ~Solver() override {
     cudaFree(state); cudaFree(acc); cudaFree(mixed[0]); cudaFree(mixed[1]);
+    cudaFree(nlbuf); cudaFree(nltmp);
     cudaFree(Ft[0]); cudaFree(Ft[1]); cudaFree(scr); cudaFree(tw); cudaFree(ifac);
     cudaFree(shtab); cudaFree(d_shifts); cudaFree(red); cudaFree(d_err);
     cudaFree(fpat); cudaFree(force); cudaFree(shell);
@@ -1143,19 +1145,59 @@ struct Solver : SolverBase {
     *eps = h[1];
   }
 
-  void spectrum(int kind, double* out, int nbins) override {
+  void spectrum(int kind, double* out, int nbins) override { binned(kind, out, nbins, 0, nullptr); }
+
+  // bins of the quadratic form q of k_spectrum (0: energy, 1: transfer with B, 2: dissipation)
+  void binned(int kind, double* out, int nbins, int q, const cpx<T>* B) {
     // partial bins [nb][nbins] followed by the final [nbins] in the reduction buffer
     const size_t cap = (size_t)red_blocks * 1024;
     int nb = (int)(cap / (size_t)nbins) - 1;
     if (nb > red_blocks) nb = red_blocks;
     if (nb < 1) throw NsError{NS_ERR_INVALID_ARG, "nbins too large"};
-    k_spectrum<T><<<nb, 256, nbins * sizeof(double), st>>>(state, N, kind, nbins, red);
+    k_spectrum<T><<<nb, 256, nbins * sizeof(double), st>>>(state, N, kind, nbins, red, q, B, c->p.nu);
     double* fin = red + (size_t)nb * nbins;
     k_spectrum_final<<<(nbins + 127) / 128, 128, 0, st>>>(red, nb, nbins, fin);
     LAUNCH_CHECK();
     CUDA_TRY(cudaMemcpyAsync(out, fin, nbins * sizeof(double), cudaMemcpyDeviceToHost, st));
     sync_check();
   }
+
+  // Nonlinear energy flux and cumulative dissipation on shell bins (Sec. 3.4)
+  cpx<T>* nlbuf = nullptr;
+  void energy_flux(const double* delta, int nshift, double* flux, double* cumd, int nbins) override {
+    if (flux) {
+      if (!nlbuf) CUDA_TRY(cudaMalloc(&nlbuf, 3 * F1 * sizeof(cpx<T>)));
+      if (nshift == 0) {
+        nl_eval(state, nullptr, nlbuf);
+      } else {
+        if (!nltmp && nshift > 1) CUDA_TRY(cudaMalloc(&nltmp, 3 * F1 * sizeof(cpx<T>)));
+        for (int sidx = 0; sidx < nshift; ++sidx) {
+          std::vector<double> sh(delta + 3 * sidx, delta + 3 * sidx + 3);
+          upload_shifts(sh);
+          nl_eval(state, shift_tab(0), sidx == 0 ? nlbuf : nltmp);
+          if (sidx > 0) ew(EW_ADD, nlbuf, nltmp, nullptr, nlbuf);
+        }
+        if (nshift > 1) ew(EW_SCALE, nlbuf, nullptr, nullptr, nlbuf, 1.0 / nshift);
+      }
+      std::vector<double> t(nbins);
+      binned(0, t.data(), nbins, 1, nlbuf);
+      double acc = 0.0;
+      for (int k = 0; k < nbins; ++k) {
+        acc += t[k];
+        flux[k] = -acc;
+      }
+    }
+    if (cumd) {
+      std::vector<double> d(nbins);
+      binned(0, d.data(), nbins, 2, nullptr);
+      double acc = 0.0;
+      for (int k = 0; k < nbins; ++k) {
+        acc += d[k];
+        cumd[k] = acc;
+      }
+    }
+  }
+  cpx<T>* nltmp = nullptr;
 };
 
 int fail(ns_ctx* c, int code, const std::string& msg) {
@@ -1385,6 +1427,18 @@ int ns_energy_spectrum(ns_ctx* c, int kind, double* out, int nbins) {
     if (!out || nbins <= 0 || nbins > 4096) return fail(c, NS_ERR_INVALID_ARG, "need out != NULL, 0 < nbins <= 4096");
     if (kind < NS_SPEC_SHELL || kind > NS_SPEC_Z) return fail(c, NS_ERR_INVALID_ARG, "unknown spectrum kind");
     c->solver->spectrum(kind, out, nbins);
+    return (int)NS_OK;
+  });
+}
+
+int ns_energy_flux(ns_ctx* c, const double* delta, int nshift, double* flux, double* cumdiss, int nbins) {
+  return guarded(c, [&]() {
+    if (nbins <= 0 || nbins > 4096) return fail(c, NS_ERR_INVALID_ARG, "need 0 < nbins <= 4096");
+    if (nshift < 0 || nshift > 8 || (nshift > 0 && !delta))
+      return fail(c, NS_ERR_INVALID_ARG, "need 0 <= nshift <= 8 and delta for nshift > 0");
+    for (int i = 0; i < 3 * nshift; ++i)
+      if (!std::isfinite(delta[i])) return fail(c, NS_ERR_INVALID_ARG, "non-finite shift");
+    c->solver->energy_flux(delta, nshift, flux, cumdiss, nbins);
     return (int)NS_OK;
   });
 }

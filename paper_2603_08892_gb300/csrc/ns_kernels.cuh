@@ -639,9 +639,14 @@ static __global__ void k_sum_pairs(const double* partial, int nblk, double* out)
 }
 
 // spectrum partials: block b accumulates its modes into smem bins, writes partial[b][bin]
+// Binned quadratic forms of the half spectrum, weights 1/2 at kx = 0 and 1 elsewhere (so a
+// bin holds half the full-spectrum sum): q = 0, |S|^2 (energy spectrum); q = 1, 2 Re(S* . B)
+// (nonlinear transfer T(k) for B = N); q = 2, 2 nu k^2 |S|^2 (dissipation spectrum).
 template <typename T>
 __global__ void __launch_bounds__(256) k_spectrum(const cpx<T>* __restrict__ S, int N, int kind,
-                                                  int nbins, double* partial) {
+                                                  int nbins, double* partial, int q = 0,
+                                                  const cpx<T>* __restrict__ B = nullptr,
+                                                  double nu = 0.0) {
   extern __shared__ double bins[];
   for (int i = threadIdx.x; i < nbins; i += blockDim.x) bins[i] = 0.0;
   __syncthreads();
@@ -655,9 +660,15 @@ __global__ void __launch_bounds__(256) k_spectrum(const cpx<T>* __restrict__ S, 
     const int ky = kof(iy, N), kz = kof(iz, N);
     double a2 = 0;
     for (int c = 0; c < 3; ++c) {
-      cpx<T> v = S[i + c * nmode];
-      a2 += (double)v.x * (double)v.x + (double)v.y * (double)v.y;
+      const cpx<T> v = S[i + c * nmode];
+      if (q == 1) {
+        const cpx<T> b = B[i + c * nmode];
+        a2 += 2.0 * ((double)v.x * (double)b.x + (double)v.y * (double)b.y);
+      } else {
+        a2 += (double)v.x * (double)v.x + (double)v.y * (double)v.y;
+      }
     }
+    if (q == 2) a2 *= 2.0 * nu * (double)(kx * kx + ky * ky + kz * kz);
     if (a2 == 0.0) continue;
     const double w = kx == 0 ? 0.5 : 1.0;
     int bin;
