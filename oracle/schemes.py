@@ -159,3 +159,35 @@ def run(S0, dt, nsteps, prob, scheme, shifts=None, seed=None, forcing=None, t0=0
         if callback is not None:
             callback(n, t, S)
     return S, t
+
+
+def cfl_time_step(S, delta, cfl, dt_max, N):
+    """Adaptive step of the CFL condition (Section 2; reading: dt = cfl / sum_i(max|u_i| / dx),
+    the maxima over the grid values of the velocity shifted by ``delta``, capped at dt_max)."""
+    u = sp.inverse(S * sp.shift_factor(N, delta))
+    dx = 2.0 * math.pi / N
+    freq = sum(float(np.abs(u[i]).max()) / dx for i in range(3))
+    return dt_max if freq <= 0.0 else min(dt_max, cfl / freq)
+
+
+def run_cfl(S0, cfl, dt_max, nsteps, prob, scheme, seed=None, forcing=None, t0=0.0, step0=0,
+            callback=None):
+    """Advance ``nsteps`` adaptive steps: each step's dt comes from the velocity that its
+    first nonlinear evaluation forms (shifted by delta_alpha for the random scheme, unshifted
+    otherwise).  Returns (S, t, list of the steps' dt)."""
+    from . import rng
+
+    S, t, dts = S0.copy(), t0, []
+    N = prob.N
+    for n in range(nsteps):
+        da = rng.shift_alpha(seed, step0 + n, N) if scheme == SCHEME_PS_RANDOM else [0.0, 0.0, 0.0]
+        dt = cfl_time_step(S, da, cfl, dt_max, N)
+        if scheme == SCHEME_PS_RANDOM:
+            S = step_ps_random(S, dt, prob, da, t, forcing)
+        else:
+            S, _ = run(S, dt, 1, prob, scheme, t0=t, forcing=forcing)
+        t = t + dt
+        dts.append(dt)
+        if callback is not None:
+            callback(n, t, S)
+    return S, t, dts

@@ -171,3 +171,34 @@ def test_split_scheme_reduces_to_random_without_forcing():
     f = fo.Forcing(N, 2.0, 3.0, 0.0, 0.5, seed=1)  # eps = 0: a = 0
     b = sc.step_ps_random(S0, 0.01, prob, da, forcing=f)
     np.testing.assert_allclose(a, b, atol=0)
+
+
+def test_cfl_step_taylor_green_closed_form():
+    # Taylor-Green: max|u_x| = max|u_y| = 1 on grids with N divisible by 4, u_z = 0, so
+    # dt = cfl dx / 2 (capped at dt_max)
+    from oracle import schemes as scx
+    for N in (8, 16, 32):
+        S = sp.set_velocity(inputs.taylor_green(N), N / 2)
+        dx = 2 * math.pi / N
+        assert abs(scx.cfl_time_step(S, [0, 0, 0], 0.4, 1.0, N) - 0.4 * dx / 2) < 1e-15
+        assert scx.cfl_time_step(S, [0, 0, 0], 0.4, 0.01, N) == 0.01
+    # a half-cell shift samples the field away from its maxima: the step gets longer
+    S = sp.set_velocity(inputs.taylor_green(8), 4.0)
+    dx = 2 * math.pi / 8
+    assert scx.cfl_time_step(S, [dx / 2] * 3, 0.4, 1.0, 8) > 0.4 * dx / 2
+
+
+def test_cfl_run_scales_with_the_velocity_and_caps():
+    from oracle import schemes as scx
+    N = 16
+    prob = scx.Problem(N, 0.01, N / 2)
+    S0 = sp.set_velocity(inputs.random_solenoidal(N, 2, kcut=5, energy_total=1.0), N / 2)
+    _, t1, d1 = scx.run_cfl(S0, 0.4, 1.0, 3, prob, scx.SCHEME_RK2)
+    # a velocity twice as large gives half the first step (CFL ~ 1/|u|)
+    _, _, d2 = scx.run_cfl(2 * S0, 0.4, 1.0, 1, prob, scx.SCHEME_RK2)
+    assert abs(d2[0] - d1[0] / 2) < 1e-15 * d1[0]
+    assert abs(t1 - sum(d1)) < 1e-15
+    # with a cap below every CFL step the run is the fixed-step run
+    S_a, t_a, d_a = scx.run_cfl(S0, 10.0, 1e-3, 3, prob, scx.SCHEME_PS_RANDOM, seed=4)
+    S_b, t_b = scx.run(S0, 1e-3, 3, prob, scx.SCHEME_PS_RANDOM, seed=4)
+    assert d_a == [1e-3] * 3 and np.array_equal(S_a, S_b) and t_a == t_b
