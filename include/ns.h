@@ -108,6 +108,14 @@ int ns_set_forcing(ns_ctx* ctx, int kind, double kf_min, double kf_max, double e
  * The random scheme draws delta_alpha of step s from splitmix64(seed, 3s+i) unless
  * ns_set_shifts supplied them.  Synchronises the context's stream before returning. */
 int ns_step(ns_ctx* ctx, double dt, int nsteps);
+/* Same, each step with an adaptive time step (Sec. 2: CFL condition, coefficient 0.4 for the
+ * RK2 schemes and 1.0 for RK4 in the paper): dt = min(dt_max, cfl / sum_i (max_x |u_i| / dx)),
+ * dx = 2 pi / N, the maxima taken over the grid values of the velocity that the step's first
+ * nonlinear evaluation forms (the state shifted by that evaluation's shift: delta_alpha for
+ * the random scheme, none otherwise), reduced inside the slab pass.  One 24-byte read-back
+ * per step.  ns_time gives the accumulated time.  NS_ERR_INVALID_ARG unless cfl > 0,
+ * dt_max > 0 (finite) and nsteps >= 0. */
+int ns_step_cfl(ns_ctx* ctx, double cfl, double dt_max, int nsteps);
 /* Test hook: delta_alpha for the next nsteps steps (host [nsteps][3], radians), consumed
  * by the following ns_step calls in order; delta_beta = delta_alpha + (pi/N)(1,1,1). */
 int ns_set_shifts(ns_ctx* ctx, const double* delta_alpha, int nsteps);

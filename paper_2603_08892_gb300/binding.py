@@ -62,6 +62,7 @@ _set_forcing = _sig("ns_set_forcing", ctypes.c_int,
                     [_vp, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                      ctypes.c_double, ctypes.c_uint64])
 _step = _sig("ns_step", ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_int])
+_step_cfl = _sig("ns_step_cfl", ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_double, ctypes.c_int])
 _set_shifts = _sig("ns_set_shifts", ctypes.c_int, [_vp, _dp, ctypes.c_int])
 _nonlinear = _sig("ns_nonlinear", ctypes.c_int, [_vp, _dp, _dp, _dp])
 _energy = _sig("ns_energy", ctypes.c_int, [_vp, _dp, _dp])
@@ -99,7 +100,7 @@ PROF_KINDS = {"k_pencil": 0, "k_yinv": 1, "k_xrow": 2, "k_yfwd": 3, "slab_pass":
 
 EXPORTED = ["ns_init", "ns_init_ex", "ns_init_error", "ns_destroy", "ns_last_error",
             "ns_set_velocity", "ns_get_velocity", "ns_get_state", "ns_set_state",
-            "ns_set_forcing", "ns_step", "ns_set_shifts", "ns_nonlinear", "ns_energy",
+            "ns_set_forcing", "ns_step", "ns_step_cfl", "ns_set_shifts", "ns_nonlinear", "ns_energy",
             "ns_energy_spectrum", "ns_energy_flux", "ns_time", "ns_set_time", "ns_device_state",
             "ns_model_bytes_per_step", "ns_fma_peak", "ns_profile", "ns_profile_read", "ns_nonlinear_noalloc", "ns_vjp", "ns_batch_init", "ns_batch_destroy", "ns_batch_last_error",
             "ns_batch_member", "ns_batch_set_velocity", "ns_batch_get_state", "ns_batch_step",
@@ -179,6 +180,10 @@ class Solver:
 
     def step(self, dt, nsteps=1):
         self._check(_step(self._h, dt, nsteps))
+
+    def step_cfl(self, cfl, dt_max, nsteps=1):
+        """nsteps steps with dt = min(dt_max, cfl / sum_i(max|u_i| / dx)) each (ns_step_cfl)."""
+        self._check(_step_cfl(self._h, float(cfl), float(dt_max), int(nsteps)))
 
     def set_shifts(self, delta_alpha):
         d = np.ascontiguousarray(delta_alpha, dtype=np.float64).reshape(-1, 3)

@@ -125,6 +125,7 @@ struct SolverBase {
   virtual void nonlinear(const double* in, const double* delta, double* out) = 0;
   virtual void energy(double* E, double* eps) = 0;
   virtual void spectrum(int kind, double* out, int nbins) = 0;
+  virtual void step_cfl(double cfl, double dt_max, int nsteps) = 0;
   virtual void energy_flux(const double* delta, int nshift, double* flux, double* cumd, int nbins) = 0;
   virtual void set_forcing(int kind, double kfmin, double kfmax, double eps, double tcorr,
                            uint64_t seed) = 0;
@@ -176,6 +177,9 @@ struct Solver : SolverBase {
   int red_blocks = 0;
   int* d_err = nullptr;
   double cur_dt = -1.0;
+  // adaptive time step (ns_step_cfl): dt = min(dt_max, cfl dx / sum_i max|u_i|) per step
+  double cfl = 0.0, cfl_dtmax = 0.0;
+  unsigned long long* d_umax = nullptr;
   // forcing
   int fkind = NS_FORCE_NONE, fK = 0;
   double fkmin = 0, fkmax = 0, feps = 0, ftcorr = 1, fD = 0;
@@ -330,6 +334,7 @@ struct Solver : SolverBase {
     red_blocks = 2 * nsm;
     CUDA_TRY(cudaMalloc(&red, (size_t)red_blocks * 1024 * sizeof(double)));
     CUDA_TRY(cudaMalloc(&d_err, sizeof(int)));
+    CUDA_TRY(cudaMalloc(&d_umax, 3 * sizeof(unsigned long long)));
     CUDA_TRY(cudaMemsetAsync(d_err, 0, sizeof(int), st));
     CUDA_TRY(cudaMemsetAsync(state, 0, 3 * F1 * cs, st));
     k_twiddle<T><<<(N + 255) / 256, 256, 0, st>>>(tw, N);
@@ -339,7 +344,7 @@ struct Solver : SolverBase {
 
   ~Solver() override {
     cudaFree(state); cudaFree(acc); cudaFree(mixed[0]); cudaFree(mixed[1]);
-    cudaFree(nlbuf); cudaFree(nltmp);
+    cudaFree(nlbuf); cudaFree(nltmp); cudaFree(d_umax);
     cudaFree(Ft[0]); cudaFree(Ft[1]); cudaFree(scr); cudaFree(tw); cudaFree(ifac);
     cudaFree(shtab); cudaFree(d_shifts); cudaFree(red); cudaFree(d_err);
     cudaFree(fpat); cudaFree(force); cudaFree(shell);
@@ -383,11 +388,15 @@ struct Solver : SolverBase {
   }
 
   // slab pass over every plane group: mixed (5 fields) -> Ft (3 fields)
-  void slab(const cpx<T>* mix, cpx<T>* out) {
+  void slab(const cpx<T>* mix, cpx<T>* out, bool umax = false) {
     SlabArgs<T> a = slab_args();
     a.mixed = mix;
     a.Ft = out;
     a.xmode = XMODE_NONLINEAR;
+    if (umax) {
+      CUDA_TRY(cudaMemsetAsync(d_umax, 0, 3 * sizeof(unsigned long long), st));
+      a.umax = d_umax;
+    }
     cudaEvent_t pass = prof_begin(NS_PROF_SLAB_PASS);
     for (int z0 = 0; z0 < N; z0 += G) {
       a.z0 = z0;
@@ -698,6 +707,18 @@ struct Solver : SolverBase {
   }
 
   // ---- schemes ------------------------------------------------------------------------
+  void step_cfl(double cfl_, double dt_max, int nsteps) override {
+    cfl = cfl_;
+    cfl_dtmax = dt_max;
+    try {
+      step(dt_max, nsteps);
+    } catch (...) {
+      cfl = 0.0;
+      throw;
+    }
+    cfl = 0.0;
+  }
+
   void step(double dt, int nsteps) override {
     if (!tuned) autotune();
     set_dt(dt);
@@ -752,14 +773,35 @@ struct Solver : SolverBase {
     pencil(a);
   }
 
-  void run_rogallo(double dt, int ns, bool approx) {
+  // time step of the coming step: fixed, or from the maxima of the velocity that the step's
+  // first slab pass has just formed (adaptive: one read-back per step)
+  double step_dt(double dt) {
+    if (cfl <= 0.0) return dt;
+    // the kernels fold the maxima into T-sized words: unsigned[3] (FP32) or uint64[3] (FP64)
+    unsigned char h[3 * sizeof(unsigned long long)];
+    CUDA_TRY(cudaMemcpyAsync(h, d_umax, 3 * sizeof(T), cudaMemcpyDeviceToHost, st));
+    sync_check();
+    double freq = 0.0;
+    for (int i = 0; i < 3; ++i) {
+      T m;
+      std::memcpy(&m, h + i * sizeof(T), sizeof(T));
+      freq += (double)m / (2.0 * M_PI / N);
+    }
+    double d = freq > 0.0 ? cfl / freq : cfl_dtmax;
+    if (d > cfl_dtmax) d = cfl_dtmax;
+    set_dt(d);
+    return d;
+  }
+
+  void run_rogallo(double dt0, int ns, bool approx) {
     const T w = (T)(1.0 / ((double)N * N * N));
     auto alpha = [&](int n) -> const cpx<T>* { return approx ? nullptr : shift_tab(2 * n); };
     auto beta = [&](int n) -> const cpx<T>* { return shift_tab(2 * n + 1); };
     init_pass(1, alpha(0), nullptr);
     for (int n = 0; n < ns; ++n) {
       const double t = c->t;
-      slab(mixed[0], Ft[0]);
+      slab(mixed[0], Ft[0], cfl > 0.0);
+      const double dt = step_dt(dt0);
       PencilArgs<T> a = pencil_args(MODE_ROG_1);
       force_coef(t, a);
       a.nF = 1; a.F[0] = Ft[0]; a.dsh[0] = alpha(n); a.wF[0] = w;
@@ -779,14 +821,16 @@ struct Solver : SolverBase {
     }
   }
 
-  void run_rk2(double dt, int ns, bool exact) {
+  void run_rk2(double dt0, int ns, bool exact) {
     const T w = (T)(1.0 / ((double)N * N * N));
     const cpx<T>* iso = exact ? shift_tab(0) : nullptr;
     init_pass(exact ? 2 : 1, nullptr, iso);
     for (int n = 0; n < ns; ++n) {
       const double t = c->t;
+      double dt = dt0;
       for (int stg = 0; stg < 2; ++stg) {
-        slab(mixed[0], Ft[0]);
+        slab(mixed[0], Ft[0], stg == 0 && cfl > 0.0);
+        if (stg == 0) dt = step_dt(dt0);
         if (exact) slab(mixed[1], Ft[1]);
         PencilArgs<T> a = pencil_args(stg == 0 ? MODE_RK2_1 : MODE_RK2_2);
         force_coef(stg == 0 ? t : t + 0.5 * dt, a);
@@ -804,15 +848,17 @@ struct Solver : SolverBase {
     }
   }
 
-  void run_rk4(double dt, int ns) {
+  void run_rk4(double dt0, int ns) {
     const T w = (T)(1.0 / ((double)N * N * N));
     init_pass(1, nullptr, nullptr);
     const int modes[4] = {MODE_RK4_1, MODE_RK4_2, MODE_RK4_3, MODE_RK4_4};
     const double ts[4] = {0.0, 0.5, 0.5, 1.0};
     for (int n = 0; n < ns; ++n) {
       const double t = c->t;
+      double dt = dt0;
       for (int stg = 0; stg < 4; ++stg) {
-        slab(mixed[0], Ft[0]);
+        slab(mixed[0], Ft[0], stg == 0 && cfl > 0.0);
+        if (stg == 0) dt = step_dt(dt0);
         PencilArgs<T> a = pencil_args(modes[stg]);
         force_coef(t + ts[stg] * dt, a);
         a.nF = 1; a.F[0] = Ft[0]; a.wF[0] = w;
@@ -1391,6 +1437,17 @@ int ns_step(ns_ctx* c, double dt, int nsteps) {
     if (!(dt > 0.0) || !std::isfinite(dt) || nsteps < 0) return fail(c, NS_ERR_INVALID_ARG, "need dt > 0, nsteps >= 0");
     if (nsteps == 0) return (int)NS_OK;
     c->solver->step(dt, nsteps);
+    return (int)NS_OK;
+  });
+}
+
+int ns_step_cfl(ns_ctx* c, double cfl, double dt_max, int nsteps) {
+  return guarded(c, [&]() {
+    if (!c->have_state) return fail(c, NS_ERR_STATE, "no velocity or state set");
+    if (!(cfl > 0.0) || !std::isfinite(cfl) || !(dt_max > 0.0) || !std::isfinite(dt_max) || nsteps < 0)
+      return fail(c, NS_ERR_INVALID_ARG, "need cfl > 0, dt_max > 0, nsteps >= 0");
+    if (nsteps == 0) return (int)NS_OK;
+    c->solver->step_cfl(cfl, dt_max, nsteps);
     return (int)NS_OK;
   });
 }

@@ -310,7 +310,40 @@ struct SlabArgs {
   T* rio;               // physical rows [3][N][N][N] (C2R output / R2C input)
   int TY, RX, xmode;
   int* err;
+  void* umax;           // or null: max_x |u_i(x)| of the velocity rows, i = 0..2, folded in
+                        // with atomicMax on the IEEE bits (unsigned / unsigned long long [3])
 };
+
+// Block maxima m0..m2 (non-negative) folded into umax[0..2], one atomic per value per block:
+// the bit patterns of non-negative IEEE numbers order like the numbers, so an unsigned
+// atomicMax is a max of the values.  scratch: 3 (blockDim.x / 32) values of shared memory
+// that are free during the call; every thread of the block calls it (blockDim.x is a
+// multiple of 32).
+template <typename T>
+__device__ void block_max3(T m0, T m1, T m2, T* scratch, void* umax) {
+  for (int o = 16; o > 0; o >>= 1) {
+    m0 = fmax(m0, __shfl_xor_sync(0xffffffffu, m0, o));
+    m1 = fmax(m1, __shfl_xor_sync(0xffffffffu, m1, o));
+    m2 = fmax(m2, __shfl_xor_sync(0xffffffffu, m2, o));
+  }
+  const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if ((threadIdx.x & 31) == 0) {
+    scratch[3 * w] = m0;
+    scratch[3 * w + 1] = m1;
+    scratch[3 * w + 2] = m2;
+  }
+  __syncthreads();
+  if (threadIdx.x < 3) {
+    T m = T(0);
+    for (int i = 0; i < nw; ++i) m = fmax(m, scratch[3 * i + threadIdx.x]);
+    if (sizeof(T) == 4)
+      atomicMax(static_cast<unsigned*>(umax) + threadIdx.x, __float_as_uint((float)m));
+    else
+      atomicMax(static_cast<unsigned long long*>(umax) + threadIdx.x,
+                (unsigned long long)__double_as_longlong((double)m));
+  }
+  __syncthreads();
+}
 
 // inverse y transforms; forms omega = i k x u from the mixed fields (nonlinear mode) or
 // passes the velocity only (C2R mode).  grid (M/TY, G)
@@ -500,14 +533,20 @@ __global__ void __launch_bounds__(512) k_xrow(SlabArgs<T> a) {
     // (fields 0..2) x (fields 3..5) on the packed real rows, written over fields 0..2
     T* re = reinterpret_cast<T*>(buf);
     const int rt = 2 * tile;  // reals per field
+    T m0 = 0, m1 = 0, m2 = 0;
     for (int e = threadIdx.x; e < 2 * nr * M; e += blockDim.x) {
       const T u0 = re[e], u1 = re[rt + e], u2 = re[2 * rt + e];
       const T w0 = re[3 * rt + e], w1 = re[4 * rt + e], w2 = re[5 * rt + e];
+      m0 = fmax(m0, fabs(u0));
+      m1 = fmax(m1, fabs(u1));
+      m2 = fmax(m2, fabs(u2));
       re[e] = u1 * w2 - u2 * w1;
       re[rt + e] = u2 * w0 - u0 * w2;
       re[2 * rt + e] = u0 * w1 - u1 * w0;
     }
     __syncthreads();
+    // CFL: max |u_i| of the rows (omega, fields 3..5, is no longer needed: scratch)
+    if (a.umax && a.xmode == XMODE_NONLINEAR) block_max3<T>(m0, m1, m2, re + 3 * rt, a.umax);
   }
 
   // forward r2c of fields 0..2

@@ -765,6 +765,7 @@ __device__ __forceinline__ void xrow_tile(const SlabArgs<T>& a, int tile_id, cpx
   __syncthreads();
 
   // u x omega on the packed real rows, written over u
+  T m[3] = {T(0), T(0), T(0)};  // max |u_i| over the rows (CFL), padding rows are zero
   for (int i = threadIdx.x; act && i < RX * M; i += NT) {
     const int row = i / M, k = i % M;
     cpx<T> u[3], w[3];
@@ -772,6 +773,7 @@ __device__ __forceinline__ void xrow_tile(const SlabArgs<T>& a, int tile_id, cpx
     for (int c = 0; c < 3; ++c) {
       u[c] = U.get(c * RX + row, k);
       w[c] = V.get(c * RX + row, k);
+      m[c] = fmax(m[c], fmax(fabs(u[c].x), fabs(u[c].y)));
     }
     // real parts are x_{2k}, imaginary parts x_{2k+1}
     const cpx<T> f0 = mk<T>(u[1].x * w[2].x - u[2].x * w[1].x, u[1].y * w[2].y - u[2].y * w[1].y);
@@ -782,6 +784,7 @@ __device__ __forceinline__ void xrow_tile(const SlabArgs<T>& a, int tile_id, cpx
     U.put(2 * RX + row, k, f2);
   }
   __syncthreads();
+  if (a.umax) block_max3<T>(m[0], m[1], m[2], reinterpret_cast<T*>(V.p), a.umax);  // V is free
   cfft_ip<T, M, 2, 3 * RX, NT, false, -1, true, C::RXR>(U, U.p, tws);
   __syncthreads();
 
