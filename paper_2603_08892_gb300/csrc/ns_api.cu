@@ -12,6 +12,7 @@
 #include <cuda_runtime.h>
 #include <sys/stat.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -291,8 +292,9 @@ struct Solver : SolverBase {
     G = (int)((48ull << 20) / plane6);
     if (G < 1) G = 1;
     if (G > N) G = N;
-    // the scratch holds up to Gmax planes: the autotuner may pick any group size up to it
-    Gmax = (int)((96ull << 20) / plane6);
+    // the scratch holds up to Gmax planes (at most 1 GB): the autotuner may pick any group
+    // size up to it; on GB300 groups larger than L2 measured faster (fewer launch tails)
+    Gmax = (int)((1024ull << 20) / plane6);
     if (Gmax < G) Gmax = G;
     if (Gmax > N) Gmax = N;
 
@@ -674,7 +676,7 @@ struct Solver : SolverBase {
       return;
     }
     std::vector<int> cand;
-    for (int q : {8, 12, 16, 19, 24, 28, 32, 38, 43, 48, 57, 64, 76, 96, 128})
+    for (int q : {8, 12, 16, 19, 24, 28, 32, 38, 43, 48, 57, 64, 76, 96, 128, 171, 256, 384, 512, 768})
       if (q <= Gmax) cand.push_back(q);
     if (cand.empty()) return;
     CUDA_TRY(cudaMemsetAsync(mixed[0], 0, 5 * F1 * sizeof(cpx<T>), st));
