@@ -178,6 +178,19 @@ struct Solver : SolverBase {
   int red_blocks = 0;
   int* d_err = nullptr;
   double cur_dt = -1.0;
+  // slab pass on two internal streams (plane groups alternate, double-buffered scratch) so
+  // the kernels of one group overlap those of the next; chosen by the autotuner
+  int slab_streams = 1;
+  cudaStream_t ss[2] = {nullptr, nullptr};
+  cudaEvent_t ev_fork = nullptr, ev_join[2] = {nullptr, nullptr};
+  void ensure_streams() {
+    if (ss[0]) return;
+    for (int i = 0; i < 2; ++i) {
+      CUDA_TRY(cudaStreamCreateWithFlags(&ss[i], cudaStreamNonBlocking));
+      CUDA_TRY(cudaEventCreateWithFlags(&ev_join[i], cudaEventDisableTiming));
+    }
+    CUDA_TRY(cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming));
+  }
   // adaptive time step (ns_step_cfl): dt = min(dt_max, cfl dx / sum_i max|u_i|) per step
   double cfl = 0.0, cfl_dtmax = 0.0;
   unsigned long long* d_umax = nullptr;
@@ -223,16 +236,16 @@ struct Solver : SolverBase {
     return e;
   }
   // brackets one launch (or a pass) of kind k; returns the stop event to record after it
-  cudaEvent_t prof_begin(int k) {
+  cudaEvent_t prof_begin(int k, cudaStream_t s = nullptr) {
     prof.launches[k] += 1;
     if (!prof.on || prof.rec.size() >= 65536) return nullptr;
     cudaEvent_t a = prof_event(), b = prof_event();
-    CUDA_TRY(cudaEventRecord(a, st));
+    CUDA_TRY(cudaEventRecord(a, s ? s : st));
     prof.rec.push_back({k, {a, b}});
     return b;
   }
-  void prof_end(cudaEvent_t b) {
-    if (b) CUDA_TRY(cudaEventRecord(b, st));
+  void prof_end(cudaEvent_t b, cudaStream_t s = nullptr) {
+    if (b) CUDA_TRY(cudaEventRecord(b, s ? s : st));
   }
   void prof_collect() {
     CUDA_TRY(cudaStreamSynchronize(st));
@@ -350,6 +363,11 @@ struct Solver : SolverBase {
     cudaFree(Ft[0]); cudaFree(Ft[1]); cudaFree(scr); cudaFree(tw); cudaFree(ifac);
     cudaFree(shtab); cudaFree(d_shifts); cudaFree(red); cudaFree(d_err);
     cudaFree(fpat); cudaFree(force); cudaFree(shell);
+    for (int i = 0; i < 2; ++i) {
+      if (ss[i]) cudaStreamDestroy(ss[i]);
+      if (ev_join[i]) cudaEventDestroy(ev_join[i]);
+    }
+    if (ev_fork) cudaEventDestroy(ev_fork);
     for (auto* p : adj) cudaFree(p);
     cudaFree(mixedB); cudaFree(FtB); cudaFree(shS); cudaFree(shR); cudaFree(ftab);
     for (auto& r : prof.rec) {
@@ -400,27 +418,42 @@ struct Solver : SolverBase {
       a.umax = d_umax;
     }
     cudaEvent_t pass = prof_begin(NS_PROF_SLAB_PASS);
-    for (int z0 = 0; z0 < N; z0 += G) {
+    const bool two = use2 && slab_streams == 2 && G < N && 2 * G <= Gmax;
+    if (two) {
+      ensure_streams();
+      CUDA_TRY(cudaEventRecord(ev_fork, st));
+      for (int i = 0; i < 2; ++i) CUDA_TRY(cudaStreamWaitEvent(ss[i], ev_fork, 0));
+    }
+    int gi = 0;
+    for (int z0 = 0; z0 < N; z0 += G, ++gi) {
+      const cudaStream_t s = two ? ss[gi & 1] : st;
       a.z0 = z0;
       a.G = (z0 + G <= N) ? G : N - z0;
-      cudaEvent_t e = prof_begin(NS_PROF_YINV);
+      a.scr = scr + (two ? (size_t)(gi & 1) * 6 * G * N * M : 0);  // double-buffered scratch
+      cudaEvent_t e = prof_begin(NS_PROF_YINV, s);
       if (use2)
-        k2.yinv<<<dim3(M / k2.TYI, a.G), k2.NTYI, k2.smYI, st>>>(a);
+        k2.yinv<<<dim3(M / k2.TYI, a.G), k2.NTYI, k2.smYI, s>>>(a);
       else
-        k_yinv<T><<<dim3(M / TY, a.G), bdYi, smYi, st>>>(a);
-      prof_end(e);
-      e = prof_begin(NS_PROF_XROW);
+        k_yinv<T><<<dim3(M / TY, a.G), bdYi, smYi, s>>>(a);
+      prof_end(e, s);
+      e = prof_begin(NS_PROF_XROW, s);
       if (use2)
-        k2.xrow<<<(a.G * N + k2.RX - 1) / k2.RX, k2.NTX, k2.smX, st>>>(a);
+        k2.xrow<<<(a.G * N + k2.RX - 1) / k2.RX, k2.NTX, k2.smX, s>>>(a);
       else
-        k_xrow<T><<<(a.G * N + RX - 1) / RX, bdX, smX, st>>>(a);
-      prof_end(e);
-      e = prof_begin(NS_PROF_YFWD);
+        k_xrow<T><<<(a.G * N + RX - 1) / RX, bdX, smX, s>>>(a);
+      prof_end(e, s);
+      e = prof_begin(NS_PROF_YFWD, s);
       if (use2)
-        k2.yfwd<<<dim3(M / k2.TY, a.G), k2.NTY, k2.smY, st>>>(a);
+        k2.yfwd<<<dim3(M / k2.TY, a.G), k2.NTY, k2.smY, s>>>(a);
       else
-        k_yfwd<T><<<dim3(M / TY, a.G), bdYf, smYf, st>>>(a);
-      prof_end(e);
+        k_yfwd<T><<<dim3(M / TY, a.G), bdYf, smYf, s>>>(a);
+      prof_end(e, s);
+    }
+    if (two) {
+      for (int i = 0; i < 2; ++i) {
+        CUDA_TRY(cudaEventRecord(ev_join[i], ss[i]));
+        CUDA_TRY(cudaStreamWaitEvent(st, ev_join[i], 0));
+      }
     }
     prof_end(pass);
     LAUNCH_CHECK();
@@ -583,11 +616,11 @@ struct Solver : SolverBase {
   }
 
   // ---- autotuner of the plane-group size of the slab pass ------------------------------
-  // Candidates G (planes per group of the L2-resident scratch) are timed on the slab pass
-  // with CUDA events; the fastest is kept and cached in a JSON file keyed by device, N and
-  // precision.  Results do not depend on G (every plane is transformed the same way).
-  // NS_AUTOTUNE=0 disables it; NS_AUTOTUNE_CACHE sets the cache file; NS_SLAB_PLANES=g
-  // forces a group size.
+  // Candidates G (planes per group of the scratch) with one or two streams are timed on the
+  // slab pass with CUDA events; the fastest is kept and cached in a JSON file keyed by device,
+  // N, precision and the slab tiles.  Results do not depend on G or on the streams (every
+  // plane is transformed the same way).  NS_AUTOTUNE=0 disables it; NS_AUTOTUNE_CACHE sets the
+  // cache file; NS_SLAB_PLANES=g forces a group size, NS_SLAB_STREAMS=1|2 the stream count.
   static std::string cache_path() {
     const char* e = std::getenv("NS_AUTOTUNE_CACHE");
     if (e && *e) return e;
@@ -659,8 +692,10 @@ struct Solver : SolverBase {
     ::mkdir(d.c_str(), 0755);
   }
 
+  // The cached value encodes the group size and the stream count: 2 G + (streams - 1).
   void autotune() {
     tuned = true;
+    if (const char* fs = std::getenv("NS_SLAB_STREAMS")) slab_streams = std::atoi(fs) == 2 ? 2 : 1;
     if (const char* fg = std::getenv("NS_SLAB_PLANES")) {  // forced group size
       const int g = std::atoi(fg);
       if (g >= 1) G = g < Gmax ? g : Gmax;
@@ -669,10 +704,11 @@ struct Solver : SolverBase {
     const char* en = std::getenv("NS_AUTOTUNE");
     if (en && std::string(en) == "0") return;
     if (Gmax <= 1 || N < 128) return;  // small grids: one group holds every plane
-    const std::string path = cache_path(), key = tune_key();
+    const std::string path = cache_path(), key = tune_key() + "|g2s";
     int g = 0;
-    if (cache_lookup(path, key, &g) && g >= 1 && g <= Gmax) {
-      G = g;
+    if (cache_lookup(path, key, &g) && g / 2 >= 1 && g / 2 <= Gmax) {
+      G = g / 2;
+      slab_streams = 1 + (g & 1);
       return;
     }
     std::vector<int> cand;
@@ -686,26 +722,32 @@ struct Solver : SolverBase {
     const bool pon = prof.on;
     prof.on = false;
     float best = 1e30f;
-    int bestG = G;
+    int bestG = G, bestS = 1;
     for (int q : cand) {
-      G = q;
-      slab(mixed[0], Ft[0]);  // warm-up
-      CUDA_TRY(cudaEventRecord(e0, st));
-      for (int r = 0; r < 8; ++r) slab(mixed[0], Ft[0]);
-      CUDA_TRY(cudaEventRecord(e1, st));
-      CUDA_TRY(cudaEventSynchronize(e1));
-      float ms = 0;
-      CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
-      if (ms < best) {
-        best = ms;
-        bestG = q;
+      for (int ns2 = 1; ns2 <= 2; ++ns2) {
+        if (ns2 == 2 && (q >= N || 2 * q > Gmax)) continue;  // two streams need two groups
+        G = q;
+        slab_streams = ns2;
+        slab(mixed[0], Ft[0]);  // warm-up
+        CUDA_TRY(cudaEventRecord(e0, st));
+        for (int r = 0; r < 8; ++r) slab(mixed[0], Ft[0]);
+        CUDA_TRY(cudaEventRecord(e1, st));
+        CUDA_TRY(cudaEventSynchronize(e1));
+        float ms = 0;
+        CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+        if (ms < best) {
+          best = ms;
+          bestG = q;
+          bestS = ns2;
+        }
       }
     }
     prof.on = pon;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     G = bestG;
-    cache_store(path, key, G);
+    slab_streams = bestS;
+    cache_store(path, key, 2 * G + (slab_streams - 1));
   }
 
   // ---- schemes ------------------------------------------------------------------------
@@ -1080,7 +1122,12 @@ struct Solver : SolverBase {
     const int nck = (nsteps + ckpt - 1) / ckpt + 1;
     const int nvec = 12 + nseg_states + nck;
     if ((int)adj.size() < nvec) {
-      for (auto* p : adj) cudaFree(p);
+      for (int i = 0; i < 2; ++i) {
+      if (ss[i]) cudaStreamDestroy(ss[i]);
+      if (ev_join[i]) cudaEventDestroy(ev_join[i]);
+    }
+    if (ev_fork) cudaEventDestroy(ev_fork);
+    for (auto* p : adj) cudaFree(p);
       adj.assign(nvec, nullptr);
       for (int i = 0; i < nvec; ++i) CUDA_TRY(cudaMalloc(&adj[i], vb));
       if (!mixedB) CUDA_TRY(cudaMalloc(&mixedB, 5 * F1 * sizeof(cpx<T>)));

@@ -300,21 +300,24 @@ def test_specialised_and_generic_kernels_agree(ns, prec, code, monkeypatch):
 
 
 def test_results_do_not_depend_on_slab_group_size(ns, monkeypatch, tmp_path):
-    # the autotuner only changes how many planes share the L2-resident scratch
+    # the autotuner only changes how the planes are grouped and on how many streams the
+    # groups run (double-buffered scratch): the arithmetic of every plane is the same
     N = 128
     u = field(N, seed=31)
     out = []
     monkeypatch.setenv("NS_AUTOTUNE_CACHE", str(tmp_path / "tune.json"))
-    for g in ("5", "128", None):
-        if g is None:
-            monkeypatch.delenv("NS_SLAB_PLANES", raising=False)
-        else:
-            monkeypatch.setenv("NS_SLAB_PLANES", g)
+    for g, streams in (("5", "1"), ("128", "1"), ("24", "2"), ("5", "2"), (None, None)):
+        for var, val in (("NS_SLAB_PLANES", g), ("NS_SLAB_STREAMS", streams)):
+            if val is None:
+                monkeypatch.delenv(var, raising=False)
+            else:
+                monkeypatch.setenv(var, val)
         with ns.Solver(N, 0.001, N / 2, scheme=4, precision=0, seed=3) as s:
             s.set_velocity(u)
             s.step(0.005, 2)
             out.append(s.get_state())
-    assert np.array_equal(out[0], out[1]) and np.array_equal(out[0], out[2])
+    for o in out[1:]:
+        assert np.array_equal(out[0], o)
     assert (tmp_path / "tune.json").exists()
 
 
