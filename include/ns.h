@@ -41,7 +41,8 @@ typedef enum {
   NS_ERR_NONFINITE = 6,    /* energy or dissipation is NaN/Inf                          */
   NS_ERR_TIMEOUT = 7,      /* a bounded device-side wait gave up                        */
   NS_ERR_STATE = 8,        /* call out of order (e.g. step before a velocity was set)   */
-  NS_ERR_INTERNAL = 9      /* a device-side consistency check failed (bad launch shape) */
+  NS_ERR_INTERNAL = 9,     /* a device-side consistency check failed (bad launch shape) */
+  NS_ERR_IO = 10           /* a checkpoint file could not be written or read, or is not one */
 } ns_status;
 
 /* Truncations (Sec. 3.2, Fig. truncation:common; Sec. 4.2, Fig.
@@ -160,6 +161,19 @@ int ns_energy_spectrum(ns_ctx* ctx, int kind, double* out, int nbins);
  * work fields of the state's size; synchronises the context's stream.  Returns
  * NS_ERR_INVALID_ARG for nbins outside 1..4096, nshift outside 0..8 or a non-finite shift. */
 int ns_energy_flux(ns_ctx* ctx, const double* delta, int nshift, double* flux, double* cumdiss, int nbins);
+
+/* Checkpoint of a context to a file, for a bitwise resume: the state in the context's own
+ * precision (FP32 or FP64 complex, [3][N][N][N/2], host byte order), time, step count, shift
+ * seed and the forcing parameters, after a header with N, precision, scheme, truncation, kmax
+ * and nu.  Written to path + ".tmp" and renamed over path.  ns_checkpoint_load reads such a
+ * file into a context created with the same N, precision, scheme, truncation, kmax and nu
+ * (else NS_ERR_INVALID_ARG) and restores the state, time, step, seed and forcing; stepping on
+ * then gives the same bits as an uninterrupted run.  NS_ERR_IO for a file that cannot be
+ * written or read, a wrong magic or a truncated file; NS_ERR_STATE to save a context without
+ * a state.  Both synchronise the context's stream.  The paper has no counterpart (its runs
+ * restart through Fluidsim's files). */
+int ns_checkpoint_save(ns_ctx* ctx, const char* path);
+int ns_checkpoint_load(ns_ctx* ctx, const char* path);
 
 /* Simulated time and number of steps done since the last ns_set_velocity. */
 int ns_time(ns_ctx* ctx, double* t, int64_t* step);

@@ -25,7 +25,7 @@ _lib = ctypes.CDLL(LIB_PATH)
 NS_OK = 0
 ERRORS = {1: "NS_ERR_INVALID_ARG", 2: "NS_ERR_UNSUPPORTED_N", 3: "NS_ERR_KMAX", 4: "NS_ERR_CUDA",
           5: "NS_ERR_OOM", 6: "NS_ERR_NONFINITE", 7: "NS_ERR_TIMEOUT", 8: "NS_ERR_STATE",
-          9: "NS_ERR_INTERNAL"}
+          9: "NS_ERR_INTERNAL", 10: "NS_ERR_IO"}
 TRUNC_SPHERICAL, TRUNC_CUBIC, TRUNC_NO_DOUBLE_ALIAS = 0, 1, 2
 RK2, RK4, RK2_PS_EXACT, RK2_PS_APPROX, RK2_PS_RANDOM = 0, 1, 2, 3, 4
 FP32, FP64 = 0, 1
@@ -63,6 +63,8 @@ _set_forcing = _sig("ns_set_forcing", ctypes.c_int,
                      ctypes.c_double, ctypes.c_uint64])
 _step = _sig("ns_step", ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_int])
 _step_cfl = _sig("ns_step_cfl", ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_double, ctypes.c_int])
+_ckpt_save = _sig("ns_checkpoint_save", ctypes.c_int, [_vp, ctypes.c_char_p])
+_ckpt_load = _sig("ns_checkpoint_load", ctypes.c_int, [_vp, ctypes.c_char_p])
 _set_shifts = _sig("ns_set_shifts", ctypes.c_int, [_vp, _dp, ctypes.c_int])
 _nonlinear = _sig("ns_nonlinear", ctypes.c_int, [_vp, _dp, _dp, _dp])
 _energy = _sig("ns_energy", ctypes.c_int, [_vp, _dp, _dp])
@@ -100,7 +102,8 @@ PROF_KINDS = {"k_pencil": 0, "k_yinv": 1, "k_xrow": 2, "k_yfwd": 3, "slab_pass":
 
 EXPORTED = ["ns_init", "ns_init_ex", "ns_init_error", "ns_destroy", "ns_last_error",
             "ns_set_velocity", "ns_get_velocity", "ns_get_state", "ns_set_state",
-            "ns_set_forcing", "ns_step", "ns_step_cfl", "ns_set_shifts", "ns_nonlinear", "ns_energy",
+            "ns_set_forcing", "ns_step", "ns_step_cfl", "ns_set_shifts",
+            "ns_checkpoint_save", "ns_checkpoint_load", "ns_nonlinear", "ns_energy",
             "ns_energy_spectrum", "ns_energy_flux", "ns_time", "ns_set_time", "ns_device_state",
             "ns_model_bytes_per_step", "ns_fma_peak", "ns_profile", "ns_profile_read", "ns_nonlinear_noalloc", "ns_vjp", "ns_batch_init", "ns_batch_destroy", "ns_batch_last_error",
             "ns_batch_member", "ns_batch_set_velocity", "ns_batch_get_state", "ns_batch_step",
@@ -184,6 +187,14 @@ class Solver:
     def step_cfl(self, cfl, dt_max, nsteps=1):
         """nsteps steps with dt = min(dt_max, cfl / sum_i(max|u_i| / dx)) each (ns_step_cfl)."""
         self._check(_step_cfl(self._h, float(cfl), float(dt_max), int(nsteps)))
+
+    def checkpoint_save(self, path):
+        """Write the state, time, step, seed and forcing to a file (ns_checkpoint_save)."""
+        self._check(_ckpt_save(self._h, os.fsencode(path)))
+
+    def checkpoint_load(self, path):
+        """Restore a checkpoint written by a context of the same configuration."""
+        self._check(_ckpt_load(self._h, os.fsencode(path)))
 
     def set_shifts(self, delta_alpha):
         d = np.ascontiguousarray(delta_alpha, dtype=np.float64).reshape(-1, 3)

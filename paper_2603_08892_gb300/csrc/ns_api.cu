@@ -127,6 +127,9 @@ struct SolverBase {
   virtual void energy(double* E, double* eps) = 0;
   virtual void spectrum(int kind, double* out, int nbins) = 0;
   virtual void step_cfl(double cfl, double dt_max, int nsteps) = 0;
+  virtual void raw_state(std::vector<unsigned char>& out) = 0;         // native-precision bytes
+  virtual void set_raw_state(const unsigned char* in, size_t n) = 0;
+  virtual void forcing_params(int* kind, double* v, uint64_t* seed) = 0;  // v: kmin, kmax, eps, tcorr
   virtual void energy_flux(const double* delta, int nshift, double* flux, double* cumd, int nbins) = 0;
   virtual void set_forcing(int kind, double kfmin, double kfmax, double eps, double tcorr,
                            uint64_t seed) = 0;
@@ -988,6 +991,21 @@ struct Solver : SolverBase {
   }
 
   void get_state(double* s) override { download(state, s); }
+  void raw_state(std::vector<unsigned char>& out) override {
+    out.resize(3 * F1 * sizeof(cpx<T>));
+    CUDA_TRY(cudaMemcpyAsync(out.data(), state, out.size(), cudaMemcpyDeviceToHost, st));
+    sync_check();
+  }
+  void set_raw_state(const unsigned char* in, size_t n) override {
+    if (n != 3 * F1 * sizeof(cpx<T>)) throw NsError{NS_ERR_IO, "checkpoint state size mismatch"};
+    CUDA_TRY(cudaMemcpyAsync(state, in, n, cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+  }
+  void forcing_params(int* kind, double* v, uint64_t* seed) override {
+    *kind = fkind;
+    v[0] = fkmin; v[1] = fkmax; v[2] = feps; v[3] = ftcorr;
+    *seed = fseed;
+  }
   void set_state(const double* s) override { upload(s, state); }
 
   void nonlinear(const double* in, const double* delta, double* out) override {
@@ -1545,6 +1563,81 @@ int ns_energy_flux(ns_ctx* c, const double* delta, int nshift, double* flux, dou
     for (int i = 0; i < 3 * nshift; ++i)
       if (!std::isfinite(delta[i])) return fail(c, NS_ERR_INVALID_ARG, "non-finite shift");
     c->solver->energy_flux(delta, nshift, flux, cumdiss, nbins);
+    return (int)NS_OK;
+  });
+}
+
+namespace {
+struct CkptHeader {
+  char magic[8];
+  int32_t version, N, precision, scheme, truncation, fkind;
+  double kmax, nu;
+  uint64_t seed;
+  double t;
+  int64_t step;
+  double fv[4];
+  uint64_t fseed;
+  uint64_t nbytes;
+};
+const char kCkptMagic[8] = {'N', 'S', 'C', 'K', 'P', 'T', '0', '1'};
+}  // namespace
+
+int ns_checkpoint_save(ns_ctx* c, const char* path) {
+  return guarded(c, [&]() {
+    if (!path) return fail(c, NS_ERR_INVALID_ARG, "null path");
+    if (!c->have_state) return fail(c, NS_ERR_STATE, "no velocity or state set");
+    std::vector<unsigned char> raw;
+    c->solver->raw_state(raw);
+    CkptHeader h;
+    memset(&h, 0, sizeof(h));
+    memcpy(h.magic, kCkptMagic, 8);
+    h.version = 1; h.N = c->p.N; h.precision = c->p.precision; h.scheme = c->p.scheme;
+    h.truncation = c->p.truncation; h.kmax = c->p.kmax; h.nu = c->p.nu; h.seed = c->p.seed;
+    h.t = c->t; h.step = c->step;
+    c->solver->forcing_params(&h.fkind, h.fv, &h.fseed);
+    h.nbytes = raw.size();
+    const std::string tmp = std::string(path) + ".tmp";
+    FILE* f = std::fopen(tmp.c_str(), "wb");
+    if (!f) return fail(c, NS_ERR_IO, "cannot open " + tmp);
+    const bool ok = std::fwrite(&h, sizeof(h), 1, f) == 1 &&
+                    std::fwrite(raw.data(), 1, raw.size(), f) == raw.size();
+    const bool closed = std::fclose(f) == 0;
+    if (!ok || !closed) {
+      std::remove(tmp.c_str());
+      return fail(c, NS_ERR_IO, "write failed: " + tmp);
+    }
+    if (std::rename(tmp.c_str(), path) != 0) return fail(c, NS_ERR_IO, "rename failed: " + std::string(path));
+    return (int)NS_OK;
+  });
+}
+
+int ns_checkpoint_load(ns_ctx* c, const char* path) {
+  return guarded(c, [&]() {
+    if (!path) return fail(c, NS_ERR_INVALID_ARG, "null path");
+    FILE* f = std::fopen(path, "rb");
+    if (!f) return fail(c, NS_ERR_IO, "cannot open " + std::string(path));
+    CkptHeader h;
+    std::vector<unsigned char> raw;
+    bool ok = std::fread(&h, sizeof(h), 1, f) == 1 && memcmp(h.magic, kCkptMagic, 8) == 0 && h.version == 1 &&
+              h.nbytes < (1ull << 40);
+    if (ok) {
+      raw.resize(h.nbytes);
+      ok = std::fread(raw.data(), 1, raw.size(), f) == raw.size();
+    }
+    std::fclose(f);
+    if (!ok) return fail(c, NS_ERR_IO, "not a complete checkpoint: " + std::string(path));
+    if (h.N != c->p.N || h.precision != c->p.precision || h.scheme != c->p.scheme ||
+        h.truncation != c->p.truncation || h.kmax != c->p.kmax || h.nu != c->p.nu)
+      return fail(c, NS_ERR_INVALID_ARG, "checkpoint of another configuration");
+    c->solver->set_raw_state(raw.data(), raw.size());
+    if (h.fkind != NS_FORCE_NONE)
+      c->solver->set_forcing(h.fkind, h.fv[0], h.fv[1], h.fv[2], h.fv[3], h.fseed);
+    c->p.seed = h.seed;
+    c->t = h.t;
+    c->step = h.step;
+    c->override_shifts.clear();
+    c->override_pos = 0;
+    c->have_state = true;
     return (int)NS_OK;
   });
 }
