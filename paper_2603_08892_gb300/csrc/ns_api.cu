@@ -326,7 +326,7 @@ struct Solver : SolverBase {
     CUDA_TRY(cudaFuncSetAttribute(k_xrow<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
     use2 = k2_find(N, &k2);
     if (use2) {
-      if ((int)k2.smP5 > optin || (int)k2.smX > optin || (int)k2.smY > optin || (int)k2.smYI > optin)
+      if ((int)k2.smP5 > optin || (int)k2.smP1 > optin || (int)k2.smX > optin || (int)k2.smY > optin || (int)k2.smYI > optin)
         throw NsError{NS_ERR_INTERNAL, "specialised tile shapes exceed the shared memory of the device"};
       CUDA_TRY(cudaFuncSetAttribute(k2.pencil, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
       CUDA_TRY(cudaFuncSetAttribute(k2.pencil1, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
@@ -482,7 +482,9 @@ struct Solver : SolverBase {
       (a.nF == 1 && a.nOut == 1   ? k2.pencil1
        : a.nF == 2 && a.nOut == 2 ? k2.pencil2
                                   : k2.pencil)<<<(M / k2.TX) * N, k2.NTP,
-                                                  (a.nF > 1 || a.nOut > 1) ? k2.smP5 : k2.smP4, st>>>(a);
+                                                  (a.nF == 1 && a.nOut == 1) ? k2.smP1
+                                                  : (a.nF > 1 || a.nOut > 1) ? k2.smP5
+                                                                             : k2.smP4, st>>>(a);
     else
       k_pencil<T><<<(M / TX) * N, bdP, smP, st>>>(a);
     prof_end(e);

@@ -110,6 +110,12 @@ __host__ __device__ constexpr int radix_cap(int set, int f32_default, bool f32) 
   return set > 0 ? set : (f32 ? f32_default : NS_MAX_RADIX);
 }
 
+// NS_PENCIL_STAGE_STATE=1: the one-input pencil also stages the 3 state tiles with cp.async at
+// the start of a tile (6 tiles of shared memory, 2 blocks per SM instead of 3)
+#ifndef NS_PENCIL_STAGE_STATE
+#define NS_PENCIL_STAGE_STATE 0
+#endif
+
 template <typename T, int N>
 struct K2Cfg {
   static constexpr int M = N / 2;
@@ -345,11 +351,17 @@ __device__ __forceinline__ void pencil_spectral_one(const PencilArgs<T>& a, cpx<
   const bool act = threadIdx.x < NT;
   const int line = threadIdx.x % TX, kx = x0 + line;
   const int iz0 = threadIdx.x / TX;
+  const bool rd0 = a.mode != MODE_NL && a.mode != MODE_PROJECT;
+  const cpx<T>* base0 = a.mode == MODE_RK4_4 ? a.acc : a.state;
   if (!tz)
     for (int c = 0; c < 3; ++c) stage_col_tile<T, N, TX, NT>(buf + c * tile, a.F[0] + c * fstride, iy, x0);
+  cp_async_commit();
+  if (NS_PENCIL_STAGE_STATE && rd0)  // the state tiles arrive during the forward transforms
+    for (int c = 0; c < 3; ++c) stage_col_tile<T, N, TX, NT>(buf + (3 + c) * tile, base0 + c * fstride, iy, x0);
+  cp_async_commit();
   load_twiddles(tws, a.tw, N);
   if (!tz) {
-    cp_async_wait_all();
+    cp_async_wait_pending<1>();
     __syncthreads();
     const cpx<T>* dz = a.dsh[0] ? a.dsh[0] + 2 * N : nullptr;
     cpx<T> d0 = mk<T>(1, 0);
@@ -371,11 +383,13 @@ __device__ __forceinline__ void pencil_spectral_one(const PencilArgs<T>& a, cpx<
     e1xy = a.ifac[kx] * a.ifac[iy];
     ehxy = a.ifac[N + kx] * a.ifac[N + iy];
   }
+  if (NS_PENCIL_STAGE_STATE) {
+    cp_async_wait_pending<0>();
+    __syncthreads();
+  }
   if (act) {
     constexpr int CHK = PER < 4 ? PER : 4;  // modes whose state loads are in flight together
-    const bool rd0 = a.mode != MODE_NL && a.mode != MODE_PROJECT;
     const bool rd1 = a.mode == MODE_RK4_2 || a.mode == MODE_RK4_3;
-    const cpx<T>* base0 = a.mode == MODE_RK4_4 ? a.acc : a.state;
     const size_t gxy = (size_t)iy * M + kx;
     for (int i0 = 0; i0 < PER; i0 += CHK) {
       cpx<T> s0[3][CHK];  // (the RK4 accumulator, read by two modes only, is loaded on use)
@@ -387,7 +401,9 @@ __device__ __forceinline__ void pencil_spectral_one(const PencilArgs<T>& a, cpx<
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
           s0[c][j] = mk<T>(0, 0);
-          if (ok && rd0) s0[c][j] = MP::ldw(&base0[c * fstride + g]);
+          if (ok && rd0)
+            s0[c][j] = NS_PENCIL_STAGE_STATE ? buf[(3 + c) * tile + lf_idx<T, TX>(iz, line)]
+                                             : MP::ldw(&base0[c * fstride + g]);
         }
       }
 #pragma unroll
@@ -437,7 +453,7 @@ __device__ __forceinline__ void pencil_tile(const PencilArgs<T>& a, int tile_id,
   // component tile c is buf + c * tile (pointer arithmetic, not an array: no local memory)
   auto bc = [&](int c) { return buf + c * tile; };
   cpx<T>* b3 = buf + 3 * tile;
-  cpx<T>* tws = buf + pencil_tiles<T, N>(nF, nOut) * tile;
+  cpx<T>* tws = buf + (NFC == 1 && NS_PENCIL_STAGE_STATE ? 6 : pencil_tiles<T, N>(nF, nOut)) * tile;
   constexpr int ntx = M / TX;
   const int iy = tile_id / ntx;
   const int x0 = (tile_id % ntx) * TX;
@@ -601,7 +617,9 @@ __device__ __forceinline__ void pencil_tile(const PencilArgs<T>& a, int tile_id,
 // the two-input variant holds 4 shared tiles (3 blocks per SM at most): it is given the
 // registers of 2 resident blocks rather than spill
 template <typename T, int N, int NFC, int NOC>
-__global__ void __launch_bounds__(K2Cfg<T, N>::NTP, NFC == 2 ? cmin(2, K2Cfg<T, N>::MINB_P) : K2Cfg<T, N>::MINB_P)
+__global__ void __launch_bounds__(K2Cfg<T, N>::NTP, (NFC == 2 || (NFC == 1 && NS_PENCIL_STAGE_STATE))
+                                                         ? cmin(2, K2Cfg<T, N>::MINB_P)
+                                                         : K2Cfg<T, N>::MINB_P)
     k2_pencil(PencilArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   pencil_tile<T, N, MemNC, NFC, NOC>(a, blockIdx.x, reinterpret_cast<cpx<T>*>(smem_raw));
@@ -829,7 +847,7 @@ struct K2Entry {
   void (*yfwd)(SlabArgs<T>) = nullptr;
   void (*xrow)(SlabArgs<T>) = nullptr;
   int TX = 0, NTP = 0, TY = 0, NTY = 0, TYI = 0, NTYI = 0, RX = 0, NTX = 0;
-  size_t smP4 = 0, smP5 = 0, smY = 0, smYI = 0, smX = 0;
+  size_t smP1 = 0, smP4 = 0, smP5 = 0, smY = 0, smYI = 0, smX = 0;
 };
 
 template <typename T, int N>
@@ -851,6 +869,7 @@ K2Entry<T> make_k2_entry() {
   e.TYI = C::TYI; e.NTYI = C::NTYI;
   e.smYI = (6 * (size_t)lf_rows<T, C::TYI>(N) * C::TYI + N) * sizeof(cpx<T>);
   e.smP4 = (3 * (size_t)lf_rows<T, C::TX>(N) * C::TX + N) * sizeof(cpx<T>);  // 3 tiles + twiddles
+  e.smP1 = NS_PENCIL_STAGE_STATE ? (6 * (size_t)lf_rows<T, C::TX>(N) * C::TX + N) * sizeof(cpx<T>) : e.smP4;
   e.smP5 = (4 * (size_t)lf_rows<T, C::TX>(N) * C::TX + N) * sizeof(cpx<T>);  // 4 tiles + twiddles
   e.smY = ((size_t)lf_rows<T, C::TY>(N) * C::TY + N) * sizeof(cpx<T>);
   e.smX = (2 * (size_t)C::XBUF + N) * sizeof(cpx<T>);
