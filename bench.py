@@ -353,9 +353,10 @@ def main():
     hbm, peak_kind = peaks()
 
     # Roofline units.  The pencil pass is one launch (INIT + 2 per step; the last has no
-    # output): 14C per launch.  The slab pass is one HBM pass made of three kernels per plane
-    # group (y inverse, x rows, y forward) whose intermediates stay in L2 by design: it reads
-    # the 5 mixed fields (5C) and writes the 3 transformed products (3C), 8C per pass.
+    # output): 14C per launch.  The slab pass is three kernels per plane group (y inverse,
+    # x rows, y forward) whose algorithmic traffic is the 5 mixed fields read (5C) and the 3
+    # transformed products written (3C), 8C per pass; its scratch is an implementation choice
+    # (L2 or HBM by group size) and shows in the measured ncu traffic, not in the model.
     nchunks = (K + 255) // 256
     pencil_bytes = (8.0 + 28.0 * Kp - 5.0) * C  # INIT + 2 passes per step, the last without output
     units = {

@@ -303,7 +303,7 @@ struct Solver : SolverBase {
     while (RX > 1 && (6 * (size_t)RX * M * cs > 100 * 1024 || fft_block(RX, M) > 512)) RX /= 2;
     bdX = fft_block(RX, M) < 256 ? 256 : fft_block(RX, M);
     smX = 6 * (size_t)RX * M * cs;
-    // plane group sized to keep the scratch (6 fields) in L2
+    // initial plane group: a scratch (6 fields) of 48 MB, small enough for L2
     const size_t plane6 = 6 * (size_t)N * M * cs;
     G = (int)((48ull << 20) / plane6);
     if (G < 1) G = 1;

@@ -5,8 +5,9 @@
 //   mixed         [5][z][ky][kx]       after the inverse z transform: u_x, u_y, u_z,
 //                                      d_z u_x, d_z u_y (phase shift already applied)
 //   Ft            [3][z][ky][kx]       FFT_xy of u x omega (mixed space)
-//   scratch       [6][g][y][kx]        y-transformed planes of the current plane group;
-//                                      sized to stay resident in L2
+//   scratch       [6][g][y][kx]        y-transformed planes of the current plane group
+//                                      (L2-resident for small groups; the group size is
+//                                      autotuned and may be the whole grid)
 // One evaluation of the nonlinear term = slab pass over all planes (k_yinv -> k_xrow ->
 // k_yfwd per plane group) followed by one pencil pass (k_pencil) that ends the forward
 // transform and applies the whole spectral stage of Sec. 4 in the same HBM pass.
