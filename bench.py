@@ -53,7 +53,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--rk4-steps", type=int, default=30)
-    ap.add_argument("--e2e-steps", type=int, default=50)
+    ap.add_argument("--e2e-steps", type=int, default=None,
+                    help="steps of the end-to-end leg (default: --steps)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
     ap.add_argument("--no-rk4", action="store_true")
     ap.add_argument("--batch-steps", type=int, default=200,
@@ -468,7 +469,7 @@ def main():
         b.close()
 
     # end to end through the C ABI with host buffers: host velocity in, E/eps out every step
-    Ke = max(3, min(args.e2e_steps, K))
+    Ke = max(3, K if args.e2e_steps is None else min(args.e2e_steps, K))
     s.step(dt, 1)
     barrier(world)
     torch.cuda.synchronize()

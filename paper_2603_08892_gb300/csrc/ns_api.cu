@@ -127,6 +127,7 @@ struct SolverBase {
   virtual void energy(double* E, double* eps) = 0;
   virtual void spectrum(int kind, double* out, int nbins) = 0;
   virtual void step_cfl(double cfl, double dt_max, int nsteps) = 0;
+  virtual void invalidate_carry() = 0;  // the next step recomputes its first input
   virtual void raw_state(std::vector<unsigned char>& out) = 0;         // native-precision bytes
   virtual void set_raw_state(const unsigned char* in, size_t n) = 0;
   virtual void forcing_params(int* kind, double* v, uint64_t* seed) = 0;  // v: kmin, kmax, eps, tcorr
@@ -194,6 +195,11 @@ struct Solver : SolverBase {
     }
     CUDA_TRY(cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming));
   }
+  // Step whose first evaluation's input the mixed fields (and the forcing record) already
+  // hold: the last pencil pass of every ns_step call prepares the next step, so the next call
+  // skips its INIT pass.  -1 whenever anything else wrote the state, the mixed fields or the
+  // forcing record.
+  int64_t carry_step = -1;
   // adaptive time step (ns_step_cfl): dt = min(dt_max, cfl dx / sum_i max|u_i|) per step
   double cfl = 0.0, cfl_dtmax = 0.0;
   unsigned long long* d_umax = nullptr;
@@ -383,6 +389,7 @@ struct Solver : SolverBase {
   void* state_ptr() override { return state; }
 
   void buffers(double dt, NsCtxBuffers* b) override {
+    carry_step = -1;  // the mixed fields / state / forcing record change here
     if (dt > 0) set_dt(dt);
     b->N = N; b->precision = c->p.precision; b->scheme = c->p.scheme; b->truncation = c->p.truncation;
     b->K2max = c->K2max; b->Kimax = c->Kimax; b->G = Gmax; b->nu = c->p.nu; b->kmax = c->p.kmax;
@@ -608,6 +615,7 @@ struct Solver : SolverBase {
 
   void set_forcing(int kind, double kfmin, double kfmax, double eps, double tcorr,
                    uint64_t seed) override {
+    carry_step = -1;  // the mixed fields / state / forcing record change here
     fkind = kind;
     if (kind == NS_FORCE_NONE) return;
     fkmin = kfmin; fkmax = kfmax; feps = eps; ftcorr = tcorr; fseed = seed;
@@ -699,6 +707,7 @@ struct Solver : SolverBase {
 
   // The cached value encodes the group size and the stream count: 2 G + (streams - 1).
   void autotune() {
+    carry_step = -1;  // the mixed fields / state / forcing record change here
     tuned = true;
     if (const char* fs = std::getenv("NS_SLAB_STREAMS")) slab_streams = std::atoi(fs) == 2 ? 2 : 1;
     if (const char* fg = std::getenv("NS_SLAB_PLANES")) {  // forced group size
@@ -756,6 +765,8 @@ struct Solver : SolverBase {
   }
 
   // ---- schemes ------------------------------------------------------------------------
+  void invalidate_carry() override { carry_step = -1; }
+
   void step_cfl(double cfl_, double dt_max, int nsteps) override {
     cfl = cfl_;
     cfl_dtmax = dt_max;
@@ -779,14 +790,15 @@ struct Solver : SolverBase {
       const bool last_chunk = s0 + ns == nsteps;
       if (fkind != NS_FORCE_NONE) prepare_forcing(c->t, c->t + ns * dt);
       if (sch == NS_RK2_PS_RANDOM || sch == NS_RK2_PS_APPROX) {
-        // shift vectors: [2n] alpha_n, [2n+1] beta_n
-        std::vector<double> sh(6 * (size_t)ns);
-        for (int n = 0; n < ns; ++n) {
+        // shift vectors: [2n] alpha_n, [2n+1] beta_n, and alpha of the step after the chunk
+        // (read without consuming an override shift) for the carried mixed fields
+        std::vector<double> sh(6 * (size_t)ns + 3);
+        for (int n = 0; n <= ns; ++n) {
           double da[3] = {0, 0, 0};
           if (sch == NS_RK2_PS_RANDOM) {
             if (c->override_pos < c->override_shifts.size()) {
               for (int i = 0; i < 3; ++i) da[i] = c->override_shifts[c->override_pos + i];
-              c->override_pos += 3;
+              if (n < ns) c->override_pos += 3;
             } else {
               for (int i = 0; i < 3; ++i)
                 da[i] = dx * uniform01(c->p.seed, (uint64_t)(3 * (c->step + n) + i));
@@ -794,7 +806,7 @@ struct Solver : SolverBase {
           }
           for (int i = 0; i < 3; ++i) {
             sh[6 * n + i] = da[i];
-            sh[6 * n + 3 + i] = da[i] + 0.5 * dx;
+            if (n < ns) sh[6 * n + 3 + i] = da[i] + 0.5 * dx;
           }
         }
         upload_shifts(sh);
@@ -846,7 +858,7 @@ struct Solver : SolverBase {
     const T w = (T)(1.0 / ((double)N * N * N));
     auto alpha = [&](int n) -> const cpx<T>* { return approx ? nullptr : shift_tab(2 * n); };
     auto beta = [&](int n) -> const cpx<T>* { return shift_tab(2 * n + 1); };
-    init_pass(1, alpha(0), nullptr);
+    if (carry_step != c->step) init_pass(1, alpha(0), nullptr);
     for (int n = 0; n < ns; ++n) {
       const double t = c->t;
       slab(mixed[0], Ft[0], cfl > 0.0);
@@ -860,20 +872,20 @@ struct Solver : SolverBase {
       PencilArgs<T> b = pencil_args(MODE_ROG_2);
       force_coef(t + dt, b);
       b.nF = 1; b.F[0] = Ft[0]; b.dsh[0] = beta(n); b.wF[0] = w;
-      b.nOut = (n + 1 < ns) ? 1 : 0;
-      b.osh[0] = (n + 1 < ns) ? alpha(n + 1) : nullptr;
+      b.nOut = 1;  // the last step of the chunk prepares the step after it
+      b.osh[0] = alpha(n + 1);
       b.out[0] = mixed[0];
-      if (fkind != NS_FORCE_NONE && b.nOut == 0) b.nOut = 0;
       pencil(b);
       c->t = t + dt;
       c->step += 1;
     }
+    carry_step = c->step;
   }
 
   void run_rk2(double dt0, int ns, bool exact) {
     const T w = (T)(1.0 / ((double)N * N * N));
     const cpx<T>* iso = exact ? shift_tab(0) : nullptr;
-    init_pass(exact ? 2 : 1, nullptr, iso);
+    if (carry_step != c->step) init_pass(exact ? 2 : 1, nullptr, iso);
     for (int n = 0; n < ns; ++n) {
       const double t = c->t;
       double dt = dt0;
@@ -886,8 +898,7 @@ struct Solver : SolverBase {
         a.nF = exact ? 2 : 1;
         a.F[0] = Ft[0]; a.dsh[0] = nullptr; a.wF[0] = exact ? (T)0.5 * w : w;
         a.F[1] = Ft[1]; a.dsh[1] = iso; a.wF[1] = (T)0.5 * w;
-        const bool out = stg == 0 || n + 1 < ns;
-        a.nOut = out ? (exact ? 2 : 1) : 0;
+        a.nOut = exact ? 2 : 1;  // the last pass prepares the next step
         a.osh[0] = nullptr; a.out[0] = mixed[0];
         a.osh[1] = iso; a.out[1] = mixed[1];
         pencil(a);
@@ -895,11 +906,12 @@ struct Solver : SolverBase {
       c->t = t + dt;
       c->step += 1;
     }
+    carry_step = c->step;
   }
 
   void run_rk4(double dt0, int ns) {
     const T w = (T)(1.0 / ((double)N * N * N));
-    init_pass(1, nullptr, nullptr);
+    if (carry_step != c->step) init_pass(1, nullptr, nullptr);
     const int modes[4] = {MODE_RK4_1, MODE_RK4_2, MODE_RK4_3, MODE_RK4_4};
     const double ts[4] = {0.0, 0.5, 0.5, 1.0};
     for (int n = 0; n < ns; ++n) {
@@ -911,17 +923,19 @@ struct Solver : SolverBase {
         PencilArgs<T> a = pencil_args(modes[stg]);
         force_coef(t + ts[stg] * dt, a);
         a.nF = 1; a.F[0] = Ft[0]; a.wF[0] = w;
-        a.nOut = (stg < 3 || n + 1 < ns) ? 1 : 0;
+        a.nOut = 1;  // the last pass prepares the next step
         a.out[0] = mixed[0];
         pencil(a);
       }
       c->t = t + dt;
       c->step += 1;
     }
+    carry_step = c->step;
   }
 
   // ---- transfers ----------------------------------------------------------------------
   void set_velocity(const double* u) override {
+    carry_step = -1;  // the mixed fields / state / forcing record change here
     const size_t n = 3 * (size_t)N * N * N;
     std::vector<T> h(n);
     for (size_t i = 0; i < n; ++i) h[i] = (T)u[i];
@@ -949,6 +963,7 @@ struct Solver : SolverBase {
 
   // spectral [3][N][N][M] -> physical host [3][N][N][N] (inverse z, y, x transforms)
   void to_physical(const cpx<T>* src, double* u) {
+    carry_step = -1;  // the mixed fields / state / forcing record change here
     PencilArgs<T> p = pencil_args(MODE_INIT);
     p.shell = nullptr;
     p.src = src;
@@ -999,6 +1014,7 @@ struct Solver : SolverBase {
     sync_check();
   }
   void set_raw_state(const unsigned char* in, size_t n) override {
+    carry_step = -1;  // the mixed fields / state / forcing record change here
     if (n != 3 * F1 * sizeof(cpx<T>)) throw NsError{NS_ERR_IO, "checkpoint state size mismatch"};
     CUDA_TRY(cudaMemcpyAsync(state, in, n, cudaMemcpyHostToDevice, st));
     CUDA_TRY(cudaStreamSynchronize(st));
@@ -1008,9 +1024,13 @@ struct Solver : SolverBase {
     v[0] = fkmin; v[1] = fkmax; v[2] = feps; v[3] = ftcorr;
     *seed = fseed;
   }
-  void set_state(const double* s) override { upload(s, state); }
+  void set_state(const double* s) override {
+    carry_step = -1;  // the mixed fields / state / forcing record change here
+    upload(s, state);
+  }
 
   void nonlinear(const double* in, const double* delta, double* out) override {
+    carry_step = -1;  // the mixed fields / state / forcing record change here
     const cpx<T>* src = state;
     if (in) {
       upload(in, acc);
@@ -1137,6 +1157,7 @@ struct Solver : SolverBase {
 
   void vjp(const double* u0, int nsteps, double dt, int ckpt, int loss, double* Lout,
            double* grad) override {
+    carry_step = -1;  // the mixed fields / state / forcing record change here
     const size_t vb = 3 * F1 * sizeof(cpx<T>);
     const int nseg_states = ckpt;
     const int nck = (nsteps + ckpt - 1) / ckpt + 1;
@@ -1280,6 +1301,7 @@ struct Solver : SolverBase {
   // Nonlinear energy flux and cumulative dissipation on shell bins (Sec. 3.4)
   cpx<T>* nlbuf = nullptr;
   void energy_flux(const double* delta, int nshift, double* flux, double* cumd, int nbins) override {
+    carry_step = -1;  // the mixed fields / state / forcing record change here
     if (flux) {
       if (!nlbuf) CUDA_TRY(cudaMalloc(&nlbuf, 3 * F1 * sizeof(cpx<T>)));
       if (nshift == 0) {
@@ -1347,6 +1369,7 @@ int ns_ctx_buffers(ns_ctx* c, double dt, NsCtxBuffers* b) {
 
 int ns_ctx_advance(ns_ctx* c, double dt, int nsteps) {
   if (!c) return NS_ERR_INVALID_ARG;
+  c->solver->invalidate_carry();  // the batch kernel wrote this member's buffers
   for (int i = 0; i < nsteps; ++i) c->t += dt;  // same accumulation as ns_step
   c->step += nsteps;
   return NS_OK;
@@ -1526,6 +1549,7 @@ int ns_set_shifts(ns_ctx* c, const double* da, int nsteps) {
     if (nsteps < 0 || (nsteps > 0 && !da)) return fail(c, NS_ERR_INVALID_ARG, "bad shifts");
     c->override_shifts.assign(da, da + 3 * (size_t)nsteps);
     c->override_pos = 0;
+    c->solver->invalidate_carry();
     return (int)NS_OK;
   });
 }

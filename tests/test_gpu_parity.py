@@ -327,3 +327,28 @@ def test_fma_peak_measures_the_device(ns):
     # 152 SMs x 128 FP32 lanes x 2 flop x ~2 GHz is ~80 TFLOP/s; FP64 is a small fraction
     assert 20e12 < f32 < 200e12
     assert 0 < f64 < f32
+
+
+@pytest.mark.parametrize("prec", [1, 0])
+@pytest.mark.parametrize("name", list(SCHEMES))
+def test_step_calls_split_anywhere_bitwise(ns, name, prec):
+    # each call's last pencil pass prepares the next step (the next call skips its INIT pass);
+    # splitting a run into calls, with diagnostics and a velocity read in between, changes no bit
+    code, _ = SCHEMES[name]
+    N, nu, dt = 24, 0.01, 0.01
+    u = field(N, seed=41)
+    runs = []
+    for split in ([6], [1, 1, 1, 1, 1, 1], [2, 3, 1]):
+        with ns.Solver(N, nu, N / 2, scheme=code, precision=prec, seed=9) as s:
+            if name == "random":
+                s.set_forcing(2.0, 3.0, 0.2, 0.5, seed=3)
+            s.set_velocity(u)
+            for i, k in enumerate(split):
+                s.step(dt, k)
+                s.energy()
+                if i == 1:
+                    s.get_velocity()
+                    s.energy_flux(12)
+            runs.append((s.get_state(), s.time()))
+    for st, t in runs[1:]:
+        assert np.array_equal(st, runs[0][0]) and t == runs[0][1]
