@@ -107,7 +107,11 @@ int ns_set_forcing(ns_ctx* ctx, int kind, double kf_min, double kf_max, double e
 
 /* Advances nsteps time steps of size dt with the context's scheme (Sec. 4.1-4.2, 6.1).
  * The random scheme draws delta_alpha of step s from splitmix64(seed, 3s+i) unless
- * ns_set_shifts supplied them.  Synchronises the context's stream before returning. */
+ * ns_set_shifts supplied them.  Stream-ordered: returns once the steps are queued on the
+ * context's stream (argument and launch errors are returned here; a failed device-side
+ * consistency check is returned by the next call that synchronises, e.g. ns_energy or
+ * ns_get_state).  The last pencil pass prepares the next step, so consecutive calls cost
+ * the same as one call over all their steps. */
 int ns_step(ns_ctx* ctx, double dt, int nsteps);
 /* Same, each step with an adaptive time step (Sec. 2: CFL condition, coefficient 0.4 for the
  * RK2 schemes and 1.0 for RK4 in the paper): dt = min(dt_max, cfl / sum_i (max_x |u_i| / dx)),

@@ -369,6 +369,7 @@ struct Solver : SolverBase {
   ~Solver() override {
     cudaFree(state); cudaFree(acc); cudaFree(mixed[0]); cudaFree(mixed[1]);
     cudaFree(nlbuf); cudaFree(nltmp); cudaFree(d_umax);
+    if (h_err) cudaFreeHost(h_err);
     cudaFree(Ft[0]); cudaFree(Ft[1]); cudaFree(scr); cudaFree(tw); cudaFree(ifac);
     cudaFree(shtab); cudaFree(d_shifts); cudaFree(red); cudaFree(d_err);
     cudaFree(fpat); cudaFree(force); cudaFree(shell);
@@ -398,12 +399,15 @@ struct Solver : SolverBase {
   }
 
   // ---- device error flag ------------------------------------------------------------
+  int* h_err = nullptr;  // pinned copy of the device flag: one stream sync per check
   void sync_check() {
+    if (!h_err) CUDA_TRY(cudaMallocHost(&h_err, sizeof(int)));
+    CUDA_TRY(cudaMemcpyAsync(h_err, d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
     CUDA_TRY(cudaStreamSynchronize(st));
-    int h = 0;
-    CUDA_TRY(cudaMemcpy(&h, d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    const int h = *h_err;
     if (h) {
-      CUDA_TRY(cudaMemset(d_err, 0, sizeof(int)));
+      CUDA_TRY(cudaMemsetAsync(d_err, 0, sizeof(int), st));
+      CUDA_TRY(cudaStreamSynchronize(st));
       throw NsError{NS_ERR_INTERNAL, "device-side launch-shape check failed (flag " + std::to_string(h) + ")"};
     }
   }
@@ -822,7 +826,7 @@ struct Solver : SolverBase {
       }
       (void)last_chunk;
     }
-    sync_check();
+    // stream-ordered: device-side checks are reported by the next synchronising call
   }
 
   void init_pass(int nOut, const cpx<T>* o0, const cpx<T>* o1) {
