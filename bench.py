@@ -353,16 +353,16 @@ def main():
     ms_step = ms_max / K
     hbm, peak_kind = peaks()
 
-    # Roofline units.  The pencil pass is one launch (INIT + 2 per step; the last has no
-    # output): 14C per launch.  The slab pass is three kernels per plane group (y inverse,
-    # x rows, y forward) whose algorithmic traffic is the 5 mixed fields read (5C) and the 3
-    # transformed products written (3C), 8C per pass; its scratch is an implementation choice
-    # (L2 or HBM by group size) and shows in the measured ncu traffic, not in the model.
+    # Roofline units.  The pencil pass is one launch (2 per step).  The slab pass is three
+    # kernels per plane group (y inverse, x rows, y forward) whose algorithmic traffic is the
+    # 5 mixed fields read (5C) and the 3 transformed products written (3C), 8C per pass; its
+    # scratch is an implementation choice (L2 or HBM by group size) and shows in the measured
+    # ncu traffic, not in the model.
     nchunks = (K + 255) // 256
-    pencil_bytes = (8.0 + 28.0 * Kp - 5.0) * C  # INIT + 2 passes per step, the last without output
+    # every pencil pass of a step reads Ft and the state and writes the state and the mixed
+    # fields of the next evaluation (the last one prepares the next step): 14C per launch
     units = {
-        "k_pencil": (pencil_bytes / max(1, prof["k_pencil"][2]), prof["k_pencil"][0],
-                     prof["k_pencil"][1]),
+        "k_pencil": (14.0 * C, prof["k_pencil"][0], prof["k_pencil"][1]),
         "slab_pass": (8.0 * C, prof["slab_pass"][0], prof["slab_pass"][1]),
     }
     roof_units = {}
@@ -376,8 +376,10 @@ def main():
     tot = {k: prof[k][0] for k in kern}
     shares = {k: round(tot[k] / max(1e-9, sum(tot.values())), 4) for k in tot}
     kernel_ms = {k: round(tot[k] / Kp, 4) for k in tot}  # event time per step, each kind
-    # launches in the timed region: per step from the instrumented run, plus one INIT per chunk
-    per_step = (sum(prof[k][2] for k in kern) - 1) / Kp
+    # launches in the timed region: the kernels per step from the instrumented run (the mixed
+    # fields carried from the previous call spare the INIT pass), plus the shift-table kernel
+    # of every chunk of 256 steps
+    per_step = sum(prof[k][2] for k in kern) / Kp
     launches = int(round(per_step * K)) + nchunks
     ru = roof_units[dom]
     roof = {"bound": "hbm",
