@@ -92,12 +92,18 @@ __host__ __device__ __forceinline__ int lf_row(int e) { return lf_padded<T, W>()
 template <typename T, int W>
 __host__ __device__ __forceinline__ int lf_idx(int e, int line) { return lf_row<T, W>(e) * W + line; }
 
+#ifndef NS_NLF_STRIDE_OLD
+#define NS_NLF_STRIDE_OLD 0
+#endif
 // Shared work tile of NL lines of length n.  LF (line-fast) layout [e][line] as above;
 // otherwise [line][e] with one pad element per 16 to spread the stride-R writes of a stage.
 template <typename T, int n, int NL, bool LF>
 struct WorkTile {
   cpx<T>* p;
-  static constexpr int LS = n + n / 16 + 1;
+  // line stride: one pad element per 16 spreads the stride-R writes within a line; choosing
+  // LS = n/16 (mod 16) makes the lines a warp covers in a radix-16 first stage (32 / (n/16)
+  // lines of n/16 consecutive elements) tile the 32 banks evenly
+  static constexpr int LS = NS_NLF_STRIDE_OLD ? n + n / 16 + 1 : n + n / 16 + (16 - n % 16) % 16;
   static __host__ __device__ constexpr int elems() { return LF ? lf_rows<T, NL>(n) * NL : NL * LS; }
   __device__ __forceinline__ int idx(int line, int e) const {
     return LF ? lf_idx<T, NL>(e, line) : line * LS + e + (e >> 4);
