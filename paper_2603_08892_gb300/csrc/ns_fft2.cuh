@@ -118,10 +118,17 @@ struct WorkTile {
 #ifndef NS_TW_PRODUCTS
 #define NS_TW_PRODUCTS 1
 #endif
+// Shared-memory twiddle tables hold entry i at tw_pad(i): one pad per 16 entries, so the
+// strided reads r * base of a stage's butterflies fall in distinct banks.
+#ifndef NS_TW_PAD
+#define NS_TW_PAD 1
+#endif
+__host__ __device__ constexpr int tw_pad(int i) { return NS_TW_PAD ? i + (i >> 4) : i; }
+__host__ __device__ constexpr int tw_elems(int n) { return NS_TW_PAD ? n + n / 16 + 1 : n; }
 template <typename T, int R>
 __device__ __forceinline__ void stage_twiddles(cpx<T>* w, const cpx<T>* __restrict__ tw, int base, T cs) {
   auto ld = [&](int r) {
-    cpx<T> v = tw[r * base];
+    cpx<T> v = tw[tw_pad(r * base)];
     v.y *= cs;
     return v;
   };
@@ -320,7 +327,7 @@ __device__ __forceinline__ void cfft_ip_to(const Src& src, cpx<T>* tile, const D
 // copy of the twiddle table into shared memory (all threads of the block participate)
 template <typename T>
 __device__ __forceinline__ void load_twiddles(cpx<T>* dst, const cpx<T>* __restrict__ tw, int n) {
-  for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = ldg(&tw[i]);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) dst[tw_pad(i)] = ldg(&tw[i]);
   __syncthreads();
 }
 

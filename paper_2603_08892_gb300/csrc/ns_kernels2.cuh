@@ -689,7 +689,7 @@ __device__ __forceinline__ void yinv_tile(const SlabArgs<T>& a, int tx, int zg, 
   cp_async_commit();
   for (int f = 3; f < 5; ++f) stage_col_tile<T, N, TY, NT, true>(in + f * tile, a.mixed + f * fs, z, x0);
   cp_async_commit();
-  for (int i = threadIdx.x; i < N; i += blockDim.x) tws[i] = ldg(&a.tw[i]);
+  for (int i = threadIdx.x; i < N; i += blockDim.x) tws[tw_pad(i)] = ldg(&a.tw[i]);
   cp_async_wait_pending<1>();
   __syncthreads();
   yinv_field<T, N, 0, MP>(a, in, W, zg, x0, sstride, tws);
@@ -739,7 +739,7 @@ __device__ __forceinline__ void xrow_tile(const SlabArgs<T>& a, int tile_id, cpx
   const RowT U{buf}, V{buf + C::XBUF};
   cpx<T>* tws = buf + 2 * C::XBUF;
   const bool act = threadIdx.x < NT;
-  for (int i = threadIdx.x; i < N; i += blockDim.x) tws[i] = ldg(&a.tw[i]);
+  for (int i = threadIdx.x; i < N; i += blockDim.x) tws[tw_pad(i)] = ldg(&a.tw[i]);
   __syncthreads();  // the pre-processing below reads twiddles written by other threads
   const int rows_total = a.G * N;
   const int r0 = tile_id * RX;
@@ -778,7 +778,7 @@ __device__ __forceinline__ void xrow_tile(const SlabArgs<T>& a, int tile_id, cpx
         B.put(line, H, (xb[c] + conjg(xb[c])) - (xb[c] - conjg(xb[c])));
       } else {
         const cpx<T> Xk = xa[c], Xm = xb[c];
-        const cpx<T> tk = tws[k];
+        const cpx<T> tk = tws[tw_pad(k)];
         const cpx<T> A = Xk + conjg(Xm), Bv = Xk - conjg(Xm);
         B.put(line, k, A + mul_si(conjg(tk) * Bv, T(1)));
         const cpx<T> A2 = Xm + conjg(Xk), B2 = Xm - conjg(Xk);
@@ -830,7 +830,7 @@ __device__ __forceinline__ void xrow_tile(const SlabArgs<T>& a, int tile_id, cpx
       MP::st(&dst[H], T(0.5) * ((Zk + conjg(Zk)) - (Zk - conjg(Zk))));
     } else {
       const cpx<T> Zk = U.get(line, k), Zm = U.get(line, M - k);
-      const cpx<T> Wk = tws[k];
+      const cpx<T> Wk = tws[tw_pad(k)];
       const cpx<T> A = Zk + conjg(Zm), B = Zk - conjg(Zm);
       MP::st(&dst[k], T(0.5) * (A - mul_si(Wk * B, T(1))));
       const cpx<T> A2 = Zm + conjg(Zk), B2 = Zm - conjg(Zk);
@@ -876,12 +876,12 @@ K2Entry<T> make_k2_entry() {
   e.xrow = k2_xrow<T, N>;
   e.TX = C::TX; e.NTP = C::NTP; e.TY = C::TY; e.NTY = C::NTY; e.RX = C::RX; e.NTX = C::NTX;
   e.TYI = C::TYI; e.NTYI = C::NTYI;
-  e.smYI = (6 * (size_t)lf_rows<T, C::TYI>(N) * C::TYI + N) * sizeof(cpx<T>);
-  e.smP4 = (3 * (size_t)lf_rows<T, C::TX>(N) * C::TX + N) * sizeof(cpx<T>);  // 3 tiles + twiddles
-  e.smP1 = NS_PENCIL_STAGE_STATE ? (6 * (size_t)lf_rows<T, C::TX>(N) * C::TX + N) * sizeof(cpx<T>) : e.smP4;
-  e.smP5 = (4 * (size_t)lf_rows<T, C::TX>(N) * C::TX + N) * sizeof(cpx<T>);  // 4 tiles + twiddles
-  e.smY = ((size_t)lf_rows<T, C::TY>(N) * C::TY + N) * sizeof(cpx<T>);
-  e.smX = (2 * (size_t)C::XBUF + N) * sizeof(cpx<T>);
+  e.smYI = (6 * (size_t)lf_rows<T, C::TYI>(N) * C::TYI + tw_elems(N)) * sizeof(cpx<T>);
+  e.smP4 = (3 * (size_t)lf_rows<T, C::TX>(N) * C::TX + tw_elems(N)) * sizeof(cpx<T>);  // 3 tiles + twiddles
+  e.smP1 = NS_PENCIL_STAGE_STATE ? (6 * (size_t)lf_rows<T, C::TX>(N) * C::TX + tw_elems(N)) * sizeof(cpx<T>) : e.smP4;
+  e.smP5 = (4 * (size_t)lf_rows<T, C::TX>(N) * C::TX + tw_elems(N)) * sizeof(cpx<T>);  // 4 tiles + twiddles
+  e.smY = ((size_t)lf_rows<T, C::TY>(N) * C::TY + tw_elems(N)) * sizeof(cpx<T>);
+  e.smX = (2 * (size_t)C::XBUF + tw_elems(N)) * sizeof(cpx<T>);
   return e;
 }
 
