@@ -116,7 +116,11 @@ __host__ __device__ constexpr int radix_cap(int set, int f32_default, bool f32) 
 #ifndef NS_PENCIL_UNROLL
 #define NS_PENCIL_UNROLL 1
 #endif
-constexpr int kPencilUnroll = NS_PENCIL_UNROLL;  // (pragma arguments are not macro-expanded)
+constexpr int kPencilUnroll = NS_PENCIL_UNROLL;
+// modes per thread whose state loads the fused spectral pass keeps in flight together
+#ifndef NS_PENCIL_CHK
+#define NS_PENCIL_CHK 4
+#endif  // (pragma arguments are not macro-expanded)
 // NS_PENCIL_STAGE_STATE=1: the one-input pencil also stages the 3 state tiles with cp.async at
 // the start of a tile (6 tiles of shared memory, 2 blocks per SM instead of 3)
 #ifndef NS_PENCIL_STAGE_STATE
@@ -396,7 +400,7 @@ __device__ __forceinline__ void pencil_spectral_one(const PencilArgs<T>& a, cpx<
     __syncthreads();
   }
   if (act) {
-    constexpr int CHK = PER < 4 ? PER : 4;  // modes whose state loads are in flight together
+    constexpr int CHK = PER < NS_PENCIL_CHK ? PER : NS_PENCIL_CHK;  // modes whose state loads are in flight together
     const bool rd1 = a.mode == MODE_RK4_2 || a.mode == MODE_RK4_3;
     const size_t gxy = (size_t)iy * M + kx;
     for (int i0 = 0; i0 < PER; i0 += CHK) {
