@@ -476,15 +476,18 @@ def main():
     barrier(world)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    s.set_velocity(u0)
+    s.set_velocity(u0)  # synchronises
+    t1 = time.perf_counter()
     for _ in range(Ke):
         s.step(dt, 1)
         s.energy()
     torch.cuda.synchronize()
-    el = reduce_max(time.perf_counter() - t0, world)
+    t2 = time.perf_counter()
+    el = reduce_max(t2 - t0, world)
     h2d = (3 * N_PS ** 3 * 4 + Ke * 48) / Ke
     line["e2e"] = {"value": world * Ke / el, "unit": "steps/s", "h2d_bytes_per_step": h2d,
-                   "d2h_bytes_per_step": 16,
+                   "d2h_bytes_per_step": 16, "set_velocity_ms": (t1 - t0) * 1000.0,
+                   "step_and_energy_ms": (t2 - t1) * 1000.0 / Ke,
                    "what": "ns_set_velocity(host 3x256^3 f64) once + per step ns_step(dt,1) and "
                            "ns_energy (E, eps to host); %d steps" % Ke}
     s.close()

@@ -624,20 +624,50 @@ __global__ void __launch_bounds__(256) k_energy(const cpx<T>* __restrict__ S, in
   const int M = N / 2;
   const size_t nmode = (size_t)N * N * M;
   double e = 0, d = 0;
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < nmode;
-       i += (size_t)gridDim.x * blockDim.x) {
-    const int kx = (int)(i % M);
-    const size_t r = i / M;
-    const int iy = (int)(r % N), iz = (int)(r / N);
-    const int ky = kof(iy, N), kz = kof(iz, N);
-    const double w = kx == 0 ? 1.0 : 2.0;
-    double a2 = 0;
-    for (int c = 0; c < 3; ++c) {
-      cpx<T> v = S[i + c * nmode];
-      a2 += (double)v.x * (double)v.x + (double)v.y * (double)v.y;
+  if constexpr (sizeof(T) == 4) {
+    // FP32 state: the terms in FP32 and each thread's share (about a hundred modes) summed
+    // with compensated (Kahan) FP32 additions, then the partial sums reduced in FP64 (FP64
+    // arithmetic per mode is ALU-bound on this GPU)
+    float es = 0.f, ec = 0.f, ds = 0.f, dc = 0.f;
+    auto kahan = [](float& sum, float& comp, float x) {
+      const float y = x - comp;
+      const float t = sum + y;
+      comp = (t - sum) - y;
+      sum = t;
+    };
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < nmode;
+         i += (size_t)gridDim.x * blockDim.x) {
+      const int kx = (int)(i % M);
+      const size_t r = i / M;
+      const int iy = (int)(r % N), iz = (int)(r / N);
+      const int ky = kof(iy, N), kz = kof(iz, N);
+      float a2 = 0.f;
+      for (int c = 0; c < 3; ++c) {
+        const cpx<T> v = S[i + c * nmode];
+        a2 = fmaf((float)v.x, (float)v.x, fmaf((float)v.y, (float)v.y, a2));
+      }
+      const float te = (kx == 0 ? 1.f : 2.f) * a2;
+      kahan(es, ec, te);
+      kahan(ds, dc, te * (float)(kx * kx + ky * ky + kz * kz));
     }
-    e += w * a2;
-    d += w * (double)(kx * kx + ky * ky + kz * kz) * a2;
+    e = (double)es - (double)ec;
+    d = (double)ds - (double)dc;
+  } else {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < nmode;
+         i += (size_t)gridDim.x * blockDim.x) {
+      const int kx = (int)(i % M);
+      const size_t r = i / M;
+      const int iy = (int)(r % N), iz = (int)(r / N);
+      const int ky = kof(iy, N), kz = kof(iz, N);
+      const double w = kx == 0 ? 1.0 : 2.0;
+      double a2 = 0;
+      for (int c = 0; c < 3; ++c) {
+        cpx<T> v = S[i + c * nmode];
+        a2 += (double)v.x * (double)v.x + (double)v.y * (double)v.y;
+      }
+      e += w * a2;
+      d += w * (double)(kx * kx + ky * ky + kz * kz) * a2;
+    }
   }
   se[threadIdx.x] = e;
   sd[threadIdx.x] = d;
