@@ -194,7 +194,7 @@ int ns_device_state(ns_ctx* ctx, void** state, void** stream, int* precision);
  * stream and returns, for one kind, the summed event time in ms, the number of timed
  * launches and the number of launches since the reset.  Kinds: */
 enum { NS_PROF_PENCIL = 0, NS_PROF_YINV = 1, NS_PROF_XROW = 2, NS_PROF_YFWD = 3,
-       NS_PROF_SLAB_PASS = 4, NS_PROF_KINDS = 5 };
+       NS_PROF_SLAB_PASS = 4, NS_PROF_SLAB_PIPE = 5, NS_PROF_KINDS = 6 };
 int ns_profile(ns_ctx* ctx, int enable);
 int ns_profile_read(ns_ctx* ctx, int kind, double* total_ms, int64_t* timed, int64_t* launches);
 

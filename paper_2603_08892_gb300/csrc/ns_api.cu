@@ -185,6 +185,12 @@ struct Solver : SolverBase {
   // slab pass on two internal streams (plane groups alternate, double-buffered scratch) so
   // the kernels of one group overlap those of the next; chosen by the autotuner
   int slab_streams = 1;
+  // slab pass as one persistent pipeline launch (k2_slabpipe) with a ring of pipe_ring
+  // scratch planes; chosen by the autotuner where the size has the kernel
+  bool pipe = false;
+  int pipe_ring = 0, pipe_lag = 0, pipe_grid = 0, pipe_stall = 0;
+  long long pipe_spin = 1ll << 26;
+  unsigned char* d_pipe = nullptr;  // [3][N] done counters, ticket, abort flag
   cudaStream_t ss[2] = {nullptr, nullptr};
   cudaEvent_t ev_fork = nullptr, ev_join[2] = {nullptr, nullptr};
   void ensure_streams() {
@@ -340,6 +346,8 @@ struct Solver : SolverBase {
       CUDA_TRY(cudaFuncSetAttribute(k2.yinv, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
       CUDA_TRY(cudaFuncSetAttribute(k2.yfwd, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
       CUDA_TRY(cudaFuncSetAttribute(k2.xrow, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+      if (k2.slabpipe)  // (it has a few bytes of static shared memory: its own size, not optin)
+        CUDA_TRY(cudaFuncSetAttribute(k2.slabpipe, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k2.smPIPE));
     }
 
     const int sch = c->p.scheme;
@@ -368,7 +376,7 @@ struct Solver : SolverBase {
 
   ~Solver() override {
     cudaFree(state); cudaFree(acc); cudaFree(mixed[0]); cudaFree(mixed[1]);
-    cudaFree(nlbuf); cudaFree(nltmp); cudaFree(d_umax);
+    cudaFree(nlbuf); cudaFree(nltmp); cudaFree(d_umax); cudaFree(d_pipe);
     if (h_err) cudaFreeHost(h_err);
     cudaFree(Ft[0]); cudaFree(Ft[1]); cudaFree(scr); cudaFree(tw); cudaFree(ifac);
     cudaFree(shtab); cudaFree(d_shifts); cudaFree(red); cudaFree(d_err);
@@ -408,6 +416,8 @@ struct Solver : SolverBase {
     if (h) {
       CUDA_TRY(cudaMemsetAsync(d_err, 0, sizeof(int), st));
       CUDA_TRY(cudaStreamSynchronize(st));
+      if (h & PIPE_ERR_TIMEOUT)
+        throw NsError{NS_ERR_TIMEOUT, "slab pipeline: a bounded wait gave up (the pass was abandoned)"};
       throw NsError{NS_ERR_INTERNAL, "device-side launch-shape check failed (flag " + std::to_string(h) + ")"};
     }
   }
@@ -432,6 +442,33 @@ struct Solver : SolverBase {
       a.umax = d_umax;
     }
     cudaEvent_t pass = prof_begin(NS_PROF_SLAB_PASS);
+    if (pipe && use2 && k2.slabpipe && pipe_ring >= 2 && pipe_ring <= Gmax) {
+      const int nb = 3 * N;
+      if (!d_pipe) CUDA_TRY(cudaMalloc(&d_pipe, nb * sizeof(int) + 16));
+      if (!pipe_grid) {
+        int per = 0;
+        CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k2.slabpipe, k2.NTPIPE, k2.smPIPE));
+        pipe_grid = (per > 0 ? per : 1) * nsm;
+      }
+      CUDA_TRY(cudaMemsetAsync(d_pipe, 0, nb * sizeof(int) + 16, st));
+      PipeCtl ctl;
+      ctl.done = reinterpret_cast<int*>(d_pipe);
+      ctl.next = reinterpret_cast<unsigned long long*>(d_pipe + nb * sizeof(int));
+      ctl.abort = reinterpret_cast<int*>(d_pipe + nb * sizeof(int) + 8);
+      ctl.spin_limit = pipe_spin;
+      ctl.ring = pipe_ring;
+      ctl.lag = pipe_lag;
+      ctl.stall = pipe_stall;
+      a.z0 = 0;
+      a.G = pipe_ring;
+      a.scr = scr;
+      cudaEvent_t e = prof_begin(NS_PROF_SLAB_PIPE);
+      k2.slabpipe<<<pipe_grid, k2.NTPIPE, k2.smPIPE, st>>>(a, ctl);
+      prof_end(e);
+      prof_end(pass);
+      LAUNCH_CHECK();
+      return;
+    }
     const bool two = use2 && slab_streams == 2 && G < N && 2 * G <= Gmax;
     if (two) {
       ensure_streams();
@@ -637,7 +674,9 @@ struct Solver : SolverBase {
   // slab pass with CUDA events; the fastest is kept and cached in a JSON file keyed by device,
   // N, precision and the slab tiles.  Results do not depend on G or on the streams (every
   // plane is transformed the same way).  NS_AUTOTUNE=0 disables it; NS_AUTOTUNE_CACHE sets the
-  // cache file; NS_SLAB_PLANES=g forces a group size, NS_SLAB_STREAMS=1|2 the stream count.
+  // cache file; NS_SLAB_PLANES=g forces a group size, NS_SLAB_STREAMS=1|2 the stream count,
+  // NS_SLAB_PIPE=1 the pipeline (ring NS_PIPE_RING, lag NS_PIPE_LAG) and =0 excludes it;
+  // NS_PIPE_SPIN bounds its waits, NS_PIPE_TEST_STALL=1 makes them unsatisfiable (test hook).
   static std::string cache_path() {
     const char* e = std::getenv("NS_AUTOTUNE_CACHE");
     if (e && *e) return e;
@@ -709,10 +748,34 @@ struct Solver : SolverBase {
     ::mkdir(d.c_str(), 0755);
   }
 
-  // The cached value encodes the group size and the stream count: 2 G + (streams - 1).
+  // The cached value encodes the mode: 4 G + m, m = 0 one stream, 1 two streams (G planes per
+  // group), 2 the pipeline (G = ring planes, lag G / 4).
+  void set_mode(int g, int m) {
+    pipe = m == 2;
+    if (pipe) {
+      pipe_ring = g;
+      pipe_lag = g / 4 > 0 ? g / 4 : 1;
+    } else {
+      G = g;
+      slab_streams = m + 1;
+    }
+  }
   void autotune() {
     carry_step = -1;  // the mixed fields / state / forcing record change here
     tuned = true;
+    if (const char* e = std::getenv("NS_PIPE_SPIN")) pipe_spin = std::max(1ll, std::atoll(e));
+    if (const char* e = std::getenv("NS_PIPE_TEST_STALL")) pipe_stall = std::atoi(e) ? 1 : 0;
+    const char* fpipe = std::getenv("NS_SLAB_PIPE");
+    const bool can_pipe = use2 && k2.slabpipe && !(fpipe && std::string(fpipe) == "0");
+    if (fpipe && std::string(fpipe) == "1" && can_pipe) {  // forced pipeline
+      const char* fr = std::getenv("NS_PIPE_RING");
+      int r = fr ? std::atoi(fr) : 32;
+      r = std::max(2, std::min(r, std::min(Gmax, N)));
+      set_mode(r, 2);
+      if (const char* fl = std::getenv("NS_PIPE_LAG")) pipe_lag = std::max(1, std::atoi(fl));
+      if (2 * pipe_lag >= pipe_ring) pipe_lag = (pipe_ring - 1) / 2 > 0 ? (pipe_ring - 1) / 2 : 1;
+      return;
+    }
     if (const char* fs = std::getenv("NS_SLAB_STREAMS")) slab_streams = std::atoi(fs) == 2 ? 2 : 1;
     if (const char* fg = std::getenv("NS_SLAB_PLANES")) {  // forced group size
       const int g = std::atoi(fg);
@@ -722,16 +785,21 @@ struct Solver : SolverBase {
     const char* en = std::getenv("NS_AUTOTUNE");
     if (en && std::string(en) == "0") return;
     if (Gmax <= 1 || N < 128) return;  // small grids: one group holds every plane
-    const std::string path = cache_path(), key = tune_key() + "|g2s";
+    const std::string path = cache_path(), key = tune_key() + (can_pipe ? "|g4p" : "|g4");
     int g = 0;
-    if (cache_lookup(path, key, &g) && g / 2 >= 1 && g / 2 <= Gmax) {
-      G = g / 2;
-      slab_streams = 1 + (g & 1);
+    if (cache_lookup(path, key, &g) && g / 4 >= 1 && g / 4 <= Gmax && (g & 3) <= 2) {
+      set_mode(g / 4, g & 3);
       return;
     }
-    std::vector<int> cand;
-    for (int q : {8, 12, 16, 19, 24, 28, 32, 38, 43, 48, 57, 64, 76, 96, 128, 171, 256, 384, 512, 768})
-      if (q <= Gmax) cand.push_back(q);
+    std::vector<std::pair<int, int>> cand;  // (G or ring, mode)
+    for (int q : {8, 12, 16, 19, 24, 28, 32, 38, 43, 48, 57, 64, 76, 96, 128, 171, 256, 384, 512, 768}) {
+      if (q > Gmax) continue;
+      cand.push_back({q, 0});
+      if (q < N && 2 * q <= Gmax) cand.push_back({q, 1});  // two streams need two groups
+    }
+    if (can_pipe)
+      for (int r : {16, 24, 32, 48})
+        if (r <= Gmax && r <= N) cand.push_back({r, 2});
     if (cand.empty()) return;
     CUDA_TRY(cudaMemsetAsync(mixed[0], 0, 5 * F1 * sizeof(cpx<T>), st));
     cudaEvent_t e0, e1;
@@ -740,32 +808,28 @@ struct Solver : SolverBase {
     const bool pon = prof.on;
     prof.on = false;
     float best = 1e30f;
-    int bestG = G, bestS = 1;
-    for (int q : cand) {
-      for (int ns2 = 1; ns2 <= 2; ++ns2) {
-        if (ns2 == 2 && (q >= N || 2 * q > Gmax)) continue;  // two streams need two groups
-        G = q;
-        slab_streams = ns2;
-        slab(mixed[0], Ft[0]);  // warm-up
-        CUDA_TRY(cudaEventRecord(e0, st));
-        for (int r = 0; r < 8; ++r) slab(mixed[0], Ft[0]);
-        CUDA_TRY(cudaEventRecord(e1, st));
-        CUDA_TRY(cudaEventSynchronize(e1));
-        float ms = 0;
-        CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
-        if (ms < best) {
-          best = ms;
-          bestG = q;
-          bestS = ns2;
-        }
+    std::pair<int, int> bestc = {G, 0};
+    for (const auto& cm : cand) {
+      set_mode(cm.first, cm.second);
+      slab(mixed[0], Ft[0]);  // warm-up
+      CUDA_TRY(cudaEventRecord(e0, st));
+      for (int r = 0; r < 8; ++r) slab(mixed[0], Ft[0]);
+      CUDA_TRY(cudaEventRecord(e1, st));
+      CUDA_TRY(cudaEventSynchronize(e1));
+      float ms = 0;
+      CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+      if (ms < best) {
+        best = ms;
+        bestc = cm;
       }
     }
+    sync_check();  // a pipeline candidate that gave up reports here
     prof.on = pon;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    G = bestG;
-    slab_streams = bestS;
-    cache_store(path, key, 2 * G + (slab_streams - 1));
+    pipe = false;
+    set_mode(bestc.first, bestc.second);
+    cache_store(path, key, 4 * bestc.first + bestc.second);
   }
 
   // ---- schemes ------------------------------------------------------------------------

@@ -94,11 +94,6 @@ struct BCfg {
   static constexpr size_t SM = SM_ab > SM_c ? SM_ab : SM_c;
 };
 
-__device__ __forceinline__ int ld_acquire(const int* p) {
-  int v;
-  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
 
 // last index i with off[i] <= r  (off ascending, off[0] = 0, off[n] = total)
 __device__ __forceinline__ int upper_member(const int* off, int n, int r) {

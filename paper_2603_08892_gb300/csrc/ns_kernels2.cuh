@@ -669,20 +669,21 @@ struct ScrCol {  // one field [plane][y|ky][kx], column tile of a plane (scratch
   }
 };
 
-template <typename T, int N, int F, class MP>
+template <typename T, int N, int F, class MP, int TY = K2Cfg<T, N>::TYI, int NT = K2Cfg<T, N>::NTYI>
 __device__ __forceinline__ void yinv_field(const SlabArgs<T>& a, const cpx<T>* in, cpx<T>* W,
                                            int zg, int x0, size_t sstride, const cpx<T>* tws) {
   using C = K2Cfg<T, N>;
-  cfft<T, N, 1, C::TYI, C::NTYI, true, 1, C::RYI>(YInvSrc<T, N, F, C::TYI>{in, x0},
-                                          ScrCol<T, N, MP>{a.scr + F * sstride, zg, x0}, W, tws);
+  cfft<T, N, 1, TY, NT, true, 1, C::RYI>(YInvSrc<T, N, F, TY>{in, x0},
+                                         ScrCol<T, N, MP>{a.scr + F * sstride, zg, x0}, W, tws);
   __syncthreads();
 }
 
 // One tile: TYI consecutive kx of plane zg; the 5 mixed input tiles are staged first.
-template <typename T, int N, class MP>
+// TY_, NT_: tile width and threads (the defaults of the size; the slab pipeline uses 4 columns)
+template <typename T, int N, class MP, int TY_ = K2Cfg<T, N>::TYI, int NT_ = K2Cfg<T, N>::NTYI>
 __device__ __forceinline__ void yinv_tile(const SlabArgs<T>& a, int tx, int zg, cpx<T>* in) {
   using C = K2Cfg<T, N>;
-  constexpr int M = N / 2, TY = C::TYI, NT = C::NTYI, tile = lf_rows<T, TY>(N) * TY;
+  constexpr int M = N / 2, TY = TY_, NT = NT_, tile = lf_rows<T, TY>(N) * TY;
   cpx<T>* W = in + 5 * tile;
   cpx<T>* tws = in + 6 * tile;
   const int x0 = tx * TY, z = a.z0 + zg;
@@ -696,14 +697,14 @@ __device__ __forceinline__ void yinv_tile(const SlabArgs<T>& a, int tx, int zg, 
   for (int i = threadIdx.x; i < N; i += blockDim.x) tws[tw_pad(i)] = ldg(&a.tw[i]);
   cp_async_wait_pending<1>();
   __syncthreads();
-  yinv_field<T, N, 0, MP>(a, in, W, zg, x0, sstride, tws);
-  yinv_field<T, N, 1, MP>(a, in, W, zg, x0, sstride, tws);
-  yinv_field<T, N, 2, MP>(a, in, W, zg, x0, sstride, tws);
-  yinv_field<T, N, 5, MP>(a, in, W, zg, x0, sstride, tws);  // omega_z: u_x, u_y only
+  yinv_field<T, N, 0, MP, TY, NT>(a, in, W, zg, x0, sstride, tws);
+  yinv_field<T, N, 1, MP, TY, NT>(a, in, W, zg, x0, sstride, tws);
+  yinv_field<T, N, 2, MP, TY, NT>(a, in, W, zg, x0, sstride, tws);
+  yinv_field<T, N, 5, MP, TY, NT>(a, in, W, zg, x0, sstride, tws);  // omega_z: u_x, u_y only
   cp_async_wait_pending<0>();
   __syncthreads();
-  yinv_field<T, N, 3, MP>(a, in, W, zg, x0, sstride, tws);
-  yinv_field<T, N, 4, MP>(a, in, W, zg, x0, sstride, tws);
+  yinv_field<T, N, 3, MP, TY, NT>(a, in, W, zg, x0, sstride, tws);
+  yinv_field<T, N, 4, MP, TY, NT>(a, in, W, zg, x0, sstride, tws);
 }
 
 template <typename T, int N>
@@ -849,6 +850,123 @@ __global__ void __launch_bounds__(K2Cfg<T, N>::NTX) k2_xrow(SlabArgs<T> a) {
   xrow_tile<T, N, MemNC>(a, blockIdx.x, reinterpret_cast<cpx<T>*>(smem_raw));
 }
 
+// ---- slab pipeline: the three slab kernels as one persistent launch -------------------
+__device__ __forceinline__ int ld_acquire(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Control block of a pipeline launch (zeroed by the host before each launch).
+struct PipeCtl {
+  unsigned long long* next;  // ticket counter
+  int* done;                 // [3][N]: finished y-inverse, x-row and y-forward tiles per plane
+  int* abort;                // set when a wait gives up: every block leaves its loop
+  long long spin_limit;      // polls before a wait gives up (then bit PIPE_ERR_TIMEOUT in err)
+  int ring, lag;             // scratch planes in the ring; slots between the three stages
+  int stall;                 // test hook: added to every awaited count (waits cannot succeed)
+};
+constexpr int PIPE_ERR_TIMEOUT = 0x100;
+#ifndef NS_PIPE_MINB
+#define NS_PIPE_MINB 3  // resident blocks per SM the register allocation must allow
+#endif
+
+// Work items of plane z: y-inverse tiles of 4 columns, x-row tiles of RX rows, y-forward
+// tiles; tickets in slot order, slot s = [y-inverse(s), x rows(s - lag), y-forward(s - 2 lag)].
+template <typename T, int N>
+struct PipeCfg {
+  using C = K2Cfg<T, N>;
+  static constexpr int M = N / 2;
+  static constexpr int TYP = 4;
+  static constexpr int NTYP = round_warps(TYP * N / C::RYI);
+  static constexpr int nYI = M / TYP, nX = N / C::RX, nYF = M / C::TY;
+  static constexpr int per_slot = nYI + nX + nYF;
+  static constexpr int NT = cmax(cmax(NTYP, C::NTX), C::NTY);
+  static constexpr bool ok = N % C::RX == 0 && M % TYP == 0 && TYP % C::MINW == 0;
+  static constexpr size_t smem = sizeof(cpx<T>) *
+      cmax(cmax(6 * lf_rows<T, TYP>(N) * TYP, lf_rows<T, C::TY>(N) * C::TY), 2 * C::XBUF) +
+      sizeof(cpx<T>) * tw_elems(N);
+};
+
+// One slab pass over all N planes with the scratch as a ring of `ring` planes: every item
+// waits (bounded) for the items it reads: x rows(z) for y-inverse(z), y-forward(z) for
+// x rows(z), y-inverse(z) for y-forward(z - ring) (the ring slot it overwrites).  Each waits on
+// an earlier ticket, held by a running block, so the pipeline progresses whatever the number
+// of resident blocks.  Data written in the launch is read through L2 (MemCG).
+// the y-pass tile bodies as separate functions (the union of the three bodies in one
+// allocation spilled); the x-row body stays inline
+template <typename T, int N>
+__device__ __noinline__ void pipe_yinv(const SlabArgs<T>& b, int tile, int zs, cpx<T>* smem) {
+  yinv_tile<T, N, MemCG, PipeCfg<T, N>::TYP, PipeCfg<T, N>::NTYP>(b, tile, zs, smem);
+}
+template <typename T, int N>
+__device__ __noinline__ void pipe_yfwd(const SlabArgs<T>& b, int tile, int zs, cpx<T>* smem) {
+  yfwd_tile<T, N, MemCG>(b, tile, zs, smem);
+}
+
+template <typename T, int N>
+__global__ void __launch_bounds__(PipeCfg<T, N>::NT, NS_PIPE_MINB)
+    k2_slabpipe(SlabArgs<T> a, PipeCtl c) {
+  using P = PipeCfg<T, N>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cpx<T>* smem = reinterpret_cast<cpx<T>*>(smem_raw);
+  __shared__ long long s_t;
+  __shared__ int s_go;
+  const long long total = (long long)(N + 2 * c.lag) * P::per_slot;
+  for (;;) {
+    if (threadIdx.x == 0) s_t = (long long)atomicAdd(c.next, 1ull);
+    __syncthreads();
+    const long long tk = s_t;
+    __syncthreads();
+    if (tk >= total) break;
+    const int slot = (int)(tk / P::per_slot), r = (int)(tk % P::per_slot);
+    int type, z, tile;
+    if (r < P::nYI) {
+      type = 0; z = slot; tile = r;
+    } else if (r < P::nYI + P::nX) {
+      type = 1; z = slot - c.lag; tile = r - P::nYI;
+    } else {
+      type = 2; z = slot - 2 * c.lag; tile = r - P::nYI - P::nX;
+    }
+    if (z < 0 || z >= N) continue;
+    const int wtype = type == 0 ? 2 : type - 1;
+    const int wz = type == 0 ? z - c.ring : z;
+    const int wcnt = (type == 0 ? P::nYF : type == 1 ? P::nYI : P::nX) + c.stall;
+    if (threadIdx.x == 0) {
+      int ok = 1;
+      if (wz >= 0) {
+        long long it = 0;
+        while (ld_acquire(&c.done[wtype * N + wz]) < wcnt) {
+          if (*(volatile int*)c.abort || ++it > c.spin_limit) {
+            ok = 0;
+            atomicOr(a.err, PIPE_ERR_TIMEOUT);
+            atomicExch(c.abort, 1);
+            break;
+          }
+          __nanosleep(64);
+        }
+      }
+      s_go = ok;
+    }
+    __syncthreads();
+    if (!s_go) break;
+    const int zs = z % c.ring;
+    SlabArgs<T> b = a;
+    b.z0 = z - zs;
+    if (type == 0)
+      pipe_yinv<T, N>(b, tile, zs, smem);
+    else if (type == 1)
+      xrow_tile<T, N, MemCG>(b, zs * P::nX + tile, smem);  // inline: it needs every register
+    else
+      pipe_yfwd<T, N>(b, tile, zs, smem);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      atomicAdd(&c.done[type * N + z], 1);
+    }
+  }
+}
+
 // ---- registry entry of one size ------------------------------------------------------
 template <typename T>
 struct K2Entry {
@@ -859,6 +977,9 @@ struct K2Entry {
   void (*yinv)(SlabArgs<T>) = nullptr;
   void (*yfwd)(SlabArgs<T>) = nullptr;
   void (*xrow)(SlabArgs<T>) = nullptr;
+  void (*slabpipe)(SlabArgs<T>, PipeCtl) = nullptr;  // null when the size has no pipeline
+  int NTPIPE = 0;
+  size_t smPIPE = 0;
   int TX = 0, NTP = 0, TY = 0, NTY = 0, TYI = 0, NTYI = 0, RX = 0, NTX = 0;
   size_t smP1 = 0, smP4 = 0, smP5 = 0, smY = 0, smYI = 0, smX = 0;
 };
@@ -878,6 +999,11 @@ K2Entry<T> make_k2_entry() {
   e.yinv = k2_yinv<T, N>;
   e.yfwd = k2_yfwd<T, N>;
   e.xrow = k2_xrow<T, N>;
+  if constexpr (PipeCfg<T, N>::ok) {
+    e.slabpipe = k2_slabpipe<T, N>;
+    e.NTPIPE = PipeCfg<T, N>::NT;
+    e.smPIPE = PipeCfg<T, N>::smem;
+  }
   e.TX = C::TX; e.NTP = C::NTP; e.TY = C::TY; e.NTY = C::NTY; e.RX = C::RX; e.NTX = C::NTX;
   e.TYI = C::TYI; e.NTYI = C::NTYI;
   e.smYI = (6 * (size_t)lf_rows<T, C::TYI>(N) * C::TYI + tw_elems(N)) * sizeof(cpx<T>);

@@ -300,14 +300,18 @@ def test_specialised_and_generic_kernels_agree(ns, prec, code, monkeypatch):
 
 
 def test_results_do_not_depend_on_slab_group_size(ns, monkeypatch, tmp_path):
-    # the autotuner only changes how the planes are grouped and on how many streams the
-    # groups run (double-buffered scratch): the arithmetic of every plane is the same
+    # the autotuner only changes how the planes are grouped, on how many streams the groups
+    # run (double-buffered scratch) or whether one pipelined launch (a ring of scratch
+    # planes) does the pass: the arithmetic of every plane is the same
     N = 128
     u = field(N, seed=31)
     out = []
     monkeypatch.setenv("NS_AUTOTUNE_CACHE", str(tmp_path / "tune.json"))
-    for g, streams in (("5", "1"), ("128", "1"), ("24", "2"), ("5", "2"), (None, None)):
-        for var, val in (("NS_SLAB_PLANES", g), ("NS_SLAB_STREAMS", streams)):
+    for g, streams, pipe in (("5", "1", None), ("128", "1", None), ("24", "2", None),
+                             ("5", "2", None), (None, None, "16"), (None, None, "5"),
+                             (None, None, None)):
+        for var, val in (("NS_SLAB_PLANES", g), ("NS_SLAB_STREAMS", streams),
+                         ("NS_SLAB_PIPE", "1" if pipe else None), ("NS_PIPE_RING", pipe)):
             if val is None:
                 monkeypatch.delenv(var, raising=False)
             else:
@@ -352,3 +356,28 @@ def test_step_calls_split_anywhere_bitwise(ns, name, prec):
             runs.append((s.get_state(), s.time()))
     for st, t in runs[1:]:
         assert np.array_equal(st, runs[0][0]) and t == runs[0][1]
+
+
+
+def test_slab_pipeline_bounded_wait_times_out_and_recovers(ns, monkeypatch, tmp_path):
+    # the pipeline's waits made unsatisfiable (test hook): the launch gives up, the next
+    # synchronising call reports NS_ERR_TIMEOUT, and the GPU keeps working
+    N = 128
+    u = field(N, seed=5)
+    monkeypatch.setenv("NS_AUTOTUNE_CACHE", str(tmp_path / "tune.json"))
+    monkeypatch.setenv("NS_SLAB_PIPE", "1")
+    monkeypatch.setenv("NS_PIPE_RING", "16")
+    monkeypatch.setenv("NS_PIPE_SPIN", "20000")
+    monkeypatch.setenv("NS_PIPE_TEST_STALL", "1")
+    with ns.Solver(N, 0.001, N / 2, scheme=4, precision=0, seed=3) as s:
+        s.set_velocity(u)
+        s.step(0.005, 1)
+        with pytest.raises(ns.NSError) as e:
+            s.energy()
+        assert e.value.code == 7
+    monkeypatch.delenv("NS_PIPE_TEST_STALL")
+    with ns.Solver(N, 0.001, N / 2, scheme=4, precision=0, seed=3) as s:
+        s.set_velocity(u)
+        s.step(0.005, 2)
+        E, _ = s.energy()
+    assert np.isfinite(E)
