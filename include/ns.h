@@ -149,7 +149,9 @@ int ns_vjp(ns_ctx* ctx, const double* u0, int nsteps, double dt, int ckpt_every,
            double* loss_out, double* grad_u0_out);
 
 /* Kinetic energy E = (1/2) sum_k |uh|^2 and dissipation eps = nu sum_k k^2 |uh|^2 (full
- * spectrum sums, FP64 accumulation; Sec. 3.4).  NS_ERR_NONFINITE if either is not finite. */
+ * spectrum sums, Sec. 3.4; FP64 states in FP64, FP32 states with each mode's terms in FP32,
+ * compensated per-thread sums and FP64 across threads; fixed order, so repeatable).
+ * NS_ERR_NONFINITE if either is not finite. */
 int ns_energy(ns_ctx* ctx, double* E, double* eps);
 /* Energy spectrum, FP64 bins k = 0..nbins-1: NS_SPEC_SHELL bins floor(|k| + 1/2),
  * NS_SPEC_X/Y/Z fold +-k_i onto |k_i| (Sec. 3.4, Eq. quality uses the 1D spectra). */

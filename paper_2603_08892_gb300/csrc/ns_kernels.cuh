@@ -615,7 +615,8 @@ __global__ void k_force_coef(const cpx<double>* __restrict__ pj, const cpx<doubl
 }
 
 // ----------------------------------------------------------------------------------------
-// Reductions (FP64 accumulation; fixed-order tree: bitwise reproducible)
+// Reductions (FP64 across threads and blocks; per thread FP64, or compensated FP32 for FP32
+// states; fixed-order tree: bitwise reproducible)
 // ----------------------------------------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(256) k_energy(const cpx<T>* __restrict__ S, int N, double nu,

@@ -2,10 +2,12 @@
 //
 // Same passes, layouts and arithmetic as the generic kernels of ns_kernels.cuh (see there
 // for the data layout): k2_pencil = z transforms + spectral stage of Sec. 4 / 6.1,
-// k2_yinv / k2_xrow / k2_yfwd = slab pass (y transforms, x rows with u x omega).  What
-// changes is how the transforms run: the first FFT stage reads global memory directly and
-// the last one writes it, every index is a compile-time expression, and the butterflies
-// are radix 16 in registers.
+// k2_yinv / k2_xrow / k2_yfwd = slab pass (y transforms, x rows with u x omega), and
+// k2_slabpipe = the slab pass as one persistent pipelined launch.  What changes is how the
+// transforms run: tiles are staged with cp.async, the first FFT stage reads the staged tile
+// or global memory and the last one writes global memory or applies the spectral factors,
+// every index is a compile-time expression, and the butterflies are radix 8 or 16 in
+// registers (per kernel, K2Cfg).
 #pragma once
 
 #include "ns_fft2.cuh"
