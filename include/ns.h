@@ -89,7 +89,9 @@ const char* ns_last_error(ns_ctx* ctx);
  * projection P, mean mode zeroed (Sec. 3.2; Sec. 4.1 below Eq. base-eq).  A
  * non-solenoidal input is projected.  Resets time and step counter to 0. */
 int ns_set_velocity(ns_ctx* ctx, const double* u);
-/* State -> physical velocity u_out (host, [3][N][N][N]). */
+/* State -> physical velocity u_out (host, [3][N][N][N]).  This call, ns_get_state, ns_step,
+ * ns_step_cfl, ns_energy, ns_energy_spectrum and ns_energy_flux return NS_ERR_STATE on a
+ * context that has no state yet (no ns_set_velocity, ns_set_state or ns_checkpoint_load). */
 int ns_get_velocity(ns_ctx* ctx, double* u_out);
 /* Copies the spectral state to/from host re_im[3][N][N][N/2][2] (no truncation or
  * projection applied on set: resuming from ns_get_state output is bitwise exact). */

@@ -1551,6 +1551,7 @@ int ns_set_velocity(ns_ctx* c, const double* u) {
 int ns_get_velocity(ns_ctx* c, double* u) {
   return guarded(c, [&]() {
     if (!u) return fail(c, NS_ERR_INVALID_ARG, "u_out is NULL");
+    if (!c->have_state) return fail(c, NS_ERR_STATE, "no velocity or state set");
     c->solver->get_velocity(u);
     return (int)NS_OK;
   });
@@ -1559,6 +1560,7 @@ int ns_get_velocity(ns_ctx* c, double* u) {
 int ns_get_state(ns_ctx* c, double* s) {
   return guarded(c, [&]() {
     if (!s) return fail(c, NS_ERR_INVALID_ARG, "re_im_out is NULL");
+    if (!c->have_state) return fail(c, NS_ERR_STATE, "no velocity or state set");
     c->solver->get_state(s);
     return (int)NS_OK;
   });
@@ -1634,6 +1636,7 @@ int ns_nonlinear(ns_ctx* c, const double* in, const double* delta, double* out) 
 int ns_energy(ns_ctx* c, double* E, double* eps) {
   return guarded(c, [&]() {
     if (!E || !eps) return fail(c, NS_ERR_INVALID_ARG, "NULL output");
+    if (!c->have_state) return fail(c, NS_ERR_STATE, "no velocity or state set");
     c->solver->energy(E, eps);
     if (!std::isfinite(*E) || !std::isfinite(*eps)) return fail(c, NS_ERR_NONFINITE, "energy is not finite");
     return (int)NS_OK;
@@ -1644,6 +1647,7 @@ int ns_energy_spectrum(ns_ctx* c, int kind, double* out, int nbins) {
   return guarded(c, [&]() {
     if (!out || nbins <= 0 || nbins > 4096) return fail(c, NS_ERR_INVALID_ARG, "need out != NULL, 0 < nbins <= 4096");
     if (kind < NS_SPEC_SHELL || kind > NS_SPEC_Z) return fail(c, NS_ERR_INVALID_ARG, "unknown spectrum kind");
+    if (!c->have_state) return fail(c, NS_ERR_STATE, "no velocity or state set");
     c->solver->spectrum(kind, out, nbins);
     return (int)NS_OK;
   });
@@ -1656,6 +1660,7 @@ int ns_energy_flux(ns_ctx* c, const double* delta, int nshift, double* flux, dou
       return fail(c, NS_ERR_INVALID_ARG, "need 0 <= nshift <= 8 and delta for nshift > 0");
     for (int i = 0; i < 3 * nshift; ++i)
       if (!std::isfinite(delta[i])) return fail(c, NS_ERR_INVALID_ARG, "non-finite shift");
+    if (!c->have_state) return fail(c, NS_ERR_STATE, "no velocity or state set");
     c->solver->energy_flux(delta, nshift, flux, cumdiss, nbins);
     return (int)NS_OK;
   });

@@ -197,6 +197,10 @@ def test_degenerate_cases(ns):
         with pytest.raises(ns.NSError) as e:
             s.step(0.01, 1)  # no state yet
         assert e.value.code == 8
+        for call in (s.energy, s.get_state, lambda: s.spectrum(0, 8), lambda: s.energy_flux(8)):
+            with pytest.raises(ns.NSError) as e:
+                call()
+            assert e.value.code == 8
         s.set_velocity(np.zeros((3, N, N, N)))
         s.step(0.01, 0)  # empty run is a no-op
         assert s.time() == (0.0, 0)
