@@ -139,8 +139,16 @@ struct K2Cfg {
   static constexpr int RYI = radix_cap(NS_RADIX_YI, NS_MAX_RADIX, F32);
   static constexpr int RYF = radix_cap(NS_RADIX_YF, 16, F32);
   static constexpr int RXR = radix_cap(NS_RADIX_X, 16, F32);
-  // pencil: TX columns of N
-  static constexpr int TX = pick_div(M, cmax(16384 / (N * CS), MINW), 16);
+  // pencil: TX columns of N (NS_PZ_LINES / NS_YF_LINES override the pencil / forward-y width)
+#ifndef NS_PZ_LINES
+#define NS_PZ_LINES 0
+#endif
+#ifndef NS_YF_LINES
+#define NS_YF_LINES 0
+#endif
+  static constexpr int TX = (NS_PZ_LINES > 0 && M % NS_PZ_LINES == 0 && NS_PZ_LINES % MINW == 0)
+                                ? NS_PZ_LINES
+                                : pick_div(M, cmax(16384 / (N * CS), MINW), 16);
   static constexpr int NTP = round_lines(TX * N / RZ, TX);
   // blocks per SM the register budget must allow (NS_PENCIL_REGS registers per thread;
   // 80 measured best at 256^3 FP32 on GB300 against 96 and 128)
@@ -149,9 +157,12 @@ struct K2Cfg {
 #endif
   static constexpr int MINB_P = cmax(1, cmin(8, 65536 / (NTP * NS_PENCIL_REGS)));
   // y passes: TY columns of N
-  static constexpr int TY = pick_div(M, cmax(16384 / (N * CS), MINW), 16);
+  static constexpr int TY = (NS_YF_LINES > 0 && M % NS_YF_LINES == 0 && NS_YF_LINES % MINW == 0)
+                                ? NS_YF_LINES
+                                : pick_div(M, cmax(16384 / (N * CS), MINW), 16);
   static constexpr int NTY = round_warps(TY * N / RYF);
-  // inverse y pass: the 5 mixed input tiles are staged in shared memory (6 tiles in all)
+  // inverse y pass: 4 shared tiles (3 input slots and a work tile); the width is the one
+  // measured best when the tile held 6 (the 5 inputs and the work tile) within 110 KB
 #ifndef NS_YI_LINES
 #define NS_YI_LINES 0
 #endif
@@ -641,8 +652,9 @@ __global__ void __launch_bounds__(K2Cfg<T, N>::NTP, (NFC == 2 || (NFC == 1 && NS
 }
 
 // ---- slab pass: y transforms --------------------------------------------------------
-// field F of the spectral-in-xy pair (u, omega) formed on the fly from the 5 mixed
-// fields staged in shared memory ([f][e][line], TY lines)
+// field F of the spectral-in-xy pair (u, omega) formed on the fly from the mixed fields
+// staged in shared memory ([slot][e][line], TY lines): slots 0, 1, 2 hold u_x, u_y, u_z,
+// then d_z u_x and d_z u_y replace u_x and u_y in slots 0 and 1 once those are transformed.
 template <typename T, int N, int F, int TY>
 struct YInvSrc {
   const cpx<T>* m;
@@ -654,8 +666,8 @@ struct YInvSrc {
     if (F == 0) return m[i];
     if (F == 1) return m[i + fs];
     if (F == 2) return m[i + 2 * fs];
-    if (F == 3) return mul_si(m[i + 2 * fs], ky) - m[i + 4 * fs];   // i ky u_z - d_z u_y
-    if (F == 4) return m[i + 3 * fs] - mul_si(m[i + 2 * fs], kx);   // d_z u_x - i kx u_z
+    if (F == 3) return mul_si(m[i + 2 * fs], ky) - m[i + fs];       // i ky u_z - d_z u_y
+    if (F == 4) return m[i] - mul_si(m[i + 2 * fs], kx);            // d_z u_x - i kx u_z
     return mul_si(m[i + fs], kx) - mul_si(m[i], ky);                // i kx u_y - i ky u_x
   }
 };
@@ -671,42 +683,54 @@ struct ScrCol {  // one field [plane][y|ky][kx], column tile of a plane (scratch
   }
 };
 
-template <typename T, int N, int F, class MP, int TY = K2Cfg<T, N>::TYI, int NT = K2Cfg<T, N>::NTYI>
-__device__ __forceinline__ void yinv_field(const SlabArgs<T>& a, const cpx<T>* in, cpx<T>* W,
-                                           int zg, int x0, size_t sstride, const cpx<T>* tws) {
+// One output field of the y-inverse.  IP: the field's only input is slot SLOT, which the
+// transform then uses as its work tile (its inputs are read before the tile is written);
+// otherwise the transform goes through the work tile W.
+template <typename T, int N, int F, class MP, int TY, int NT, bool IP = false>
+__device__ __forceinline__ void yinv_field(const SlabArgs<T>& a, cpx<T>* in, cpx<T>* W, int zg,
+                                           int x0, size_t sstride, const cpx<T>* tws) {
   using C = K2Cfg<T, N>;
-  cfft<T, N, 1, TY, NT, true, 1, C::RYI>(YInvSrc<T, N, F, TY>{in, x0},
-                                         ScrCol<T, N, MP>{a.scr + F * sstride, zg, x0}, W, tws);
+  const YInvSrc<T, N, F, TY> src{in, x0};
+  const ScrCol<T, N, MP> dst{a.scr + F * sstride, zg, x0};
+  if constexpr (IP)
+    cfft_src_in_work<T, N, 1, TY, NT, true, 1, C::RYI>(src, dst, in + F * (lf_rows<T, TY>(N) * TY), tws);
+  else
+    cfft<T, N, 1, TY, NT, true, 1, C::RYI>(src, dst, W, tws);
   __syncthreads();
 }
 
-// One tile: TYI consecutive kx of plane zg; the 5 mixed input tiles are staged first.
+// One tile: TYI consecutive kx of plane zg, in 4 shared tiles (3 input slots and a work tile).
+// u_x, u_y, u_z are staged first; omega_z (from u_x, u_y) goes through the work tile, u_x and
+// u_y are transformed in place, and d_z u_x, d_z u_y are then copied into their slots while the
+// next transform runs; omega_y, omega_x and u_z (in place) follow.
 // TY_, NT_: tile width and threads (the defaults of the size; the slab pipeline uses 4 columns)
 template <typename T, int N, class MP, int TY_ = K2Cfg<T, N>::TYI, int NT_ = K2Cfg<T, N>::NTYI>
 __device__ __forceinline__ void yinv_tile(const SlabArgs<T>& a, int tx, int zg, cpx<T>* in) {
-  using C = K2Cfg<T, N>;
   constexpr int M = N / 2, TY = TY_, NT = NT_, tile = lf_rows<T, TY>(N) * TY;
-  cpx<T>* W = in + 5 * tile;
-  cpx<T>* tws = in + 6 * tile;
+  cpx<T>* W = in + 3 * tile;
+  cpx<T>* tws = in + 4 * tile;
   const int x0 = tx * TY, z = a.z0 + zg;
   const size_t sstride = (size_t)a.G * N * M;
   const size_t fs = (size_t)N * N * M;
-  // two copy groups: u (fields 0-2) first, d_z u_x and d_z u_y (3-4) in flight meanwhile
   for (int f = 0; f < 3; ++f) stage_col_tile<T, N, TY, NT, true>(in + f * tile, a.mixed + f * fs, z, x0);
   cp_async_commit();
-  for (int f = 3; f < 5; ++f) stage_col_tile<T, N, TY, NT, true>(in + f * tile, a.mixed + f * fs, z, x0);
-  cp_async_commit();
   for (int i = threadIdx.x; i < N; i += blockDim.x) tws[tw_pad(i)] = ldg(&a.tw[i]);
-  cp_async_wait_pending<1>();
-  __syncthreads();
-  yinv_field<T, N, 0, MP, TY, NT>(a, in, W, zg, x0, sstride, tws);
-  yinv_field<T, N, 1, MP, TY, NT>(a, in, W, zg, x0, sstride, tws);
-  yinv_field<T, N, 2, MP, TY, NT>(a, in, W, zg, x0, sstride, tws);
-  yinv_field<T, N, 5, MP, TY, NT>(a, in, W, zg, x0, sstride, tws);  // omega_z: u_x, u_y only
   cp_async_wait_pending<0>();
   __syncthreads();
-  yinv_field<T, N, 3, MP, TY, NT>(a, in, W, zg, x0, sstride, tws);
-  yinv_field<T, N, 4, MP, TY, NT>(a, in, W, zg, x0, sstride, tws);
+  yinv_field<T, N, 5, MP, TY, NT>(a, in, W, zg, x0, sstride, tws);        // omega_z
+  yinv_field<T, N, 0, MP, TY, NT, true>(a, in, W, zg, x0, sstride, tws);  // u_x in slot 0
+  stage_col_tile<T, N, TY, NT, true>(in, a.mixed + 3 * fs, z, x0);        // d_z u_x -> slot 0
+  cp_async_commit();
+  yinv_field<T, N, 1, MP, TY, NT, true>(a, in, W, zg, x0, sstride, tws);  // u_y in slot 1
+  stage_col_tile<T, N, TY, NT, true>(in + tile, a.mixed + 4 * fs, z, x0); // d_z u_y -> slot 1
+  cp_async_commit();
+  cp_async_wait_pending<1>();
+  __syncthreads();
+  yinv_field<T, N, 4, MP, TY, NT>(a, in, W, zg, x0, sstride, tws);        // omega_y
+  cp_async_wait_pending<0>();
+  __syncthreads();
+  yinv_field<T, N, 3, MP, TY, NT>(a, in, W, zg, x0, sstride, tws);        // omega_x
+  yinv_field<T, N, 2, MP, TY, NT, true>(a, in, W, zg, x0, sstride, tws);  // u_z in slot 2
 }
 
 template <typename T, int N>
@@ -886,7 +910,7 @@ struct PipeCfg {
   static constexpr int NT = cmax(cmax(NTYP, C::NTX), C::NTY);
   static constexpr bool ok = N % C::RX == 0 && M % TYP == 0 && TYP % C::MINW == 0;
   static constexpr size_t smem = sizeof(cpx<T>) *
-      cmax(cmax(6 * lf_rows<T, TYP>(N) * TYP, lf_rows<T, C::TY>(N) * C::TY), 2 * C::XBUF) +
+      cmax(cmax(4 * lf_rows<T, TYP>(N) * TYP, lf_rows<T, C::TY>(N) * C::TY), 2 * C::XBUF) +
       sizeof(cpx<T>) * tw_elems(N);
 };
 
@@ -1008,7 +1032,7 @@ K2Entry<T> make_k2_entry() {
   }
   e.TX = C::TX; e.NTP = C::NTP; e.TY = C::TY; e.NTY = C::NTY; e.RX = C::RX; e.NTX = C::NTX;
   e.TYI = C::TYI; e.NTYI = C::NTYI;
-  e.smYI = (6 * (size_t)lf_rows<T, C::TYI>(N) * C::TYI + tw_elems(N)) * sizeof(cpx<T>);
+  e.smYI = (4 * (size_t)lf_rows<T, C::TYI>(N) * C::TYI + tw_elems(N)) * sizeof(cpx<T>);
   e.smP4 = (3 * (size_t)lf_rows<T, C::TX>(N) * C::TX + tw_elems(N)) * sizeof(cpx<T>);  // 3 tiles + twiddles
   e.smP1 = NS_PENCIL_STAGE_STATE ? (6 * (size_t)lf_rows<T, C::TX>(N) * C::TX + tw_elems(N)) * sizeof(cpx<T>) : e.smP4;
   e.smP5 = (4 * (size_t)lf_rows<T, C::TX>(N) * C::TX + tw_elems(N)) * sizeof(cpx<T>);  // 4 tiles + twiddles
