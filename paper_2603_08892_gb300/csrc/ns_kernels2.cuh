@@ -94,8 +94,9 @@ __device__ __forceinline__ void stage_col_tile(cpx<T>* dst, const cpx<T>* src, i
 }
 
 // Radix cap of each kernel's transforms (pencil z, inverse y, forward y, x rows); 0 = the
-// measured default: in FP32 radix 16 for the forward y and the x rows (one shared-memory pass
-// fewer), radix 8 for the pencil and the inverse y (more threads per tile); 8 in FP64.
+// measured default: in FP32 radix 16 for both y passes and the x rows (one shared-memory pass
+// fewer; the inverse y, bound by shared memory, 0.268 against 0.287 ms per step at 256^3 with
+// radix 8), radix 8 for the pencil (more threads per tile); 8 in FP64.
 #ifndef NS_RADIX_Z
 #define NS_RADIX_Z 0
 #endif
@@ -136,7 +137,7 @@ struct K2Cfg {
   static constexpr int MINW = 32 / CS;  // 32-byte global segments
   static constexpr bool F32 = sizeof(T) == 4;
   static constexpr int RZ = radix_cap(NS_RADIX_Z, NS_MAX_RADIX, F32);
-  static constexpr int RYI = radix_cap(NS_RADIX_YI, NS_MAX_RADIX, F32);
+  static constexpr int RYI = radix_cap(NS_RADIX_YI, 16, F32);
   static constexpr int RYF = radix_cap(NS_RADIX_YF, 16, F32);
   static constexpr int RXR = radix_cap(NS_RADIX_X, 16, F32);
   // pencil: TX columns of N (NS_PZ_LINES / NS_YF_LINES override the pencil / forward-y width)
@@ -171,8 +172,11 @@ struct K2Cfg {
                                  ? NS_YI_LINES
                                  : pick_div(M, cmax(110000 / (6 * N * CS), MINW), 16);
   static constexpr int NTYI = round_warps(TYI * N / RYI);
-  // x rows: RX rows of M, processed three fields at a time
-  static constexpr int RX = cmin(cmax(8192 / (M * CS), 1), 16);
+  // x rows: RX rows of M, processed three fields at a time (NS_XR_ROWS overrides RX)
+#ifndef NS_XR_ROWS
+#define NS_XR_ROWS 0
+#endif
+  static constexpr int RX = NS_XR_ROWS > 0 ? NS_XR_ROWS : cmin(cmax(8192 / (M * CS), 1), 16);
   static constexpr int NTX = round_warps(3 * RX * M / RXR);
   static constexpr int XLS = WorkTile<T, M, 3 * RX, false>::LS;
   static constexpr int XBUF = 3 * RX * XLS;  // elements of one 3-field row buffer
