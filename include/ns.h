@@ -90,8 +90,9 @@ const char* ns_last_error(ns_ctx* ctx);
  * non-solenoidal input is projected.  Resets time and step counter to 0. */
 int ns_set_velocity(ns_ctx* ctx, const double* u);
 /* State -> physical velocity u_out (host, [3][N][N][N]).  This call, ns_get_state, ns_step,
- * ns_step_cfl, ns_energy, ns_energy_spectrum and ns_energy_flux return NS_ERR_STATE on a
- * context that has no state yet (no ns_set_velocity, ns_set_state or ns_checkpoint_load). */
+ * ns_step_cfl, ns_step_diag, ns_energy, ns_energy_spectrum and ns_energy_flux return
+ * NS_ERR_STATE on a context that has no state yet (no ns_set_velocity, ns_set_state or
+ * ns_checkpoint_load). */
 int ns_get_velocity(ns_ctx* ctx, double* u_out);
 /* Copies the spectral state to/from host re_im[3][N][N][N/2][2] (no truncation or
  * projection applied on set: resuming from ns_get_state output is bitwise exact). */
@@ -123,6 +124,16 @@ int ns_step(ns_ctx* ctx, double dt, int nsteps);
  * per step.  ns_time gives the accumulated time.  NS_ERR_INVALID_ARG unless cfl > 0,
  * dt_max > 0 (finite) and nsteps >= 0. */
 int ns_step_cfl(ns_ctx* ctx, double cfl, double dt_max, int nsteps);
+/* Same as ns_step, and E and eps (as ns_energy defines them, Sec. 3.4) of the state after each
+ * step written to the host arrays E_out[nsteps] and eps_out[nsteps] (caller-owned).  The sums
+ * are taken by the pencil pass that writes each step's state (per-tile partial sums, then a
+ * fixed-order FP64 sum; sizes without the size-specialised kernels run a separate reduction),
+ * and each step's pair is written by the device into mapped pinned host memory as it is
+ * produced: no host synchronisation per step; the call returns once every step has completed.  The first call
+ * allocates the series buffers (for max(nsteps, 4096) steps; a longer call reallocates).  NS_ERR_INVALID_ARG unless dt > 0, nsteps >= 0
+ * and both outputs are non-NULL (nsteps > 0); NS_ERR_NONFINITE if the last pair is not finite.
+ * The values agree with ns_energy after each step to rounding (the summation order differs). */
+int ns_step_diag(ns_ctx* ctx, double dt, int nsteps, double* E_out, double* eps_out);
 /* Test hook: delta_alpha for the next nsteps steps (host [nsteps][3], radians), consumed
  * by the following ns_step calls in order; delta_beta = delta_alpha + (pi/N)(1,1,1). */
 int ns_set_shifts(ns_ctx* ctx, const double* delta_alpha, int nsteps);

@@ -63,6 +63,7 @@ _set_forcing = _sig("ns_set_forcing", ctypes.c_int,
                      ctypes.c_double, ctypes.c_uint64])
 _step = _sig("ns_step", ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_int])
 _step_cfl = _sig("ns_step_cfl", ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_double, ctypes.c_int])
+_step_diag = _sig("ns_step_diag", ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_int, _dp, _dp])
 _ckpt_save = _sig("ns_checkpoint_save", ctypes.c_int, [_vp, ctypes.c_char_p])
 _ckpt_load = _sig("ns_checkpoint_load", ctypes.c_int, [_vp, ctypes.c_char_p])
 _set_shifts = _sig("ns_set_shifts", ctypes.c_int, [_vp, _dp, ctypes.c_int])
@@ -102,7 +103,7 @@ PROF_KINDS = {"k_pencil": 0, "k_yinv": 1, "k_xrow": 2, "k_yfwd": 3, "slab_pass":
 
 EXPORTED = ["ns_init", "ns_init_ex", "ns_init_error", "ns_destroy", "ns_last_error",
             "ns_set_velocity", "ns_get_velocity", "ns_get_state", "ns_set_state",
-            "ns_set_forcing", "ns_step", "ns_step_cfl", "ns_set_shifts",
+            "ns_set_forcing", "ns_step", "ns_step_cfl", "ns_step_diag", "ns_set_shifts",
             "ns_checkpoint_save", "ns_checkpoint_load", "ns_nonlinear", "ns_energy",
             "ns_energy_spectrum", "ns_energy_flux", "ns_time", "ns_set_time", "ns_device_state",
             "ns_model_bytes_per_step", "ns_fma_peak", "ns_profile", "ns_profile_read", "ns_nonlinear_noalloc", "ns_vjp", "ns_batch_init", "ns_batch_destroy", "ns_batch_last_error",
@@ -187,6 +188,14 @@ class Solver:
     def step_cfl(self, cfl, dt_max, nsteps=1):
         """nsteps steps with dt = min(dt_max, cfl / sum_i(max|u_i| / dx)) each (ns_step_cfl)."""
         self._check(_step_cfl(self._h, float(cfl), float(dt_max), int(nsteps)))
+
+    def step_diag(self, dt, nsteps=1):
+        """nsteps steps of size dt; returns (E, eps) after each step as two arrays (ns_step_diag)."""
+        n = int(nsteps)
+        E = np.zeros(max(n, 1))
+        eps = np.zeros(max(n, 1))
+        self._check(_step_diag(self._h, float(dt), n, _ptr(E), _ptr(eps)))
+        return E[:n], eps[:n]
 
     def checkpoint_save(self, path):
         """Write the state, time, step, seed and forcing to a file (ns_checkpoint_save)."""

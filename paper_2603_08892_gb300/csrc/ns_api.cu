@@ -127,6 +127,7 @@ struct SolverBase {
   virtual void energy(double* E, double* eps) = 0;
   virtual void spectrum(int kind, double* out, int nbins) = 0;
   virtual void step_cfl(double cfl, double dt_max, int nsteps) = 0;
+  virtual void step_diag(double dt, int nsteps, double* E, double* eps) = 0;
   virtual void invalidate_carry() = 0;  // the next step recomputes its first input
   virtual void raw_state(std::vector<unsigned char>& out) = 0;         // native-precision bytes
   virtual void set_raw_state(const unsigned char* in, size_t n) = 0;
@@ -338,14 +339,22 @@ struct Solver : SolverBase {
     CUDA_TRY(cudaFuncSetAttribute(k_xrow<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
     use2 = k2_find(N, &k2);
     if (use2) {
-      if ((int)k2.smP5 > optin || (int)k2.smP1 > optin || (int)k2.smX > optin || (int)k2.smY > optin || (int)k2.smYI > optin)
-        throw NsError{NS_ERR_INTERNAL, "specialised tile shapes exceed the shared memory of the device"};
-      CUDA_TRY(cudaFuncSetAttribute(k2.pencil, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
-      CUDA_TRY(cudaFuncSetAttribute(k2.pencil1, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
-      CUDA_TRY(cudaFuncSetAttribute(k2.pencil2, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
-      CUDA_TRY(cudaFuncSetAttribute(k2.yinv, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
-      CUDA_TRY(cudaFuncSetAttribute(k2.yfwd, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
-      CUDA_TRY(cudaFuncSetAttribute(k2.xrow, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+      // each kernel may take the opt-in limit less its own static shared memory
+      auto allow = [&](auto* f, size_t need) {
+        cudaFuncAttributes fa;
+        CUDA_TRY(cudaFuncGetAttributes(&fa, f));
+        const int dyn = optin - (int)fa.sharedSizeBytes;
+        if ((long long)need > (long long)dyn)
+          throw NsError{NS_ERR_INTERNAL, "specialised tile shapes exceed the shared memory of the device"};
+        CUDA_TRY(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn));
+      };
+      allow(k2.pencil, k2.smP5);
+      allow(k2.pencil1, k2.smP1);
+      allow(k2.pencil1e, k2.smP1);
+      allow(k2.pencil2, k2.smP5);
+      allow(k2.yinv, k2.smYI);
+      allow(k2.yfwd, k2.smY);
+      allow(k2.xrow, k2.smX);
       if (k2.slabpipe)  // (it has a few bytes of static shared memory: its own size, not optin)
         CUDA_TRY(cudaFuncSetAttribute(k2.slabpipe, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k2.smPIPE));
     }
@@ -377,7 +386,9 @@ struct Solver : SolverBase {
   ~Solver() override {
     cudaFree(state); cudaFree(acc); cudaFree(mixed[0]); cudaFree(mixed[1]);
     cudaFree(nlbuf); cudaFree(nltmp); cudaFree(d_umax); cudaFree(d_pipe);
+    cudaFree(d_epart);
     if (h_err) cudaFreeHost(h_err);
+    if (h_series) cudaFreeHost(h_series);
     cudaFree(Ft[0]); cudaFree(Ft[1]); cudaFree(scr); cudaFree(tw); cudaFree(ifac);
     cudaFree(shtab); cudaFree(d_shifts); cudaFree(red); cudaFree(d_err);
     cudaFree(fpat); cudaFree(force); cudaFree(shell);
@@ -407,6 +418,15 @@ struct Solver : SolverBase {
   }
 
   // ---- device error flag ------------------------------------------------------------
+  // per-step diagnostics (step_diag): the final pencil pass of each step leaves per-tile sums
+  // of its written state in d_epart; their fixed-order sum is written by the device, 16 bytes
+  // per step, straight into the mapped pinned host array h_series (device address d_series)
+  bool diag = false;
+  int diag_n = 0;
+  size_t series_cap = 0;
+  double* d_epart = nullptr;
+  double* d_series = nullptr;
+  double* h_series = nullptr;
   int* h_err = nullptr;  // pinned copy of the device flag: one stream sync per check
   void sync_check() {
     if (!h_err) CUDA_TRY(cudaMallocHost(&h_err, sizeof(int)));
@@ -527,7 +547,7 @@ struct Solver : SolverBase {
   void pencil(const PencilArgs<T>& a) {
     cudaEvent_t e = prof_begin(NS_PROF_PENCIL);
     if (use2)
-      (a.nF == 1 && a.nOut == 1   ? k2.pencil1
+      (a.nF == 1 && a.nOut == 1   ? (a.epart ? k2.pencil1e : k2.pencil1)
        : a.nF == 2 && a.nOut == 2 ? k2.pencil2
                                   : k2.pencil)<<<(M / k2.TX) * N, k2.NTP,
                                                   (a.nF == 1 && a.nOut == 1) ? k2.smP1
@@ -537,6 +557,60 @@ struct Solver : SolverBase {
       k_pencil<T><<<(M / TX) * N, bdP, smP, st>>>(a);
     prof_end(e);
     LAUNCH_CHECK();
+  }
+
+  // the pencil pass that writes a step's new state; with diagnostics on, also E and eps of that
+  // state (Sec. 3.4): fused into the pass (per-tile sums) on the size-specialised kernels, a
+  // separate reduction otherwise; no host synchronisation per step
+  void final_pencil(PencilArgs<T> a) {
+    if (!diag) {
+      pencil(a);
+      return;
+    }
+    const int ntiles = use2 ? (M / k2.TX) * N : 0;
+    if (use2) a.epart = d_epart;
+    pencil(a);
+    double* out = d_series + 2 * (size_t)diag_n;
+    if (use2) {
+      k_sum_pairs<<<1, 256, 0, st>>>(d_epart, ntiles, out, 0.5, c->p.nu);
+    } else {
+      const int nb = red_blocks;
+      k_energy<T><<<nb, 256, 0, st>>>(state, N, c->p.nu, red);
+      k_sum_pairs<<<1, 256, 0, st>>>(red, nb, out);
+    }
+    LAUNCH_CHECK();
+    ++diag_n;
+  }
+
+  void step_diag(double dt, int nsteps, double* E, double* eps) override {
+    if ((size_t)nsteps > series_cap) {  // at least 4096 steps: later calls allocate nothing
+      const size_t cap = nsteps > 4096 ? (size_t)nsteps : 4096;
+      if (h_series) {
+        CUDA_TRY(cudaStreamSynchronize(st));  // no kernel of this stream still writes into it
+        CUDA_TRY(cudaFreeHost(h_series));
+      }
+      d_series = nullptr;
+      h_series = nullptr;
+      series_cap = 0;
+      CUDA_TRY(cudaHostAlloc(&h_series, 2 * cap * sizeof(double), cudaHostAllocMapped));
+      CUDA_TRY(cudaHostGetDevicePointer(&d_series, h_series, 0));
+      series_cap = cap;
+    }
+    if (use2 && !d_epart) CUDA_TRY(cudaMalloc(&d_epart, 2 * (size_t)(M / k2.TX) * N * sizeof(double)));
+    diag = true;
+    diag_n = 0;
+    try {
+      step(dt, nsteps);
+    } catch (...) {
+      diag = false;
+      throw;
+    }
+    diag = false;
+    sync_check();
+    for (int i = 0; i < nsteps; ++i) {
+      E[i] = h_series[2 * (size_t)i];
+      eps[i] = h_series[2 * (size_t)i + 1];
+    }
   }
 
   const cpx<T>* shift_tab(int idx) const { return idx < 0 ? nullptr : shtab + (size_t)idx * 3 * N; }
@@ -943,7 +1017,7 @@ struct Solver : SolverBase {
       b.nOut = 1;  // the last step of the chunk prepares the step after it
       b.osh[0] = alpha(n + 1);
       b.out[0] = mixed[0];
-      pencil(b);
+      final_pencil(b);
       c->t = t + dt;
       c->step += 1;
     }
@@ -969,7 +1043,10 @@ struct Solver : SolverBase {
         a.nOut = exact ? 2 : 1;  // the last pass prepares the next step
         a.osh[0] = nullptr; a.out[0] = mixed[0];
         a.osh[1] = iso; a.out[1] = mixed[1];
-        pencil(a);
+        if (stg == 1)
+          final_pencil(a);
+        else
+          pencil(a);
       }
       c->t = t + dt;
       c->step += 1;
@@ -993,7 +1070,10 @@ struct Solver : SolverBase {
         a.nF = 1; a.F[0] = Ft[0]; a.wF[0] = w;
         a.nOut = 1;  // the last pass prepares the next step
         a.out[0] = mixed[0];
-        pencil(a);
+        if (stg == 3)
+          final_pencil(a);
+        else
+          pencil(a);
       }
       c->t = t + dt;
       c->step += 1;
@@ -1002,13 +1082,44 @@ struct Solver : SolverBase {
   }
 
   // ---- transfers ----------------------------------------------------------------------
+  // Host FP64 <-> device T arrays of n reals.  FP64 contexts copy; FP32 contexts copy the FP64
+  // values through the slab scratch (in chunks of its size) and convert them on the device, so
+  // the host only copies (the conversions round as the host's casts do).
+  size_t stage_doubles() const { return 6 * (size_t)Gmax * N * M * sizeof(cpx<T>) / sizeof(double); }
+  void to_device(const double* h, T* d, size_t n) {
+    if constexpr (sizeof(T) == sizeof(double)) {
+      CUDA_TRY(cudaMemcpyAsync(d, h, n * sizeof(double), cudaMemcpyHostToDevice, st));
+    } else {
+      double* stg = reinterpret_cast<double*>(scr);
+      const size_t cap = stage_doubles();
+      for (size_t o = 0; o < n; o += cap) {
+        const size_t m = n - o < cap ? n - o : cap;
+        CUDA_TRY(cudaMemcpyAsync(stg, h + o, m * sizeof(double), cudaMemcpyHostToDevice, st));
+        k_real_from_double<T><<<8 * nsm, 256, 0, st>>>(stg, d + o, m);
+        LAUNCH_CHECK();
+      }
+    }
+  }
+  void to_host(const T* d, double* h, size_t n) {
+    if constexpr (sizeof(T) == sizeof(double)) {
+      CUDA_TRY(cudaMemcpyAsync(h, d, n * sizeof(double), cudaMemcpyDeviceToHost, st));
+    } else {
+      double* stg = reinterpret_cast<double*>(scr);
+      const size_t cap = stage_doubles();
+      for (size_t o = 0; o < n; o += cap) {
+        const size_t m = n - o < cap ? n - o : cap;
+        k_real_to_double<T><<<8 * nsm, 256, 0, st>>>(d + o, stg, m);
+        LAUNCH_CHECK();
+        CUDA_TRY(cudaMemcpyAsync(h + o, stg, m * sizeof(double), cudaMemcpyDeviceToHost, st));
+      }
+    }
+  }
+
   void set_velocity(const double* u) override {
     carry_step = -1;  // the mixed fields / state / forcing record change here
     const size_t n = 3 * (size_t)N * N * N;
-    std::vector<T> h(n);
-    for (size_t i = 0; i < n; ++i) h[i] = (T)u[i];
     T* rin = reinterpret_cast<T*>(mixed[0]);  // 5 N^3 reals >= 3 N^3
-    CUDA_TRY(cudaMemcpyAsync(rin, h.data(), n * sizeof(T), cudaMemcpyHostToDevice, st));
+    to_device(u, rin, n);
     SlabArgs<T> a = slab_args();
     a.rio = rin;
     a.Ft = Ft[0];
@@ -1049,29 +1160,18 @@ struct Solver : SolverBase {
       k_xrow<T><<<(a.G * N + RX - 1) / RX, bdX, smX, st>>>(a);
     }
     LAUNCH_CHECK();
-    const size_t n = 3 * (size_t)N * N * N;
-    std::vector<T> h(n);
-    CUDA_TRY(cudaMemcpyAsync(h.data(), rout, n * sizeof(T), cudaMemcpyDeviceToHost, st));
+    to_host(rout, u, 3 * (size_t)N * N * N);
     sync_check();
-    for (size_t i = 0; i < n; ++i) u[i] = (double)h[i];
   }
 
+  // spectral [3][N][N][M] complex <-> host re_im[...][2] (the same layout as reals)
   void download(const cpx<T>* src, double* out) {
-    const size_t n = 3 * F1;
-    std::vector<cpx<T>> h(n);
-    CUDA_TRY(cudaMemcpyAsync(h.data(), src, n * sizeof(cpx<T>), cudaMemcpyDeviceToHost, st));
+    to_host(reinterpret_cast<const T*>(src), out, 2 * 3 * F1);
     sync_check();
-    for (size_t i = 0; i < n; ++i) {
-      out[2 * i] = (double)h[i].x;
-      out[2 * i + 1] = (double)h[i].y;
-    }
   }
 
   void upload(const double* in, cpx<T>* dst) {
-    const size_t n = 3 * F1;
-    std::vector<cpx<T>> h(n);
-    for (size_t i = 0; i < n; ++i) h[i] = mk<T>((T)in[2 * i], (T)in[2 * i + 1]);
-    CUDA_TRY(cudaMemcpyAsync(dst, h.data(), n * sizeof(cpx<T>), cudaMemcpyHostToDevice, st));
+    to_device(in, reinterpret_cast<T*>(dst), 2 * 3 * F1);
     CUDA_TRY(cudaStreamSynchronize(st));
   }
 
@@ -1610,6 +1710,19 @@ int ns_step_cfl(ns_ctx* c, double cfl, double dt_max, int nsteps) {
       return fail(c, NS_ERR_INVALID_ARG, "need cfl > 0, dt_max > 0, nsteps >= 0");
     if (nsteps == 0) return (int)NS_OK;
     c->solver->step_cfl(cfl, dt_max, nsteps);
+    return (int)NS_OK;
+  });
+}
+
+int ns_step_diag(ns_ctx* c, double dt, int nsteps, double* E_out, double* eps_out) {
+  return guarded(c, [&]() {
+    if (!c->have_state) return fail(c, NS_ERR_STATE, "no velocity or state set");
+    if (!(dt > 0.0) || !std::isfinite(dt) || nsteps < 0) return fail(c, NS_ERR_INVALID_ARG, "need dt > 0, nsteps >= 0");
+    if (nsteps > 0 && (!E_out || !eps_out)) return fail(c, NS_ERR_INVALID_ARG, "E_out / eps_out is NULL");
+    if (nsteps == 0) return (int)NS_OK;
+    c->solver->step_diag(dt, nsteps, E_out, eps_out);
+    if (!std::isfinite(E_out[nsteps - 1]) || !std::isfinite(eps_out[nsteps - 1]))
+      return fail(c, NS_ERR_NONFINITE, "energy is not finite");
     return (int)NS_OK;
   });
 }

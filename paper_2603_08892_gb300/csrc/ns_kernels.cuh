@@ -115,6 +115,7 @@ struct PencilArgs {
   const cpx<T>* osh[2];  // shift tables of the outputs
   cpx<T>* out[2];        // [5][N][N][M]
   int* err;
+  double* epart;         // [tiles][2]: sums of w |S|^2 and w k^2 |S|^2 of the written state, or null
 };
 
 template <typename T>
@@ -686,7 +687,9 @@ __global__ void __launch_bounds__(256) k_energy(const cpx<T>* __restrict__ S, in
   }
 }
 
-static __global__ void k_sum_pairs(const double* partial, int nblk, double* out) {
+// out = (f0 * sum_i partial[2i], f1 * sum_i partial[2i+1]) in a fixed order (one block)
+static __global__ void k_sum_pairs(const double* partial, int nblk, double* out, double f0 = 1.0,
+                                   double f1 = 1.0) {
   __shared__ double s0[256], s1[256];
   double a = 0, b = 0;
   for (int i = threadIdx.x; i < nblk; i += blockDim.x) {
@@ -704,8 +707,8 @@ static __global__ void k_sum_pairs(const double* partial, int nblk, double* out)
     __syncthreads();
   }
   if (threadIdx.x == 0) {
-    out[0] = s0[0];
-    out[1] = s1[0];
+    out[0] = f0 * s0[0];
+    out[1] = f1 * s1[0];
   }
 }
 

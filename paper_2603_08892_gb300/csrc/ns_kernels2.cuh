@@ -364,13 +364,49 @@ struct DeshiftOut {
   }
 };
 
+// Energy and dissipation sums of the state a final-stage pencil tile writes (Sec. 3.4: E =
+// 1/2 sum w |S|^2, eps = nu sum w k^2 |S|^2, w = 1 at kx = 0 and 2 elsewhere): each thread's
+// sums (in T, a few modes each) are reduced across the block in FP64 and stored as the
+// tile's pair; a fixed-order sum over the tiles follows.  Every thread of the block calls it.
+template <typename T>
+__device__ __forceinline__ void tile_energy_store(double* epart, T e, T d) {
+  __shared__ double red[2][32];
+  double a = (double)e, b = (double)d;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_down_sync(0xffffffffu, a, o);
+    b += __shfl_down_sync(0xffffffffu, b, o);
+  }
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) {
+    red[0][w] = a;
+    red[1][w] = b;
+  }
+  __syncthreads();
+  if (w == 0) {
+    const int nw = (int)(blockDim.x + 31) >> 5;
+    a = l < nw ? red[0][l] : 0.0;
+    b = l < nw ? red[1][l] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      a += __shfl_down_sync(0xffffffffu, a, o);
+      b += __shfl_down_sync(0xffffffffu, b, o);
+    }
+    if (l == 0) {
+      epart[2 * blockIdx.x] = a;
+      epart[2 * blockIdx.x + 1] = b;
+    }
+  }
+}
+
 // Spectral stage of a pencil tile with one input: the three components of F are staged,
 // transformed in place (the last stage de-shifting and weighting), then one pass per mode
 // applies N(0) = 0, truncation, projection and forcing and the RK stage combine of all three
 // components, leaving S_next (shifted for the output when there is one output) in the tiles.
-template <typename T, int N, class MP>
+template <typename T, int N, class MP, bool EP>
 __device__ __forceinline__ void pencil_spectral_one(const PencilArgs<T>& a, cpx<T>* buf, cpx<T>* tws,
-                                                    int iy, int x0, int nOut, bool tz) {
+                                                    int iy, int x0, int nOut, bool tz, T& eacc,
+                                                    T& dacc) {
   using C = K2Cfg<T, N>;
   constexpr int M = N / 2, TX = C::TX, NT = C::NTP, tile = lf_rows<T, C::TX>(N) * TX;
   constexpr int PER = (tile + NT - 1) / NT;
@@ -456,13 +492,20 @@ __device__ __forceinline__ void pencil_spectral_one(const PencilArgs<T>& a, cpx<
         }
         cpx<T> shz = oxy;
         if (pre) shz = oxy * MP::ld(&a.osh[0][2 * N + iz]);
+        T m2 = 0;  // |S|^2 of the written state (EP: final stages with a.epart)
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
           const cpx<T> s1 = rd1 ? MP::ldw(&a.acc[c * fstride + g]) : mk<T>(0, 0);
           cpx<T> sn = stage_combine<T, MP>(a, c, c * fstride + g, nv[c], s0[c][j], s1, E1, Eh);
           shell_record<T, MP>(a, c, kx, ky, kz, sn);
+          if constexpr (EP) m2 += sn.x * sn.x + sn.y * sn.y;
           if (pre) sn = sn * shz;
           buf[c * tile + e] = sn;
+        }
+        if constexpr (EP) {
+          const T wm = (kx == 0 ? T(1) : T(2)) * m2;
+          eacc += wm;
+          dacc += wm * (T)(kx * kx + ky * ky + kz * kz);
         }
       }
     }
@@ -473,7 +516,7 @@ __device__ __forceinline__ void pencil_spectral_one(const PencilArgs<T>& a, cpx<
 // NFC, NOC: the number of inputs and outputs known at compile time (-1: read from the
 // arguments).  (1, 1) is every RK2, Rogallo and RK4 stage, (2, 2) the exact scheme's stage;
 // fixing them keeps those kernels free of register spills.
-template <typename T, int N, class MP, int NFC = -1, int NOC = -1>
+template <typename T, int N, class MP, int NFC = -1, int NOC = -1, bool EP = false>
 __device__ __forceinline__ void pencil_tile(const PencilArgs<T>& a, int tile_id, cpx<T>* buf) {
   using C = K2Cfg<T, N>;
   const int nF = NFC >= 0 ? NFC : a.nF, nOut = NOC >= 0 ? NOC : a.nOut;
@@ -497,8 +540,9 @@ __device__ __forceinline__ void pencil_tile(const PencilArgs<T>& a, int tile_id,
   const bool pre = nOut == 1 && a.osh[0] != nullptr;  // S_next is shifted in the tiles
   const bool tt = pencil_tile_truncated<T, TX>(a, x0, ky);  // N = 0 on the whole tile
   const bool tz = nF > 0 && tt;                               // so its inputs are not transformed
+  T eacc = 0, dacc = 0;  // energy sums of the written state (a.epart)
   if constexpr (NFC == 1) {
-    pencil_spectral_one<T, N, MP>(a, buf, tws, iy, x0, nOut, tz);
+    pencil_spectral_one<T, N, MP, EP>(a, buf, tws, iy, x0, nOut, tz, eacc, dacc);
   } else {
     const int nFe = tz ? 0 : nF;  // inputs that are transformed
     // 1) inputs: all three components staged asynchronously, then transformed in place
@@ -595,6 +639,12 @@ __device__ __forceinline__ void pencil_tile(const PencilArgs<T>& a, int tile_id,
           const cpx<T> n = nFe > 0 ? bc(c)[e] : mk<T>(0, 0);
           cpx<T> sn = stage_combine<T, MP>(a, c, g, n, s0[j], s1[j], E1, Eh);
           shell_record<T, MP>(a, c, kx, ky, kof(iz, N), sn);
+          if (a.epart) {
+            const int kz = kof(iz, N);
+            const T wm = (kx == 0 ? T(1) : T(2)) * (sn.x * sn.x + sn.y * sn.y);
+            eacc += wm;
+            dacc += wm * (T)(kx * kx + ky * ky + kz * kz);
+          }
           if (pre) sn = sn * (oxy * MP::ld(&a.osh[0][2 * N + iz]));
           bc(c)[e] = sn;
         }
@@ -603,6 +653,12 @@ __device__ __forceinline__ void pencil_tile(const PencilArgs<T>& a, int tile_id,
     __syncthreads();
   }
 
+  // one-input tiles take the sums only in the EP variant; the others whenever a.epart is set
+  if constexpr (NFC == 1) {
+    if constexpr (EP) tile_energy_store<T>(a.epart, eacc, dacc);
+  } else if (a.epart) {
+    tile_energy_store<T>(a.epart, eacc, dacc);
+  }
   if (tt) {  // S_next vanishing on the whole tile (a truncated state): zero outputs, no transforms
     bool nz = false;
     if (act)
@@ -647,13 +703,14 @@ __device__ __forceinline__ void pencil_tile(const PencilArgs<T>& a, int tile_id,
 
 // the two-input variant holds 4 shared tiles (3 blocks per SM at most): it is given the
 // registers of 2 resident blocks rather than spill
-template <typename T, int N, int NFC, int NOC>
+// EP: the one-input variant that also stores the tile's energy sums (a.epart non-null)
+template <typename T, int N, int NFC, int NOC, bool EP = false>
 __global__ void __launch_bounds__(K2Cfg<T, N>::NTP, (NFC == 2 || (NFC == 1 && NS_PENCIL_STAGE_STATE))
                                                          ? cmin(2, K2Cfg<T, N>::MINB_P)
                                                          : K2Cfg<T, N>::MINB_P)
     k2_pencil(PencilArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  pencil_tile<T, N, MemNC, NFC, NOC>(a, blockIdx.x, reinterpret_cast<cpx<T>*>(smem_raw));
+  pencil_tile<T, N, MemNC, NFC, NOC, EP>(a, blockIdx.x, reinterpret_cast<cpx<T>*>(smem_raw));
 }
 
 // ---- slab pass: y transforms --------------------------------------------------------
@@ -1004,6 +1061,7 @@ struct K2Entry {
   int N = 0;
   void (*pencil)(PencilArgs<T>) = nullptr;   // any number of inputs / outputs
   void (*pencil1)(PencilArgs<T>) = nullptr;  // one input, one output
+  void (*pencil1e)(PencilArgs<T>) = nullptr; // same, also storing the tile's energy sums
   void (*pencil2)(PencilArgs<T>) = nullptr;  // two inputs, two outputs
   void (*yinv)(SlabArgs<T>) = nullptr;
   void (*yfwd)(SlabArgs<T>) = nullptr;
@@ -1026,6 +1084,7 @@ K2Entry<T> make_k2_entry() {
 #endif
   // NS_PENCIL_VARIANTS=0 routes every pencil pass through the generic kernel (comparisons)
   e.pencil1 = NS_PENCIL_VARIANTS ? k2_pencil<T, N, 1, 1> : e.pencil;
+  e.pencil1e = NS_PENCIL_VARIANTS ? k2_pencil<T, N, 1, 1, true> : e.pencil;
   e.pencil2 = NS_PENCIL_VARIANTS ? k2_pencil<T, N, 2, 2> : e.pencil;
   e.yinv = k2_yinv<T, N>;
   e.yfwd = k2_yfwd<T, N>;
