@@ -81,7 +81,7 @@ struct BCfg {
     const size_t tw = (size_t)tw_elems(N);
     const size_t p = (3 * (size_t)lf_rows<T, C::TX>(N) * C::TX + tw) * cs;
     const size_t yi = (4 * (size_t)lf_rows<T, C::TYI>(N) * C::TYI + tw) * cs;  // 3 input slots + work
-    const size_t yf = ((size_t)lf_rows<T, C::TY>(N) * C::TY + tw) * cs, x = (2 * (size_t)C::XBUF + tw) * cs;
+    const size_t yf = ((size_t)lf_rows<T, C::TY>(N) * C::TY + tw) * cs, x = ((size_t)C::XELEMS + tw) * cs;
     const size_t a = p > yi ? p : yi, b = yf > x ? yf : x;
     return a > b ? a : b;
   }

@@ -178,8 +178,10 @@ struct K2Cfg {
 #endif
   static constexpr int RX = NS_XR_ROWS > 0 ? NS_XR_ROWS : cmin(cmax(8192 / (M * CS), 1), 16);
   static constexpr int NTX = round_warps(3 * RX * M / RXR);
-  static constexpr int XLS = WorkTile<T, M, 3 * RX, false>::LS;
-  static constexpr int XBUF = 3 * RX * XLS;  // elements of one 3-field row buffer
+  // elements of the x-row tile: 3 RX complex lines of length N (two real rows per line), and
+  // the blocks per SM its shared memory allows (the register budget is held to that many)
+  static constexpr int XELEMS = WorkTile<T, N, 3 * RX, false>::elems();
+  static constexpr int MINB_X = cmax(1, cmin(8, (227 * 1024) / ((XELEMS + tw_elems(N)) * CS + 1024)));
   static __host__ __device__ constexpr int pencil_tiles(int nF) { return nF > 1 ? 5 : 4; }
 };
 
@@ -823,39 +825,43 @@ __global__ void __launch_bounds__(K2Cfg<T, N>::NTY, 2) k2_yfwd(SlabArgs<T> a) {
 }
 
 // ---- slab pass: x rows --------------------------------------------------------------
-// One tile: RX consecutive rows (plane, y) of the group.
+// One tile: RX consecutive rows (plane, y) of the group.  Each row holds the half spectra
+// (kx < N/2, the Nyquist mode zero) of 6 real fields, and two real rows share one complex line
+// of length N: the line of fields a and b is z = a + i b, whose full spectrum is
+// Z[k] = A[k] + i B[k] and Z[N - k] = conj(A[k]) + i conj(B[k]) (A[0], B[0] real).  Inverse
+// lines per row: (u_x, u_y), (u_z, w_x), (w_y, w_z); the products come back as lines (f_0, f_1)
+// of every row and (f_2 of row q, f_2 of row q + RXh), whose forward transforms P split into
+// F_a[k] = (P[k] + conj(P[N - k])) / 2 and F_b[k] = (P[k] - conj(P[N - k])) / (2 i).  All
+// transforms are unnormalised, as the r2c / c2r pair they replace.
 template <typename T, int N, class MP>
 __device__ __forceinline__ void xrow_tile(const SlabArgs<T>& a, int tile_id, cpx<T>* buf) {
   using C = K2Cfg<T, N>;
-  constexpr int M = N / 2, RX = C::RX, NT = C::NTX;
-  using RowT = WorkTile<T, M, 3 * RX, false>;
-  const RowT U{buf}, V{buf + C::XBUF};
-  cpx<T>* tws = buf + 2 * C::XBUF;
+  constexpr int M = N / 2, RX = C::RX, NT = C::NTX, RXh = (RX + 1) / 2;
+  constexpr int NLI = 3 * RX, NLF = RX + RXh;  // inverse and forward lines
+  const WorkTile<T, N, NLI, false> L{buf};     // line p RX + r: pair p of row r
+  cpx<T>* tws = buf + C::XELEMS;
   const bool act = threadIdx.x < NT;
   for (int i = threadIdx.x; i < N; i += blockDim.x) tws[tw_pad(i)] = ldg(&a.tw[i]);
-  __syncthreads();  // the pre-processing below reads twiddles written by other threads
   const int rows_total = a.G * N;
   const int r0 = tile_id * RX;
   const int nr = min(RX, rows_total - r0);
   const size_t sstride = (size_t)a.G * N * M;
 
-  // load the 6 fields with the c2r pre-processing (Hermitian half row -> packed Z'): item
-  // (f, row, k) handles k = 0 with M/2, or the pair (k, M - k); each thread issues all of its
-  // loads before any arithmetic.  Rows past the end of the group are zero-filled.
-  static_assert(M % 2 == 0, "x rows of even length");
-  constexpr int H = M / 2;
-  constexpr int NI = 6 * RX * H, KI = (NI + NT - 1) / NT;
+  // 1) item (p, row, k) reads mode k of fields 2p and 2p + 1 and writes Z[k] and Z[N - k] of
+  //    line p RX + row (k = 0: Z[0] from the real parts and Z[M] = 0).  Every load is issued
+  //    before any store; rows past the end of the group are zero.
+  constexpr int NI = 3 * RX * M, KI = (NI + NT - 1) / NT;
   cpx<T> xa[KI], xb[KI];
 #pragma unroll
   for (int c = 0; c < KI; ++c) {
     const int i = threadIdx.x + c * NT;
     xa[c] = xb[c] = mk<T>(0, 0);
     if (act && (NI % NT == 0 || i < NI)) {
-      const int f = i / (RX * H), row = (i / H) % RX, k = i % H;
+      const int p = i / (RX * M), row = (i / M) % RX, k = i % M;
       if (row < nr) {
-        const cpx<T>* src = a.scr + f * sstride + (size_t)(r0 + row) * M;
-        xa[c] = MP::ld(&src[k]);
-        xb[c] = MP::ld(&src[k == 0 ? H : M - k]);
+        const cpx<T>* src = a.scr + 2 * p * sstride + (size_t)(r0 + row) * M + k;
+        xa[c] = MP::ld(src);
+        xb[c] = MP::ld(src + sstride);
       }
     }
   }
@@ -863,77 +869,69 @@ __device__ __forceinline__ void xrow_tile(const SlabArgs<T>& a, int tile_id, cpx
   for (int c = 0; c < KI; ++c) {
     const int i = threadIdx.x + c * NT;
     if (act && (NI % NT == 0 || i < NI)) {
-      const int f = i / (RX * H), row = (i / H) % RX, k = i % H;
-      const int line = f * RX + row;
-      const WorkTile<T, M, 6 * RX, false> B{buf};  // U then V: field f, row r is line f RX + r
+      const int p = i / (RX * M), row = (i / M) % RX, k = i % M;
+      const int line = p * RX + row;
+      const cpx<T> A = xa[c], B = xb[c];
       if (k == 0) {
-        B.put(line, 0, mk<T>(xa[c].x, xa[c].x));
-        B.put(line, H, (xb[c] + conjg(xb[c])) - (xb[c] - conjg(xb[c])));
+        L.put(line, 0, mk<T>(A.x, B.x));
+        L.put(line, M, mk<T>(0, 0));
       } else {
-        const cpx<T> Xk = xa[c], Xm = xb[c];
-        const cpx<T> tk = tws[tw_pad(k)];
-        const cpx<T> A = Xk + conjg(Xm), Bv = Xk - conjg(Xm);
-        B.put(line, k, A + mul_si(conjg(tk) * Bv, T(1)));
-        const cpx<T> A2 = Xm + conjg(Xk), B2 = Xm - conjg(Xk);
-        B.put(line, M - k, A2 - mul_si(tk * B2, T(1)));
+        L.put(line, k, mk<T>(A.x - B.y, A.y + B.x));      // A + i B
+        L.put(line, N - k, mk<T>(A.x + B.y, B.x - A.y));  // conj(A) + i conj(B)
       }
     }
   }
   __syncthreads();
-  // the six inverse transforms in one in-place call (lines 0 .. 6 RX - 1)
-  cfft_ip<T, M, 2, 6 * RX, NT, false, 1, true, C::RXR>(WorkTile<T, M, 6 * RX, false>{buf}, buf, tws);
+  // 2) the 3 RX inverse transforms in one in-place call
+  cfft_ip<T, N, 1, NLI, NT, false, 1, true, C::RXR>(L, buf, tws);
   __syncthreads();
 
-  // u x omega on the packed real rows, written over u
+  // 3) u x omega: item (q, x) takes rows q and q + RXh (when RX is odd the last q has one) at
+  //    point x, writes (f_0, f_1) over each row's first line and (f_2(q), f_2(q + RXh)) over
+  //    line RX + q (row q's second line): every line it writes is one it has read
   T m[3] = {T(0), T(0), T(0)};  // max |u_i| over the rows (CFL), padding rows are zero
-  for (int i = threadIdx.x; act && i < RX * M; i += NT) {
-    const int row = i / M, k = i % M;
-    cpx<T> u[3], w[3];
+  for (int i = threadIdx.x; act && i < RXh * N; i += NT) {
+    const int q = i / N, x = i % N;
+    T f2[2] = {T(0), T(0)};
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      u[c] = U.get(c * RX + row, k);
-      w[c] = V.get(c * RX + row, k);
-      m[c] = fmax(m[c], fmax(fabs(u[c].x), fabs(u[c].y)));
+    for (int h = 0; h < 2; ++h) {
+      const int row = q + h * RXh;
+      if (row < RX) {
+        const cpx<T> z0 = L.get(row, x), z1 = L.get(RX + row, x), z2 = L.get(2 * RX + row, x);
+        const T ux = z0.x, uy = z0.y, uz = z1.x, wx = z1.y, wy = z2.x, wz = z2.y;
+        m[0] = fmax(m[0], fabs(ux));
+        m[1] = fmax(m[1], fabs(uy));
+        m[2] = fmax(m[2], fabs(uz));
+        L.put(row, x, mk<T>(uy * wz - uz * wy, uz * wx - ux * wz));
+        f2[h] = ux * wy - uy * wx;
+      }
     }
-    // real parts are x_{2k}, imaginary parts x_{2k+1}
-    const cpx<T> f0 = mk<T>(u[1].x * w[2].x - u[2].x * w[1].x, u[1].y * w[2].y - u[2].y * w[1].y);
-    const cpx<T> f1 = mk<T>(u[2].x * w[0].x - u[0].x * w[2].x, u[2].y * w[0].y - u[0].y * w[2].y);
-    const cpx<T> f2 = mk<T>(u[0].x * w[1].x - u[1].x * w[0].x, u[0].y * w[1].y - u[1].y * w[0].y);
-    U.put(row, k, f0);
-    U.put(RX + row, k, f1);
-    U.put(2 * RX + row, k, f2);
+    L.put(RX + q, x, mk<T>(f2[0], f2[1]));
   }
   __syncthreads();
-  if (a.umax) block_max3<T>(m[0], m[1], m[2], reinterpret_cast<T*>(V.p), a.umax);  // V is free
-  cfft_ip<T, M, 2, 3 * RX, NT, false, -1, true, C::RXR>(U, U.p, tws);
+  // lines NLF .. 3 RX - 1 are free now
+  if (a.umax) block_max3<T>(m[0], m[1], m[2], reinterpret_cast<T*>(buf + NLF * L.LS), a.umax);
+  // 4) the NLF forward transforms of the products
+  cfft_ip<T, N, 1, NLF, NT, false, -1, true, C::RXR>(WorkTile<T, N, NLF, false>{buf}, buf, tws);
   __syncthreads();
 
-  // r2c post-processing and store: item (f, row, k) writes k = 0 with M/2, or the pair
-  // (k, M - k)
-  constexpr int NO = 3 * RX * H;
+  // 5) split and store: item (line, k), k < M
+  constexpr int NO = NLF * M;
   for (int i = threadIdx.x; act && i < NO; i += NT) {
-    const int f = i / (RX * H), row = (i / H) % RX, k = i % H;
-    if (row >= nr) continue;
-    const int line = f * RX + row;
-    cpx<T>* dst = a.scr + f * sstride + (size_t)(r0 + row) * M;
-    if (k == 0) {
-      const cpx<T> Z = U.get(line, 0);
-      MP::st(&dst[0], mk<T>(Z.x + Z.y, T(0)));
-      const cpx<T> Zk = U.get(line, H);
-      MP::st(&dst[H], T(0.5) * ((Zk + conjg(Zk)) - (Zk - conjg(Zk))));
-    } else {
-      const cpx<T> Zk = U.get(line, k), Zm = U.get(line, M - k);
-      const cpx<T> Wk = tws[tw_pad(k)];
-      const cpx<T> A = Zk + conjg(Zm), B = Zk - conjg(Zm);
-      MP::st(&dst[k], T(0.5) * (A - mul_si(Wk * B, T(1))));
-      const cpx<T> A2 = Zm + conjg(Zk), B2 = Zm - conjg(Zk);
-      MP::st(&dst[M - k], T(0.5) * (A2 + mul_si(conjg(Wk) * B2, T(1))));
-    }
+    const int line = i / M, k = i % M;
+    const cpx<T> P = L.get(line, k), Q = L.get(line, k == 0 ? 0 : N - k);
+    const cpx<T> Fa = mk<T>(T(0.5) * (P.x + Q.x), T(0.5) * (P.y - Q.y));
+    const cpx<T> Fb = mk<T>(T(0.5) * (P.y + Q.y), T(0.5) * (Q.x - P.x));
+    const bool own = line < RX;  // (f_0, f_1) of row `line`, else f_2 of rows q, q + RXh
+    const int ra = own ? line : line - RX, rb = own ? line : line - RX + RXh;
+    const int fa = own ? 0 : 2, fb = own ? 1 : 2;
+    if (ra < nr) MP::st(&a.scr[fa * sstride + (size_t)(r0 + ra) * M + k], Fa);
+    if (rb < nr) MP::st(&a.scr[fb * sstride + (size_t)(r0 + rb) * M + k], Fb);
   }
 }
 
 template <typename T, int N>
-__global__ void __launch_bounds__(K2Cfg<T, N>::NTX) k2_xrow(SlabArgs<T> a) {
+__global__ void __launch_bounds__(K2Cfg<T, N>::NTX, K2Cfg<T, N>::MINB_X) k2_xrow(SlabArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   xrow_tile<T, N, MemNC>(a, blockIdx.x, reinterpret_cast<cpx<T>*>(smem_raw));
 }
@@ -972,7 +970,7 @@ struct PipeCfg {
   static constexpr int NT = cmax(cmax(NTYP, C::NTX), C::NTY);
   static constexpr bool ok = N % C::RX == 0 && M % TYP == 0 && TYP % C::MINW == 0;
   static constexpr size_t smem = sizeof(cpx<T>) *
-      cmax(cmax(4 * lf_rows<T, TYP>(N) * TYP, lf_rows<T, C::TY>(N) * C::TY), 2 * C::XBUF) +
+      cmax(cmax(4 * lf_rows<T, TYP>(N) * TYP, lf_rows<T, C::TY>(N) * C::TY), C::XELEMS) +
       sizeof(cpx<T>) * tw_elems(N);
 };
 
@@ -1101,7 +1099,7 @@ K2Entry<T> make_k2_entry() {
   e.smP1 = NS_PENCIL_STAGE_STATE ? (6 * (size_t)lf_rows<T, C::TX>(N) * C::TX + tw_elems(N)) * sizeof(cpx<T>) : e.smP4;
   e.smP5 = (4 * (size_t)lf_rows<T, C::TX>(N) * C::TX + tw_elems(N)) * sizeof(cpx<T>);  // 4 tiles + twiddles
   e.smY = ((size_t)lf_rows<T, C::TY>(N) * C::TY + tw_elems(N)) * sizeof(cpx<T>);
-  e.smX = (2 * (size_t)C::XBUF + tw_elems(N)) * sizeof(cpx<T>);
+  e.smX = ((size_t)C::XELEMS + tw_elems(N)) * sizeof(cpx<T>);
   return e;
 }
 
