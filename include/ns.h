@@ -270,6 +270,19 @@ int ns_nonlinear_noalloc(const void* state, void* out, int N, double kmax, int t
  * one pencil pass per evaluation), for roofline reporting. */
 double ns_model_bytes_per_step(ns_ctx* ctx);
 
+/* The one-dimensional quadratic model of Sec. 3.3 (Eq. model-1d, the "nl1d" example of where
+ * the aliases of a quadratic term land): dS/dt = -sign(S) S^2 on [0, 2 pi), pseudo-spectral on
+ * N points (even, 4 <= N <= 2048; N need not be 2^a 3^b) with the truncation k < kmax
+ * (0 < kmax <= N/2, Sec. 3.2) applied to the initial field and to every nonlinear term, and
+ * the RK2 of Sec. 4.1 without viscosity (S_half = S + dt/2 N(S), S_new = S + dt N(S_half)),
+ * N(S) = T FFT[-sign(S) S^2] with the product taken on the grid.  nbatch independent fields:
+ * s0 host [nbatch][N] physical initial values; out host [nbatch][N/2 + 1][2] the half spectra
+ * S(k) = (1/N) sum_j S(x_j) e^{-i k x_j} after nsteps steps (nsteps = 0: the truncated initial
+ * spectra).  FP64, one block per field on the current device; synchronous; allocates and
+ * frees its own device buffers.  NS_ERR_INVALID_ARG for sizes or pointers outside these
+ * ranges, NS_ERR_OOM / NS_ERR_CUDA on a CUDA failure. */
+int ns_nl1d(int N, double kmax, double dt, int nsteps, int nbatch, const double* s0, double* out);
+
 /* Measured CUDA-core FMA throughput of `device` in flop/s (2 flops per FMA) for precision
  * NS_FP32 or NS_FP64: one timed launch of independent FMA chains filling every SM (a few ms
  * in FP32, tens of ms in FP64).  It is the peak of the secondary, arithmetic roofline of the

@@ -77,6 +77,8 @@ _device_state = _sig("ns_device_state", ctypes.c_int,
                      [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(ctypes.c_int)])
 _model_bytes = _sig("ns_model_bytes_per_step", ctypes.c_double, [_vp])
 _fma_peak = _sig("ns_fma_peak", ctypes.c_int, [ctypes.c_int, ctypes.c_int, _dp])
+_nl1d = _sig("ns_nl1d", ctypes.c_int, [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                         ctypes.c_int, _dp, _dp])
 _profile = _sig("ns_profile", ctypes.c_int, [_vp, ctypes.c_int])
 _profile_read = _sig("ns_profile_read", ctypes.c_int,
                      [_vp, ctypes.c_int, _dp, ctypes.POINTER(ctypes.c_int64),
@@ -106,7 +108,7 @@ EXPORTED = ["ns_init", "ns_init_ex", "ns_init_error", "ns_destroy", "ns_last_err
             "ns_set_forcing", "ns_step", "ns_step_cfl", "ns_step_diag", "ns_set_shifts",
             "ns_checkpoint_save", "ns_checkpoint_load", "ns_nonlinear", "ns_energy",
             "ns_energy_spectrum", "ns_energy_flux", "ns_time", "ns_set_time", "ns_device_state",
-            "ns_model_bytes_per_step", "ns_fma_peak", "ns_profile", "ns_profile_read", "ns_nonlinear_noalloc", "ns_vjp", "ns_batch_init", "ns_batch_destroy", "ns_batch_last_error",
+            "ns_model_bytes_per_step", "ns_nl1d", "ns_fma_peak", "ns_profile", "ns_profile_read", "ns_nonlinear_noalloc", "ns_vjp", "ns_batch_init", "ns_batch_destroy", "ns_batch_last_error",
             "ns_batch_member", "ns_batch_set_velocity", "ns_batch_get_state", "ns_batch_step",
             "ns_batch_energy", "ns_batch_set_spin_limit", "ns_batch_test_stall", "ns_batch_grid"]
 
@@ -286,6 +288,22 @@ class Solver:
             self._check(_profile_read(self._h, k, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(nl)))
             out[name] = (ms.value, n.value, nl.value)
         return out
+
+
+def nl1d(s0, kmax, dt, nsteps):
+    """The 1D quadratic model of Sec. 3.3 (ns_nl1d): s0 [nbatch][N] (or [N]) physical initial
+    fields; returns the complex half spectra [nbatch][N/2 + 1] (or [N/2 + 1]) after nsteps RK2
+    steps."""
+    s = np.ascontiguousarray(s0, dtype=np.float64)
+    one = s.ndim == 1
+    s = s.reshape(1, -1) if one else s
+    nb, N = s.shape
+    out = np.zeros((nb, N // 2 + 1, 2))
+    rc = _nl1d(N, float(kmax), float(dt), int(nsteps), nb, _ptr(s), _ptr(out))
+    if rc != NS_OK:
+        raise NSError(rc, "ns_nl1d failed")
+    z = out[..., 0] + 1j * out[..., 1]
+    return z[0] if one else z
 
 
 def fma_peak(precision=None, device=0):
