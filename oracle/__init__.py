@@ -32,5 +32,7 @@ Modules:
 * :mod:`oracle.diagnostics` energy, dissipation, spectra, spectral error index (pinned);
 * :mod:`oracle.rng`         splitmix64 counter generator and the random shifts (pinned);
 * :mod:`oracle.adjoint`     transposed (adjoint) step for gradients (pinned by
-  dot-product and finite-difference tests).
+  dot-product and finite-difference tests);
+* :mod:`oracle.nl1d`        the 1D quadratic model of Section 3.3 (pinned by its closed-form
+  first evaluation, the Taylor expansion of one step and the exact solution).
 """
