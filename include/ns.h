@@ -87,7 +87,10 @@ const char* ns_last_error(ns_ctx* ctx);
 
 /* Physical velocity u (host, [3][N][N][N]) -> state: forward FFT, truncation T, Leray
  * projection P, mean mode zeroed (Sec. 3.2; Sec. 4.1 below Eq. base-eq).  A
- * non-solenoidal input is projected.  Resets time and step counter to 0. */
+ * non-solenoidal input is projected.  Resets time and step counter to 0.  Host arrays of
+ * this and the following transfer calls are FP64; FP32 contexts copy them as they are and
+ * round on the device (to nearest, as a host cast does), so a page-locked host buffer
+ * transfers fastest. */
 int ns_set_velocity(ns_ctx* ctx, const double* u);
 /* State -> physical velocity u_out (host, [3][N][N][N]).  This call, ns_get_state, ns_step,
  * ns_step_cfl, ns_step_diag, ns_energy, ns_energy_spectrum and ns_energy_flux return
@@ -129,8 +132,8 @@ int ns_step_cfl(ns_ctx* ctx, double cfl, double dt_max, int nsteps);
  * are taken by the pencil pass that writes each step's state (per-tile partial sums, then a
  * fixed-order FP64 sum; sizes without the size-specialised kernels run a separate reduction),
  * and each step's pair is written by the device into mapped pinned host memory as it is
- * produced: no host synchronisation per step; the call returns once every step has completed.  The first call
- * allocates the series buffers (for max(nsteps, 4096) steps; a longer call reallocates).  NS_ERR_INVALID_ARG unless dt > 0, nsteps >= 0
+ * produced: no host synchronisation per step; the call returns once every step has
+ * completed.  The first call allocates the series buffers (for max(nsteps, 4096) steps; a longer call reallocates).  NS_ERR_INVALID_ARG unless dt > 0, nsteps >= 0
  * and both outputs are non-NULL (nsteps > 0); NS_ERR_NONFINITE if the last pair is not finite.
  * The values agree with ns_energy after each step to rounding (the summation order differs). */
 int ns_step_diag(ns_ctx* ctx, double dt, int nsteps, double* E_out, double* eps_out);
