@@ -133,9 +133,10 @@ int ns_step_cfl(ns_ctx* ctx, double cfl, double dt_max, int nsteps);
  * fixed-order FP64 sum; sizes without the size-specialised kernels run a separate reduction),
  * and each step's pair is written by the device into mapped pinned host memory as it is
  * produced: no host synchronisation per step; the call returns once every step has
- * completed.  The first call allocates the series buffers (for max(nsteps, 4096) steps; a longer call reallocates).  NS_ERR_INVALID_ARG unless dt > 0, nsteps >= 0
- * and both outputs are non-NULL (nsteps > 0); NS_ERR_NONFINITE if the last pair is not finite.
- * The values agree with ns_energy after each step to rounding (the summation order differs). */
+ * completed.  The first call allocates the series buffers (for max(nsteps, 4096) steps; a
+ * longer call reallocates).  NS_ERR_INVALID_ARG unless dt > 0, nsteps >= 0 and both outputs
+ * are non-NULL (nsteps > 0); NS_ERR_NONFINITE if the last pair is not finite.  The values
+ * agree with ns_energy after each step to rounding (the summation order differs). */
 int ns_step_diag(ns_ctx* ctx, double dt, int nsteps, double* E_out, double* eps_out);
 /* Test hook: delta_alpha for the next nsteps steps (host [nsteps][3], radians), consumed
  * by the following ns_step calls in order; delta_beta = delta_alpha + (pi/N)(1,1,1). */
