@@ -6,7 +6,9 @@ The product path (the CUDA library and its Python binding) never imports, links 
 anything here, and nothing here imports the product path.
 
 The oracle is plain, slow and written to be checked against the paper by eye:
-NumPy in float64, ``numpy.fft`` as the only library primitive, no blocking or fusion.
+NumPy in float64, ``numpy.fft`` as the only library primitive (or ``scipy.fft``, the same
+pocketfft transforms on several threads, see ``spectral.set_fft_workers``), no blocking or
+fusion.
 Every function cites the passage of the paper it follows ("Lambert, Reneuve & Augier,
 Aliasing and phase shifting in pseudo-spectral simulations of the incompressible
 Navier-Stokes equations").

@@ -19,6 +19,34 @@ Paper passages followed:
 import numpy as np
 
 TRUNC_SPHERICAL = 0
+
+# Threads of the 3D transforms.  None: numpy.fft (single thread).  An integer n: scipy.fft
+# with n workers -- the same pocketfft algorithm, split across threads, for the full-size
+# (256^3 and larger) oracle runs of the tests and of the timed CPU baseline.
+_FFT_WORKERS = None
+
+
+def set_fft_workers(n):
+    """Use ``n`` threads for the 3D transforms (None: numpy.fft, one thread); returns the old value."""
+    global _FFT_WORKERS
+    old, _FFT_WORKERS = _FFT_WORKERS, (None if n is None else max(1, int(n)))
+    return old
+
+
+def _rfftn(u):
+    if _FFT_WORKERS is None:
+        return np.fft.rfftn(u, axes=(-3, -2, -1))
+    import scipy.fft
+
+    return scipy.fft.rfftn(u, axes=(-3, -2, -1), workers=_FFT_WORKERS)
+
+
+def _irfftn(full, N):
+    if _FFT_WORKERS is None:
+        return np.fft.irfftn(full, s=(N, N, N), axes=(-3, -2, -1))
+    import scipy.fft
+
+    return scipy.fft.irfftn(full, s=(N, N, N), axes=(-3, -2, -1), workers=_FFT_WORKERS)
 TRUNC_CUBIC = 1
 TRUNC_NO_DOUBLE_ALIAS = 2
 
@@ -55,7 +83,7 @@ def forward(u):
     with the kx = N/2 plane dropped.
     """
     N = u.shape[-1]
-    uh = np.fft.rfftn(u, axes=(-3, -2, -1)) / float(N) ** 3
+    uh = _rfftn(u) / float(N) ** 3
     return uh[..., : N // 2]
 
 
@@ -68,7 +96,7 @@ def inverse(uh):
     N = uh.shape[-2]
     full = np.zeros(uh.shape[:-1] + (N // 2 + 1,), dtype=complex)
     full[..., : N // 2] = uh
-    return np.fft.irfftn(full, s=(N, N, N), axes=(-3, -2, -1)) * float(N) ** 3
+    return _irfftn(full, N) * float(N) ** 3
 
 
 def kmax2_threshold(kmax):
