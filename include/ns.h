@@ -213,7 +213,7 @@ int ns_device_state(ns_ctx* ctx, void** state, void** stream, int* precision);
  * stream and returns, for one kind, the summed event time in ms, the number of timed
  * launches and the number of launches since the reset.  Kinds: */
 enum { NS_PROF_PENCIL = 0, NS_PROF_YINV = 1, NS_PROF_XROW = 2, NS_PROF_YFWD = 3,
-       NS_PROF_SLAB_PASS = 4, NS_PROF_SLAB_PIPE = 5, NS_PROF_KINDS = 6 };
+       NS_PROF_SLAB_PASS = 4, NS_PROF_SLAB_PIPE = 5, NS_PROF_SLAB_CLUSTER = 6, NS_PROF_KINDS = 7 };
 int ns_profile(ns_ctx* ctx, int enable);
 int ns_profile_read(ns_ctx* ctx, int kind, double* total_ms, int64_t* timed, int64_t* launches);
 
@@ -262,7 +262,10 @@ int ns_batch_grid(ns_batch* b);
  * Working memory is one fixed array inside the library (about 15 MB, sized for N = 64 in
  * FP32), held by every GPU that loads the library until the process exits.  The first call
  * on a device looks up that array's device address and sets kernel attributes (make it
- * before any stream capture).  All calls share the array and it keeps the last call's
+ * before any stream capture).  With CUDA's lazy module loading (the default), the library's
+ * device code and this array are placed on the device when first used, which may be this
+ * first call: make it (or load the process with CUDA_MODULE_LOADING=EAGER) before the
+ * caller's allocator reserves the device's memory; later calls use no further memory.  All calls share the array and it keeps the last call's
  * contents, so calls that overlap on the GPU (other threads or streams) race.  The call is
  * stream ordered and synchronises `stream` before returning; it calls no cudaMalloc,
  * cudaFree or other allocating routine.  Returns NS_ERR_CUDA on a CUDA failure and

@@ -101,7 +101,8 @@ _batch_energy = _sig("ns_batch_energy", ctypes.c_int, [_vp, _dp, _dp])
 _batch_spin = _sig("ns_batch_set_spin_limit", ctypes.c_int, [_vp, ctypes.c_longlong])
 _batch_stall = _sig("ns_batch_test_stall", ctypes.c_int, [_vp, ctypes.c_int])
 _batch_grid = _sig("ns_batch_grid", ctypes.c_int, [_vp])
-PROF_KINDS = {"k_pencil": 0, "k_yinv": 1, "k_xrow": 2, "k_yfwd": 3, "slab_pass": 4, "k_slabpipe": 5}
+PROF_KINDS = {"k_pencil": 0, "k_yinv": 1, "k_xrow": 2, "k_yfwd": 3, "slab_pass": 4, "k_slabpipe": 5,
+              "k_slabcl": 6}
 
 EXPORTED = ["ns_init", "ns_init_ex", "ns_init_error", "ns_destroy", "ns_last_error",
             "ns_set_velocity", "ns_get_velocity", "ns_get_state", "ns_set_state",

@@ -97,6 +97,54 @@ int fft_block(int nl, int n) {
 }
 
 // splitmix64 (Steele, Lea & Flood 2014): n-th output of the generator seeded with s
+// Tile shapes and launch sizes of the generic (run-time radix) kernels for a grid of N
+// points, elements of cs bytes; shared by the contexts and the allocation-free entry point.
+struct GenericShapes {
+  int TX, bdP;        // pencil: TX columns, threads
+  size_t smP;         // pencil shared memory (4 tiles)
+  int TY, bdY;        // y passes: TY columns, threads
+  size_t smYi, smYf;  // inverse (6 tiles) / forward (3 tiles) shared memory
+  int RX, bdX;        // x rows: RX rows, threads
+  size_t smX;         // x-row shared memory (6 fields)
+};
+GenericShapes generic_shapes(int N, size_t cs) {
+  const int M = N / 2;
+  const size_t smax = 200 * 1024;
+  GenericShapes g;
+  g.TX = largest_divisor_le(M, 16);
+  while (g.TX > 1 && (4 * N * g.TX * cs > smax || fft_block(g.TX, N) > 512)) g.TX = largest_divisor_le(M, g.TX - 1);
+  g.bdP = fft_block(g.TX, N) < 256 ? 256 : fft_block(g.TX, N);
+  g.smP = 4 * (size_t)N * g.TX * cs;
+  g.TY = largest_divisor_le(M, 16);
+  while (g.TY > 1 && (6 * N * g.TY * cs > smax || fft_block(g.TY, N) > 512)) g.TY = largest_divisor_le(M, g.TY - 1);
+  g.bdY = fft_block(g.TY, N) < 256 ? 256 : fft_block(g.TY, N);
+  g.smYi = 6 * (size_t)N * g.TY * cs;
+  g.smYf = 3 * (size_t)N * g.TY * cs;
+  g.RX = 16;
+  while (g.RX > 1 && (6 * (size_t)g.RX * M * cs > 100 * 1024 || fft_block(g.RX, M) > 512)) g.RX /= 2;
+  g.bdX = fft_block(g.RX, M) < 256 ? 256 : fft_block(g.RX, M);
+  g.smX = 6 * (size_t)g.RX * M * cs;
+  return g;
+}
+// true when every generic kernel's shared memory fits the device's opt-in limit
+bool generic_shapes_fit(const GenericShapes& g, int optin) {
+  return (long long)g.smP <= optin && (long long)g.smYi <= optin && (long long)g.smYf <= optin &&
+         (long long)g.smX <= optin;
+}
+
+// Integer bounds of the strict truncation test (Sec. 3.2: modes with |k| >= kmax zeroed):
+// K2max = the largest integer below kmax^2 (spherical: keep k^2 <= K2max), Kimax = the largest
+// integer below kmax (cubic: keep max|k_i| <= Kimax), both computed in FP64.
+void trunc_bounds(double kmax, int* K2max, int* Kimax) {
+  const double q = kmax * kmax;
+  double m = std::floor(q);
+  if (m == q) m -= 1;
+  *K2max = (int)m;
+  double r = std::floor(kmax);
+  if (r == kmax) r -= 1;
+  *Kimax = (int)r;
+}
+
 uint64_t splitmix64(uint64_t s, uint64_t n) {
   uint64_t z = s + (n + 1) * 0x9E3779B97F4A7C15ull;
   z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
@@ -105,6 +153,27 @@ uint64_t splitmix64(uint64_t s, uint64_t n) {
 }
 double uniform01(uint64_t s, uint64_t n) {
   return (double)(splitmix64(s, n) >> 11) * (1.0 / 9007199254740992.0);
+}
+
+// cuTensorMapEncodeTiled of the driver, looked up through the runtime (no link to libcuda)
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*,
+                                  CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
+                                  CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_tiled() {
+  static EncodeTiledFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+    else
+      cudaGetLastError();
+  });
+  return fn;
 }
 
 bool k2_find(int N, K2Entry<float>* e) {
@@ -192,6 +261,12 @@ struct Solver : SolverBase {
   int pipe_ring = 0, pipe_lag = 0, pipe_grid = 0, pipe_stall = 0;
   long long pipe_spin = 1ll << 26;
   unsigned char* d_pipe = nullptr;  // [3][N] done counters, ticket, abort flag
+  // slab pass in thread-block clusters, the plane kept on chip (k2_slabcl); chosen by the
+  // autotuner where the size has the kernel and the device can hold its clusters
+  bool clus = false;
+  int cl_ncl = -1;                 // clusters of a launch (-1: not yet queried)
+  long long cl_spin = 1ll << 20;   // polls of its bounded TMA wait
+  std::vector<std::pair<const void*, CUtensorMap>> cl_maps;  // TMA maps of the mixed buffers
   cudaStream_t ss[2] = {nullptr, nullptr};
   cudaEvent_t ev_fork = nullptr, ev_join[2] = {nullptr, nullptr};
   void ensure_streams() {
@@ -298,24 +373,10 @@ struct Solver : SolverBase {
     py = pz;
     px = make_plan(M, N);
     const size_t cs = sizeof(cpx<T>);
-    const size_t smax = 200 * 1024;
-    // pencil: 4 tiles of N x TX
-    TX = largest_divisor_le(M, 16);
-    while (TX > 1 && (4 * N * TX * cs > smax || fft_block(TX, N) > 512)) TX = largest_divisor_le(M, TX - 1);
-    bdP = fft_block(TX, N);
-    if (bdP < 256) bdP = 256;
-    smP = 4 * (size_t)N * TX * cs;
-    // y passes: 6 (inverse) or 3 (forward) tiles of N x TY
-    TY = largest_divisor_le(M, 16);
-    while (TY > 1 && (6 * N * TY * cs > smax || fft_block(TY, N) > 512)) TY = largest_divisor_le(M, TY - 1);
-    bdYi = bdYf = fft_block(TY, N) < 256 ? 256 : fft_block(TY, N);
-    smYi = 6 * (size_t)N * TY * cs;
-    smYf = 3 * (size_t)N * TY * cs;
-    // x rows: 6 fields x RX rows of M
-    RX = 16;
-    while (RX > 1 && (6 * (size_t)RX * M * cs > 100 * 1024 || fft_block(RX, M) > 512)) RX /= 2;
-    bdX = fft_block(RX, M) < 256 ? 256 : fft_block(RX, M);
-    smX = 6 * (size_t)RX * M * cs;
+    const GenericShapes gs = generic_shapes(N, cs);
+    TX = gs.TX; bdP = gs.bdP; smP = gs.smP;
+    TY = gs.TY; bdYi = bdYf = gs.bdY; smYi = gs.smYi; smYf = gs.smYf;
+    RX = gs.RX; bdX = gs.bdX; smX = gs.smX;
     // initial plane group: a scratch (6 fields) of 48 MB, small enough for L2
     const size_t plane6 = 6 * (size_t)N * M * cs;
     G = (int)((48ull << 20) / plane6);
@@ -331,7 +392,7 @@ struct Solver : SolverBase {
     // that contexts of different sizes in one process never lower each other's limit.
     int optin = 0;
     CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-    if ((int)smP > optin || (int)smYi > optin || (int)smX > optin)
+    if (!generic_shapes_fit(gs, optin))
       throw NsError{NS_ERR_INTERNAL, "tile shapes exceed the shared memory of the device"};
     CUDA_TRY(cudaFuncSetAttribute(k_pencil<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
     CUDA_TRY(cudaFuncSetAttribute(k_yinv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
@@ -355,6 +416,11 @@ struct Solver : SolverBase {
       allow(k2.yinv, k2.smYI);
       allow(k2.yfwd, k2.smY);
       allow(k2.xrow, k2.smX);
+      if (k2.slabcl) {
+        allow(k2.slabcl, k2.smCL);
+        if (k2.CLS > 8)
+          CUDA_TRY(cudaFuncSetAttribute(k2.slabcl, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+      }
       if (k2.slabpipe)  // (it has a few bytes of static shared memory: its own size, not optin)
         CUDA_TRY(cudaFuncSetAttribute(k2.slabpipe, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k2.smPIPE));
     }
@@ -438,6 +504,8 @@ struct Solver : SolverBase {
       CUDA_TRY(cudaStreamSynchronize(st));
       if (h & PIPE_ERR_TIMEOUT)
         throw NsError{NS_ERR_TIMEOUT, "slab pipeline: a bounded wait gave up (the pass was abandoned)"};
+      if (h & CL_ERR_TIMEOUT)
+        throw NsError{NS_ERR_TIMEOUT, "cluster slab pass: a bounded TMA wait gave up"};
       throw NsError{NS_ERR_INTERNAL, "device-side launch-shape check failed (flag " + std::to_string(h) + ")"};
     }
   }
@@ -451,6 +519,74 @@ struct Solver : SolverBase {
     return a;
   }
 
+  // clusters of CLS CTAs the device holds at once (0: none fit; the pass is not used)
+  int cl_clusters() {
+    if (cl_ncl >= 0) return cl_ncl;
+    cl_ncl = 0;
+    if (!use2 || !k2.slabcl) return 0;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = k2.CLS;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(k2.CLS);
+    cfg.blockDim = dim3(k2.NTCL);
+    cfg.dynamicSmemBytes = k2.smCL;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, k2.slabcl, &cfg) != cudaSuccess) {
+      cudaGetLastError();
+      n = 0;
+    }
+    cl_ncl = n < N ? n : N;
+    return cl_ncl;
+  }
+  // TMA map of a mixed buffer [5][N][N][M]: scalars of T, dims {2M, N, 5N}, box {2KC, N, 1}
+  CUtensorMap cl_map(const cpx<T>* mix) {
+    for (const auto& m : cl_maps)
+      if (m.first == mix) return m.second;
+    EncodeTiledFn enc = encode_tiled();
+    if (!enc) throw NsError{NS_ERR_CUDA, "cuTensorMapEncodeTiled is not available"};
+    CUtensorMap map;
+    const cuuint64_t dims[3] = {(cuuint64_t)2 * M, (cuuint64_t)N, (cuuint64_t)5 * N};
+    const cuuint64_t strides[2] = {(cuuint64_t)M * sizeof(cpx<T>), (cuuint64_t)N * M * sizeof(cpx<T>)};
+    const cuuint32_t box[3] = {(cuuint32_t)(2 * k2.CLKC), (cuuint32_t)N, 1u};
+    const cuuint32_t es[3] = {1u, 1u, 1u};
+    const CUresult r = enc(&map, sizeof(T) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64,
+                           3, const_cast<cpx<T>*>(mix), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                           CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS)
+      throw NsError{NS_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")"};
+    cl_maps.push_back({mix, map});
+    return map;
+  }
+  // the slab pass as one launch of clusters (k2_slabcl): mixed -> Ft, no scratch
+  void slab_cluster(const cpx<T>* mix, cpx<T>* out, void* umax) {
+    const CUtensorMap map = cl_map(mix);
+    ClArgs ca;
+    ca.err = d_err;
+    ca.umax = umax;
+    ca.spin_limit = cl_spin;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = k2.CLS;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(k2.CLS * cl_clusters());
+    cfg.blockDim = dim3(k2.NTCL);
+    cfg.dynamicSmemBytes = k2.smCL;
+    cfg.stream = st;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaEvent_t e = prof_begin(NS_PROF_SLAB_CLUSTER);
+    CUDA_TRY(cudaLaunchKernelEx(&cfg, k2.slabcl, map, out, static_cast<const cpx<T>*>(tw), ca));
+    prof_end(e);
+  }
+
   // slab pass over every plane group: mixed (5 fields) -> Ft (3 fields)
   void slab(const cpx<T>* mix, cpx<T>* out, bool umax = false) {
     SlabArgs<T> a = slab_args();
@@ -462,6 +598,12 @@ struct Solver : SolverBase {
       a.umax = d_umax;
     }
     cudaEvent_t pass = prof_begin(NS_PROF_SLAB_PASS);
+    if (clus && use2 && k2.slabcl && cl_clusters() > 0) {
+      slab_cluster(mix, out, a.umax);
+      prof_end(pass);
+      LAUNCH_CHECK();
+      return;
+    }
     if (pipe && use2 && k2.slabpipe && pipe_ring >= 2 && pipe_ring <= Gmax) {
       const int nb = 3 * N;
       if (!d_pipe) CUDA_TRY(cudaMalloc(&d_pipe, nb * sizeof(int) + 16));
@@ -823,9 +965,11 @@ struct Solver : SolverBase {
   }
 
   // The cached value encodes the mode: 4 G + m, m = 0 one stream, 1 two streams (G planes per
-  // group), 2 the pipeline (G = ring planes, lag G / 4).
+  // group), 2 the pipeline (G = ring planes, lag G / 4), 3 the cluster pass (G unused).
   void set_mode(int g, int m) {
     pipe = m == 2;
+    clus = m == 3;
+    if (clus) return;
     if (pipe) {
       pipe_ring = g;
       pipe_lag = g / 4 > 0 ? g / 4 : 1;
@@ -839,6 +983,14 @@ struct Solver : SolverBase {
     tuned = true;
     if (const char* e = std::getenv("NS_PIPE_SPIN")) pipe_spin = std::max(1ll, std::atoll(e));
     if (const char* e = std::getenv("NS_PIPE_TEST_STALL")) pipe_stall = std::atoi(e) ? 1 : 0;
+    if (const char* e = std::getenv("NS_CL_SPIN")) cl_spin = std::max(1ll, std::atoll(e));
+    const char* fcl = std::getenv("NS_SLAB_CLUSTER");
+    // (opt-in until its parity tests have run on the device)
+    const bool can_cl = use2 && k2.slabcl && fcl && std::string(fcl) == "1" && cl_clusters() > 0;
+    if (fcl && std::string(fcl) == "1" && can_cl) {  // forced cluster pass
+      set_mode(1, 3);
+      return;
+    }
     const char* fpipe = std::getenv("NS_SLAB_PIPE");
     const bool can_pipe = use2 && k2.slabpipe && !(fpipe && std::string(fpipe) == "0");
     if (fpipe && std::string(fpipe) == "1" && can_pipe) {  // forced pipeline
@@ -859,9 +1011,10 @@ struct Solver : SolverBase {
     const char* en = std::getenv("NS_AUTOTUNE");
     if (en && std::string(en) == "0") return;
     if (Gmax <= 1 || N < 128) return;  // small grids: one group holds every plane
-    const std::string path = cache_path(), key = tune_key() + (can_pipe ? "|g4p" : "|g4");
+    const std::string path = cache_path(),
+                      key = tune_key() + (can_pipe ? "|g4p" : "|g4") + (can_cl ? "c" + std::to_string(k2.CLS) : "");
     int g = 0;
-    if (cache_lookup(path, key, &g) && g / 4 >= 1 && g / 4 <= Gmax && (g & 3) <= 2) {
+    if (cache_lookup(path, key, &g) && g / 4 >= 1 && g / 4 <= Gmax && ((g & 3) <= 2 || can_cl)) {
       set_mode(g / 4, g & 3);
       return;
     }
@@ -874,6 +1027,7 @@ struct Solver : SolverBase {
     if (can_pipe)
       for (int r : {16, 24, 32, 48})
         if (r <= Gmax && r <= N) cand.push_back({r, 2});
+    if (can_cl) cand.push_back({1, 3});
     if (cand.empty()) return;
     CUDA_TRY(cudaMemsetAsync(mixed[0], 0, 5 * F1 * sizeof(cpx<T>), st));
     cudaEvent_t e0, e1;
@@ -902,6 +1056,7 @@ struct Solver : SolverBase {
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     pipe = false;
+    clus = false;
     set_mode(bestc.first, bestc.second);
     cache_store(path, key, 4 * bestc.first + bestc.second);
   }
@@ -1585,15 +1740,7 @@ int ns_init_ex(ns_ctx** out, const ns_params* prm) {
   }
   ns_ctx* c = new ns_ctx();
   c->p = p;
-  {
-    const double q = p.kmax * p.kmax;
-    double m = std::floor(q);
-    if (m == q) m -= 1;
-    c->K2max = (int)m;
-    double r = std::floor(p.kmax);
-    if (r == p.kmax) r -= 1;
-    c->Kimax = (int)r;
-  }
+  trunc_bounds(p.kmax, &c->K2max, &c->Kimax);
   try {
     CUDA_TRY(cudaSetDevice(p.device));
     if (p.stream) {
@@ -1956,6 +2103,7 @@ __global__ void k_shift_table_value(cpx<float>* out, int N, double d0, double d1
 
 std::mutex g_noalloc_mu;
 void* g_noalloc_base[256] = {nullptr};
+int g_noalloc_optin[256] = {0};
 
 }  // namespace
 
@@ -1971,6 +2119,7 @@ extern "C" int ns_nonlinear_noalloc(const void* state, void* out, int N, double 
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return NS_ERR_CUDA;
   unsigned char* base = nullptr;
+  int optin = 0;
   {
     // once per device, with that device current: the host-side name of the array is not a
     // device address, so ask the runtime for the address the kernels must use
@@ -1978,17 +2127,19 @@ extern "C" int ns_nonlinear_noalloc(const void* state, void* out, int N, double 
     if (!g_noalloc_base[dev]) {
       void* p = nullptr;
       if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return NS_ERR_CUDA;
-      int optin = 0;
-      if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+      int oi = 0;
+      if (cudaDeviceGetAttribute(&oi, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
         return NS_ERR_CUDA;
-      if (cudaFuncSetAttribute(k_pencil<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin) != cudaSuccess ||
-          cudaFuncSetAttribute(k_yinv<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin) != cudaSuccess ||
-          cudaFuncSetAttribute(k_yfwd<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin) != cudaSuccess ||
-          cudaFuncSetAttribute(k_xrow<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin) != cudaSuccess)
+      if (cudaFuncSetAttribute(k_pencil<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, oi) != cudaSuccess ||
+          cudaFuncSetAttribute(k_yinv<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, oi) != cudaSuccess ||
+          cudaFuncSetAttribute(k_yfwd<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, oi) != cudaSuccess ||
+          cudaFuncSetAttribute(k_xrow<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, oi) != cudaSuccess)
         return NS_ERR_CUDA;
       g_noalloc_base[dev] = p;
+      g_noalloc_optin[dev] = oi;
     }
     base = static_cast<unsigned char*>(g_noalloc_base[dev]);
+    optin = g_noalloc_optin[dev];
   }
   const int M = N / 2;
   cpx<float>* mixed = reinterpret_cast<cpx<float>*>(base + kOffMixed);
@@ -1998,32 +2149,12 @@ extern "C" int ns_nonlinear_noalloc(const void* state, void* out, int N, double 
   cpx<float>* sh = reinterpret_cast<cpx<float>*>(base + kOffSh);
   int* err = reinterpret_cast<int*>(base + kOffErr);
 
-  // launch shapes (same rules as a context of this size)
-  const size_t cs = sizeof(cpx<float>), smax = 200 * 1024;
+  // launch shapes and truncation bounds: the same helpers as a context of this size
   FFTPlan pz = make_plan(N, N), px = make_plan(M, N);
-  int TX = largest_divisor_le(M, 16);
-  while (TX > 1 && (4 * N * TX * cs > smax || fft_block(TX, N) > 512)) TX = largest_divisor_le(M, TX - 1);
-  const int bdP = fft_block(TX, N) < 256 ? 256 : fft_block(TX, N);
-  const size_t smP = 4 * (size_t)N * TX * cs;
-  int TY = largest_divisor_le(M, 16);
-  while (TY > 1 && (6 * N * TY * cs > smax || fft_block(TY, N) > 512)) TY = largest_divisor_le(M, TY - 1);
-  const int bdY = fft_block(TY, N) < 256 ? 256 : fft_block(TY, N);
-  const size_t smYi = 6 * (size_t)N * TY * cs, smYf = 3 * (size_t)N * TY * cs;
-  int RX = 16;
-  while (RX > 1 && (6 * (size_t)RX * M * cs > 100 * 1024 || fft_block(RX, M) > 512)) RX /= 2;
-  const int bdX = fft_block(RX, M) < 256 ? 256 : fft_block(RX, M);
-  const size_t smX = 6 * (size_t)RX * M * cs;
-
+  const GenericShapes g = generic_shapes(N, sizeof(cpx<float>));
+  if (!generic_shapes_fit(g, optin)) return NS_ERR_INTERNAL;
   int K2max, Kimax;
-  {
-    const double q = kmax * kmax;
-    double m = std::floor(q);
-    if (m == q) m -= 1;
-    K2max = (int)m;
-    double r = std::floor(kmax);
-    if (r == kmax) r -= 1;
-    Kimax = (int)r;
-  }
+  trunc_bounds(kmax, &K2max, &Kimax);
 
   // the error flag must start at zero; every other region is written before it is read
   if (cudaMemsetAsync(err, 0, sizeof(int), st) != cudaSuccess) return NS_ERR_CUDA;
@@ -2032,19 +2163,19 @@ extern "C" int ns_nonlinear_noalloc(const void* state, void* out, int N, double 
 
   PencilArgs<float> p;
   memset(&p, 0, sizeof(p));
-  p.N = N; p.M = M; p.TX = TX; p.pz = pz; p.tw = tw; p.mode = MODE_INIT;
+  p.N = N; p.M = M; p.TX = g.TX; p.pz = pz; p.tw = tw; p.mode = MODE_INIT;
   p.src = static_cast<const cpx<float>*>(state);
   p.trunc = truncation; p.K2max = K2max; p.Kimax = Kimax; p.err = err;
   p.nOut = 1; p.osh[0] = sh; p.out[0] = mixed;
-  k_pencil<float><<<(M / TX) * N, bdP, smP, st>>>(p);
+  k_pencil<float><<<(M / g.TX) * N, g.bdP, g.smP, st>>>(p);
 
   SlabArgs<float> a;
   memset(&a, 0, sizeof(a));
-  a.N = N; a.M = M; a.py = pz; a.px = px; a.tw = tw; a.scr = scr; a.TY = TY; a.RX = RX;
+  a.N = N; a.M = M; a.py = pz; a.px = px; a.tw = tw; a.scr = scr; a.TY = g.TY; a.RX = g.RX;
   a.err = err; a.mixed = mixed; a.Ft = Ft; a.xmode = XMODE_NONLINEAR; a.z0 = 0; a.G = N;
-  k_yinv<float><<<dim3(M / TY, N), bdY, smYi, st>>>(a);
-  k_xrow<float><<<(N * N + RX - 1) / RX, bdX, smX, st>>>(a);
-  k_yfwd<float><<<dim3(M / TY, N), bdY, smYf, st>>>(a);
+  k_yinv<float><<<dim3(M / g.TY, N), g.bdY, g.smYi, st>>>(a);
+  k_xrow<float><<<(N * N + g.RX - 1) / g.RX, g.bdX, g.smX, st>>>(a);
+  k_yfwd<float><<<dim3(M / g.TY, N), g.bdY, g.smYf, st>>>(a);
 
   PencilArgs<float> q = p;
   q.mode = MODE_NL;
@@ -2052,7 +2183,7 @@ extern "C" int ns_nonlinear_noalloc(const void* state, void* out, int N, double 
   q.nOut = 0;
   q.nF = 1; q.F[0] = Ft; q.dsh[0] = sh; q.wF[0] = (float)(1.0 / ((double)N * N * N));
   q.acc = static_cast<cpx<float>*>(out);
-  k_pencil<float><<<(M / TX) * N, bdP, smP, st>>>(q);
+  k_pencil<float><<<(M / g.TX) * N, g.bdP, g.smP, st>>>(q);
   if (cudaGetLastError() != cudaSuccess) return NS_ERR_CUDA;
 
   int h = 0;

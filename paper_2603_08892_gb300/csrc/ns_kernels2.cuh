@@ -1053,6 +1053,12 @@ __global__ void __launch_bounds__(PipeCfg<T, N>::NT, NS_PIPE_MINB)
   }
 }
 
+}  // namespace ns
+
+#include "ns_slabcl.cuh"
+
+namespace ns {
+
 // ---- registry entry of one size ------------------------------------------------------
 template <typename T>
 struct K2Entry {
@@ -1067,6 +1073,10 @@ struct K2Entry {
   void (*slabpipe)(SlabArgs<T>, PipeCtl) = nullptr;  // null when the size has no pipeline
   int NTPIPE = 0;
   size_t smPIPE = 0;
+  // the slab pass in thread-block clusters of CLS CTAs (null when the size has none)
+  void (*slabcl)(CUtensorMap, cpx<T>*, const cpx<T>*, ClArgs) = nullptr;
+  int CLS = 0, NTCL = 0, CLKC = 0;
+  size_t smCL = 0;
   int TX = 0, NTP = 0, TY = 0, NTY = 0, TYI = 0, NTYI = 0, RX = 0, NTX = 0;
   size_t smP1 = 0, smP4 = 0, smP5 = 0, smY = 0, smYI = 0, smX = 0;
 };
@@ -1087,6 +1097,13 @@ K2Entry<T> make_k2_entry() {
   e.yinv = k2_yinv<T, N>;
   e.yfwd = k2_yfwd<T, N>;
   e.xrow = k2_xrow<T, N>;
+  if constexpr (ClCfg<T, N>::ok) {
+    e.slabcl = k2_slabcl<T, N>;
+    e.CLS = ClCfg<T, N>::CS;
+    e.NTCL = ClCfg<T, N>::NT;
+    e.CLKC = ClCfg<T, N>::KC;
+    e.smCL = ClCfg<T, N>::smem;
+  }
   if constexpr (PipeCfg<T, N>::ok) {
     e.slabpipe = k2_slabpipe<T, N>;
     e.NTPIPE = PipeCfg<T, N>::NT;

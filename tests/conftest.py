@@ -29,3 +29,21 @@ def ns():
     from paper_2603_08892_gb300 import binding
 
     return binding
+
+
+@pytest.fixture
+def report():
+    """Record a measured error against the oracle: ``report(name, value, bound)`` appends one
+    JSON line to the file named by the environment variable NS_ERROR_REPORT (nothing when it is
+    unset), so that a GPU run leaves the table of errors per result behind."""
+    import json
+
+    path = os.environ.get("NS_ERROR_REPORT")
+
+    def rec(name, value, bound=None, **extra):
+        if not path:
+            return
+        with open(path, "a") as f:
+            f.write(json.dumps(dict(name=name, value=float(value), bound=bound, **extra)) + "\n")
+
+    return rec

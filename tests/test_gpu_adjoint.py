@@ -16,7 +16,7 @@ def rel(a, b):
 
 @pytest.mark.parametrize("forced", [False, True])
 @pytest.mark.parametrize("scheme", [4, 3])
-def test_fp64_gradient_matches_oracle(ns, forced, scheme):
+def test_fp64_gradient_matches_oracle(ns, report, forced, scheme):
     N, nu, dt, nsteps = 16, 0.01, 0.01, 7
     kmax = N / 2
     u0 = inputs.hit_initial(N, 7)
@@ -28,6 +28,7 @@ def test_fp64_gradient_matches_oracle(ns, forced, scheme):
     f = fo.Forcing(N, 2.0, 3.0, 1.0, 0.02, seed=7) if forced else None
     Lr, gr = ad.grad_final_dissipation(u0, nsteps, dt, prob, seed=5, forcing=f, ckpt_every=3,
                                        approx=scheme == 3)
+    report("adjoint_gradient_%s_N16_7_steps_fp64" % ("forced" if forced else "decaying"), rel(g, gr), 1e-10)
     assert abs(L - Lr) < 1e-12 * Lr
     assert rel(g, gr) < 1e-10
 
@@ -48,7 +49,7 @@ def test_fp64_gradient_central_differences_on_gpu(ns):
             assert abs(fd - float(np.sum(g * v))) < 1e-6 * abs(fd)
 
 
-def test_fp32_forced_gradient_against_fp64_oracle(ns):
+def test_fp32_forced_gradient_against_fp64_oracle(ns, report):
     # reduced config-5 shape: forced HIT at 32^3, 20 steps, checkpoints every 10, FP32
     N, dt, nsteps = 32, 0.005, 20
     kmax = N / 2
@@ -60,8 +61,10 @@ def test_fp32_forced_gradient_against_fp64_oracle(ns):
     prob = sc.Problem(N, nu, kmax)
     f = fo.Forcing(N, 2.0, 3.0, 1.0, 0.5, seed=7)
     Lr, gr = ad.grad_final_dissipation(u0, nsteps, dt, prob, seed=7, forcing=f, ckpt_every=10)
+    report("adjoint_loss_forced_N32_20_steps_fp32", abs(L - Lr) / Lr, 1e-4)
+    report("adjoint_gradient_forced_N32_20_steps_fp32", rel(g, gr), 2e-5)
     assert abs(L - Lr) < 1e-4 * Lr
-    assert rel(g, gr) < 2e-3
+    assert rel(g, gr) < 2e-5  # measured 1.6e-6
 
 
 def test_autograd_function(ns):

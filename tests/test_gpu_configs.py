@@ -114,7 +114,7 @@ def test_config3_forced_hit_512_split_and_768_rk4(ns):
     assert abs((E1 - E0) / (3 * dt) + 0.5 * (d0 + d1)) < 0.02 * d0
 
 
-def test_config5_adjoint_64_forced_50_steps(ns):
+def test_config5_adjoint_64_forced_50_steps(ns, report):
     N, nsteps, ckpt = 64, 50, 10
     kmax = N / 2
     nu = kmax ** (-4.0 / 3.0)
@@ -138,5 +138,10 @@ def test_config5_adjoint_64_forced_50_steps(ns):
     prob = sc.Problem(N, nu, kmax)
     f = fo.Forcing(N, 2.0, 3.0, 1.0, 0.5, seed=7)
     Lr, gr = ad.grad_final_dissipation(u0, nsteps, dt, prob, seed=7, forcing=f, ckpt_every=ckpt)
+    report("adjoint_gradient_config5_N64_50_steps_fp64", rel(g64, gr), 1e-9)
+    report("adjoint_loss_config5_N64_50_steps_fp32", abs(L32 - Lr) / Lr, 1e-4)
+    report("adjoint_gradient_config5_N64_50_steps_fp32", rel(g32, gr), 1e-4)
     assert abs(L64 - Lr) < 1e-11 * Lr and rel(g64, gr) < 1e-9
-    assert abs(L32 - Lr) < 1e-4 * Lr and rel(g32, gr) < 5e-3
+    # FP32: u = 6e-8 rounding per stage, carried through 50 forward and 50 adjoint steps
+    # (measured 1.6e-6 over 20 steps at 32^3)
+    assert abs(L32 - Lr) < 1e-4 * Lr and rel(g32, gr) < 1e-4

@@ -67,7 +67,7 @@ def test_nonlinear_term_matches_oracle(ns, N, trunc, frac, prec):
         for delta in ([0, 0, 0], [dx / 2] * 3, [0.31 * dx, 0.77 * dx, 0.05 * dx]):
             got = s.nonlinear(delta, S)
             ref = onl.nonlinear(S, delta, kmax, trunc)
-            assert rel(got, ref) < TOL[prec] * (5 if prec == 0 else 1)
+            assert rel(got, ref) < TOL[prec]  # FP32 measured <= 1.7e-6 (N <= 96)
 
 
 @pytest.mark.parametrize("prec", [1, 0])
@@ -278,7 +278,7 @@ def test_generic_kernel_sizes(ns, N, prec):
     delta = [0.2 * dx, 0.9 * dx, 0.4 * dx]
     with ns.Solver(N, 0.01, kmax, scheme=4, precision=prec, seed=2) as s:
         got = s.nonlinear(delta, S)
-        assert rel(got, onl.nonlinear(S, delta, kmax)) < TOL[prec] * 5
+        assert rel(got, onl.nonlinear(S, delta, kmax)) < TOL[prec]
         s.set_state(S)
         s.step(0.01, 2)
         out = s.get_state()
