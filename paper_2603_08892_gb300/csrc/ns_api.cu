@@ -264,7 +264,8 @@ struct Solver : SolverBase {
   // slab pass in thread-block clusters, the plane kept on chip (k2_slabcl); chosen by the
   // autotuner where the size has the kernel and the device can hold its clusters
   bool clus = false;
-  int cl_ncl = -1;                 // clusters of a launch (-1: not yet queried)
+  int cl_var = 1;                  // thread-count variant of the cluster kernel
+  int cl_ncl = -1;                 // clusters the device holds at once (-1: not yet queried)
   long long cl_spin = 1ll << 20;   // polls of its bounded TMA wait
   std::vector<std::pair<const void*, CUtensorMap>> cl_maps;  // TMA maps of the mixed buffers
   cudaStream_t ss[2] = {nullptr, nullptr};
@@ -416,11 +417,12 @@ struct Solver : SolverBase {
       allow(k2.yinv, k2.smYI);
       allow(k2.yfwd, k2.smY);
       allow(k2.xrow, k2.smX);
-      if (k2.slabcl) {
-        allow(k2.slabcl, k2.smCL);
-        if (k2.CLS > 8)
-          CUDA_TRY(cudaFuncSetAttribute(k2.slabcl, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
-      }
+      for (int v = 0; v < 2; ++v)
+        if (k2.slabcl[v]) {
+          allow(k2.slabcl[v], k2.smCL);
+          if (k2.CLS > 8)
+            CUDA_TRY(cudaFuncSetAttribute(k2.slabcl[v], cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+        }
       if (k2.slabpipe)  // (it has a few bytes of static shared memory: its own size, not optin)
         CUDA_TRY(cudaFuncSetAttribute(k2.slabpipe, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k2.smPIPE));
     }
@@ -523,7 +525,7 @@ struct Solver : SolverBase {
   int cl_clusters() {
     if (cl_ncl >= 0) return cl_ncl;
     cl_ncl = 0;
-    if (!use2 || !k2.slabcl) return 0;
+    if (!use2 || !k2.slabcl[0]) return 0;
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeClusterDimension;
@@ -531,16 +533,16 @@ struct Solver : SolverBase {
     at[0].val.clusterDim.y = 1;
     at[0].val.clusterDim.z = 1;
     cfg.gridDim = dim3(k2.CLS);
-    cfg.blockDim = dim3(k2.NTCL);
+    cfg.blockDim = dim3(k2.NTCL[0]);
     cfg.dynamicSmemBytes = k2.smCL;
     cfg.attrs = at;
     cfg.numAttrs = 1;
     int n = 0;
-    if (cudaOccupancyMaxActiveClusters(&n, k2.slabcl, &cfg) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveClusters(&n, k2.slabcl[0], &cfg) != cudaSuccess) {
       cudaGetLastError();
       n = 0;
     }
-    cl_ncl = n < N ? n : N;
+    cl_ncl = n;
     return cl_ncl;
   }
   // TMA map of a mixed buffer [5][N][N][M]: scalars of T, dims {2M, N, 5N}, box {2KC, N, 1}
@@ -576,14 +578,14 @@ struct Solver : SolverBase {
     at[0].val.clusterDim.x = k2.CLS;
     at[0].val.clusterDim.y = 1;
     at[0].val.clusterDim.z = 1;
-    cfg.gridDim = dim3(k2.CLS * cl_clusters());
-    cfg.blockDim = dim3(k2.NTCL);
+    cfg.gridDim = dim3(k2.CLS * (N / k2.CLPL));  // every cluster takes CLPL planes
+    cfg.blockDim = dim3(k2.NTCL[cl_var]);
     cfg.dynamicSmemBytes = k2.smCL;
     cfg.stream = st;
     cfg.attrs = at;
     cfg.numAttrs = 1;
     cudaEvent_t e = prof_begin(NS_PROF_SLAB_CLUSTER);
-    CUDA_TRY(cudaLaunchKernelEx(&cfg, k2.slabcl, map, out, static_cast<const cpx<T>*>(tw), ca));
+    CUDA_TRY(cudaLaunchKernelEx(&cfg, k2.slabcl[cl_var], map, out, static_cast<const cpx<T>*>(tw), ca));
     prof_end(e);
   }
 
@@ -598,7 +600,7 @@ struct Solver : SolverBase {
       a.umax = d_umax;
     }
     cudaEvent_t pass = prof_begin(NS_PROF_SLAB_PASS);
-    if (clus && use2 && k2.slabcl && cl_clusters() > 0) {
+    if (clus && use2 && k2.slabcl[cl_var] && cl_clusters() > 0) {
       slab_cluster(mix, out, a.umax);
       prof_end(pass);
       LAUNCH_CHECK();
@@ -892,6 +894,7 @@ struct Solver : SolverBase {
   // plane is transformed the same way).  NS_AUTOTUNE=0 disables it; NS_AUTOTUNE_CACHE sets the
   // cache file; NS_SLAB_PLANES=g forces a group size, NS_SLAB_STREAMS=1|2 the stream count,
   // NS_SLAB_PIPE=1 the pipeline (ring NS_PIPE_RING, lag NS_PIPE_LAG) and =0 excludes it;
+  // NS_SLAB_CLUSTER=1 the cluster pass (thread variant NS_CL_VARIANT) and =0 excludes it;
   // NS_PIPE_SPIN bounds its waits, NS_PIPE_TEST_STALL=1 makes them unsatisfiable (test hook).
   static std::string cache_path() {
     const char* e = std::getenv("NS_AUTOTUNE_CACHE");
@@ -965,11 +968,15 @@ struct Solver : SolverBase {
   }
 
   // The cached value encodes the mode: 4 G + m, m = 0 one stream, 1 two streams (G planes per
-  // group), 2 the pipeline (G = ring planes, lag G / 4), 3 the cluster pass (G unused).
+  // group), 2 the pipeline (G = ring planes, lag G / 4), 3 the cluster pass (G = 1 + its
+  // thread-count variant).
   void set_mode(int g, int m) {
     pipe = m == 2;
     clus = m == 3;
-    if (clus) return;
+    if (clus) {
+      cl_var = g == 2 ? 1 : 0;  // G field: 1 = 384 threads, 2 = 768 threads
+      return;
+    }
     if (pipe) {
       pipe_ring = g;
       pipe_lag = g / 4 > 0 ? g / 4 : 1;
@@ -985,10 +992,10 @@ struct Solver : SolverBase {
     if (const char* e = std::getenv("NS_PIPE_TEST_STALL")) pipe_stall = std::atoi(e) ? 1 : 0;
     if (const char* e = std::getenv("NS_CL_SPIN")) cl_spin = std::max(1ll, std::atoll(e));
     const char* fcl = std::getenv("NS_SLAB_CLUSTER");
-    // (opt-in until its parity tests have run on the device)
-    const bool can_cl = use2 && k2.slabcl && fcl && std::string(fcl) == "1" && cl_clusters() > 0;
-    if (fcl && std::string(fcl) == "1" && can_cl) {  // forced cluster pass
-      set_mode(1, 3);
+    const bool can_cl = use2 && k2.slabcl[0] && !(fcl && std::string(fcl) == "0") && cl_clusters() > 0;
+    if (fcl && std::string(fcl) == "1" && can_cl) {  // forced cluster pass (NS_CL_VARIANT 0 or 1)
+      const char* fv = std::getenv("NS_CL_VARIANT");
+      set_mode(fv && std::atoi(fv) == 0 ? 1 : 2, 3);
       return;
     }
     const char* fpipe = std::getenv("NS_SLAB_PIPE");
@@ -1027,7 +1034,8 @@ struct Solver : SolverBase {
     if (can_pipe)
       for (int r : {16, 24, 32, 48})
         if (r <= Gmax && r <= N) cand.push_back({r, 2});
-    if (can_cl) cand.push_back({1, 3});
+    if (can_cl)
+      for (int v = 0; v < 2; ++v) cand.push_back({1 + v, 3});
     if (cand.empty()) return;
     CUDA_TRY(cudaMemsetAsync(mixed[0], 0, 5 * F1 * sizeof(cpx<T>), st));
     cudaEvent_t e0, e1;

@@ -164,9 +164,13 @@ __device__ __forceinline__ void stage_twiddles(cpx<T>* w, const cpx<T>* __restri
 // twiddles W_{NS R}^{p r} (p = j mod NS), a radix-R DFT, and writes q NS R + p + r NS.
 // HOLD: every input is read (and a barrier passed) before any output is written.
 // Threads with threadIdx.x >= NT take no butterflies but pass the barriers.
+// tid: the thread's index in the block (threadIdx.x; a caller may pass a value the compiler
+// cannot prove loop-invariant, to keep the stage's index arithmetic out of its registers
+// across unrelated code).
 template <typename T, int n, int R, int NS, int TWS, int NL, int NT, bool LF, int DIR, bool HOLD,
           class Src, class Dst>
-__device__ __forceinline__ void cstage(const Src& src, const Dst& dst, const cpx<T>* __restrict__ tw) {
+__device__ __forceinline__ void cstage(const Src& src, const Dst& dst, const cpx<T>* __restrict__ tw,
+                                       int tid = threadIdx.x) {
   constexpr int NB = n / R;
   constexpr int TOT = NB * NL;
   constexpr int KB = (TOT + NT - 1) / NT;
@@ -203,8 +207,8 @@ __device__ __forceinline__ void cstage(const Src& src, const Dst& dst, const cpx
     cpx<T> v[KB][R];
 #pragma unroll
     for (int c = 0; c < KB; ++c) {
-      const int b = threadIdx.x + c * NT;
-      if (threadIdx.x < NT && (TOT % NT == 0 || b < TOT)) {
+      const int b = tid + c * NT;
+      if (tid < NT && (TOT % NT == 0 || b < TOT)) {
         int line, j;
         map(b, line, j);
         compute(v[c], line, j);
@@ -213,8 +217,8 @@ __device__ __forceinline__ void cstage(const Src& src, const Dst& dst, const cpx
     __syncthreads();
 #pragma unroll
     for (int c = 0; c < KB; ++c) {
-      const int b = threadIdx.x + c * NT;
-      if (threadIdx.x < NT && (TOT % NT == 0 || b < TOT)) {
+      const int b = tid + c * NT;
+      if (tid < NT && (TOT % NT == 0 || b < TOT)) {
         int line, j;
         map(b, line, j);
         emit(v[c], line, j);
@@ -223,8 +227,8 @@ __device__ __forceinline__ void cstage(const Src& src, const Dst& dst, const cpx
   } else {
 #pragma unroll
     for (int c = 0; c < KB; ++c) {
-      const int b = threadIdx.x + c * NT;
-      if (threadIdx.x < NT && (TOT % NT == 0 || b < TOT)) {
+      const int b = tid + c * NT;
+      if (tid < NT && (TOT % NT == 0 || b < TOT)) {
         int line, j;
         map(b, line, j);
         cpx<T> v[R];
@@ -289,22 +293,22 @@ template <typename T, int n, int TWS, int NL, int NT, bool LF, int DIR, bool ALI
           int MR = NS_MAX_RADIX>
 struct CStagesIP {
   static constexpr CPlan P = cplan(n, MR);
-  template <class Src, class Dst>
-  static __device__ __forceinline__ void run(const Src& src, const WorkTile<T, n, NL, LF>& B,
-                                             const Dst& dst, const cpx<T>* __restrict__ tw) {
+  template <class Src, class Tile, class Dst>
+  static __device__ __forceinline__ void run(const Src& src, const Tile& B, const Dst& dst,
+                                             const cpx<T>* __restrict__ tw, int tid = threadIdx.x) {
     constexpr int R = P.r[S];
     constexpr bool last = S + 1 == P.nst;
     if constexpr (S == 0 && last)
-      cstage<T, n, R, NS, TWS, NL, NT, LF, DIR, ALIAS>(src, dst, tw);
+      cstage<T, n, R, NS, TWS, NL, NT, LF, DIR, ALIAS>(src, dst, tw, tid);
     else if constexpr (S == 0)
-      cstage<T, n, R, NS, TWS, NL, NT, LF, DIR, ALIAS>(src, B, tw);
+      cstage<T, n, R, NS, TWS, NL, NT, LF, DIR, ALIAS>(src, B, tw, tid);
     else if constexpr (last)
-      cstage<T, n, R, NS, TWS, NL, NT, LF, DIR, true>(B, dst, tw);
+      cstage<T, n, R, NS, TWS, NL, NT, LF, DIR, true>(B, dst, tw, tid);
     else
-      cstage<T, n, R, NS, TWS, NL, NT, LF, DIR, true>(B, B, tw);
+      cstage<T, n, R, NS, TWS, NL, NT, LF, DIR, true>(B, B, tw, tid);
     if constexpr (!last) {
       __syncthreads();
-      CStagesIP<T, n, TWS, NL, NT, LF, DIR, ALIAS, S + 1, NS * R, MR>::run(src, B, dst, tw);
+      CStagesIP<T, n, TWS, NL, NT, LF, DIR, ALIAS, S + 1, NS * R, MR>::run(src, B, dst, tw, tid);
     }
   }
 };
@@ -322,6 +326,15 @@ template <typename T, int n, int TWS, int NL, int NT, bool LF, int DIR, bool ALI
 __device__ __forceinline__ void cfft_ip_to(const Src& src, cpx<T>* tile, const Dst& dst,
                                            const cpx<T>* __restrict__ tw) {
   CStagesIP<T, n, TWS, NL, NT, LF, DIR, ALIAS, 0, 1, MR>::run(src, WorkTile<T, n, NL, LF>{tile}, dst, tw);
+}
+
+// In-place transform of NL lines over any tile accessor B (get / put of (line, e)); the last
+// stage writes through dst.  tid as in cstage.
+template <typename T, int n, int TWS, int NL, int NT, bool LF, int DIR, bool ALIAS,
+          int MR = NS_MAX_RADIX, class Src, class Tile, class Dst>
+__device__ __forceinline__ void cfft_ip_tid(const Src& src, const Tile& B, const Dst& dst,
+                                            const cpx<T>* __restrict__ tw, int tid) {
+  CStagesIP<T, n, TWS, NL, NT, LF, DIR, ALIAS, 0, 1, MR>::run(src, B, dst, tw, tid);
 }
 
 // copy of the twiddle table into shared memory (all threads of the block participate)

@@ -1073,9 +1073,10 @@ struct K2Entry {
   void (*slabpipe)(SlabArgs<T>, PipeCtl) = nullptr;  // null when the size has no pipeline
   int NTPIPE = 0;
   size_t smPIPE = 0;
-  // the slab pass in thread-block clusters of CLS CTAs (null when the size has none)
-  void (*slabcl)(CUtensorMap, cpx<T>*, const cpx<T>*, ClArgs) = nullptr;
-  int CLS = 0, NTCL = 0, CLKC = 0;
+  // the slab pass in thread-block clusters of CLS CTAs (null when the size has none), two
+  // thread counts: variant v has NTCL[v] threads
+  void (*slabcl[2])(CUtensorMap, cpx<T>*, const cpx<T>*, ClArgs) = {nullptr, nullptr};
+  int CLS = 0, NTCL[2] = {0, 0}, CLKC = 0, CLPL = 1;
   size_t smCL = 0;
   int TX = 0, NTP = 0, TY = 0, NTY = 0, TYI = 0, NTYI = 0, RX = 0, NTX = 0;
   size_t smP1 = 0, smP4 = 0, smP5 = 0, smY = 0, smYI = 0, smX = 0;
@@ -1098,10 +1099,13 @@ K2Entry<T> make_k2_entry() {
   e.yfwd = k2_yfwd<T, N>;
   e.xrow = k2_xrow<T, N>;
   if constexpr (ClCfg<T, N>::ok) {
-    e.slabcl = k2_slabcl<T, N>;
+    e.slabcl[0] = k2_slabcl<T, N, 384>;
+    e.slabcl[1] = k2_slabcl<T, N, 768>;
+    e.NTCL[0] = 384;
+    e.NTCL[1] = 768;
     e.CLS = ClCfg<T, N>::CS;
-    e.NTCL = ClCfg<T, N>::NT;
     e.CLKC = ClCfg<T, N>::KC;
+    e.CLPL = ClCfg<T, N>::PL;
     e.smCL = ClCfg<T, N>::smem;
   }
   if constexpr (PipeCfg<T, N>::ok) {
