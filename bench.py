@@ -57,6 +57,8 @@ def parse():
                     help="steps of the end-to-end leg (default: --steps)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
     ap.add_argument("--no-rk4", action="store_true")
+    ap.add_argument("--no-accuracy", action="store_true",
+                    help="skip the accuracy leg (PS 256^3 FP32/FP64 and RK4 384^3 to t = 9)")
     ap.add_argument("--batch-steps", type=int, default=200,
                     help="steps of the 64-member ensemble leg (0: skip)")
     ap.add_argument("--quality", action="store_true",
@@ -171,36 +173,58 @@ def barrier(world):
         dist.barrier()
 
 
-def cpu_oracle_rate(budget_s=60.0, max_steps=3, warmup=0):
-    """Oracle steps/s on the workload (whole 256^3 steps, bounded by a wall-time budget)."""
+def host_cores():
+    """(threads this process may use, CPU model name from lscpu)."""
+    cores = len(os.sched_getaffinity(0))
+    model = "unknown"
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    return cores, model
+
+
+def cpu_oracle_rate(budget_s=60.0, max_steps=3, warmup=0, seed=SEED):
+    """Oracle steps/s on the workload (whole 256^3 steps, bounded by a wall-time budget), its
+    3D transforms on every host core (scipy.fft workers).  Returns (rate, steps, seconds,
+    final state)."""
     from oracle import rng as orng
     from oracle import schemes as sc
     from oracle import spectral as osp
     from paper_2603_08892_gb300 import inputs
 
-    N = N_PS
-    dt = dt_for(N)
-    prob = sc.Problem(N, NU, KMAX)
-    S = osp.set_velocity(inputs.taylor_green(N), KMAX)
-    for n in range(warmup):
-        S = sc.step_ps_random(S, dt, prob, orng.shift_alpha(SEED, n, N))
-    t0 = time.perf_counter()
-    n = 0
-    while n < max_steps:
-        S = sc.step_ps_random(S, dt, prob, orng.shift_alpha(SEED, warmup + n, N))
-        n += 1
-        if time.perf_counter() - t0 > budget_s:
-            break
-    el = time.perf_counter() - t0
-    return n / el, n, el
+    cores, _ = host_cores()
+    old = osp.set_fft_workers(cores)
+    try:
+        N = N_PS
+        dt = dt_for(N)
+        prob = sc.Problem(N, NU, KMAX)
+        S = osp.set_velocity(inputs.taylor_green(N), KMAX)
+        for n in range(warmup):
+            S = sc.step_ps_random(S, dt, prob, orng.shift_alpha(seed, n, N))
+        t0 = time.perf_counter()
+        n = 0
+        while n < max_steps:
+            S = sc.step_ps_random(S, dt, prob, orng.shift_alpha(seed, warmup + n, N))
+            n += 1
+            if time.perf_counter() - t0 > budget_s:
+                break
+        el = time.perf_counter() - t0
+    finally:
+        osp.set_fft_workers(old)
+    return n / el, n, el, S
 
 
 def run_reference(args, rank, world):
     if rank != 0:
         return
     steps = max(1, args.steps)
-    rate, n, el = cpu_oracle_rate(budget_s=150.0, max_steps=steps, warmup=min(args.warmup, 1))
-    cores = 1  # numpy.fft (pocketfft) and numpy elementwise run on one thread
+    rate, n, el, _ = cpu_oracle_rate(budget_s=150.0, max_steps=steps, warmup=min(args.warmup, 1))
+    cores, model = host_cores()  # the 3D transforms use every core; elementwise work one
     line = {
         "impl": "reference", "metric": METRIC, "value": rate, "unit": "steps/s",
         "n_gpus": args.gpus, "steps": n, "warmup": min(args.warmup, 1),
@@ -209,8 +233,10 @@ def run_reference(args, rank, world):
         "config": {"workload": WORKLOAD + " -- FP64 CPU oracle", "N": N_PS, "dt": dt_for(N_PS)},
         "gcells_per_s": rate * N_PS ** 3 / 1e9,
         "cpu_baseline": {"value": rate, "unit": "steps/s", "cores": cores, "kind": "oracle",
-                         "sample": "%d whole 256^3 steps after %d warm-up step(s), %.1f s"
-                                   % (n, min(args.warmup, 1), el)},
+                         "cpu_model": model,
+                         "sample": "%d whole 256^3 steps after %d warm-up step(s), %.1f s (FP64 "
+                                   "NumPy oracle, 3D transforms by scipy.fft on %d threads)"
+                                   % (n, min(args.warmup, 1), el, cores)},
         "e2e": {"value": rate, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -266,6 +292,56 @@ def run_quality(local):
                     "E_end": E, "eps_end": eps})
         print(json.dumps(out[-1]), flush=True)
     print(json.dumps({"study": "quality", "kmax": kmax, "Re": 1600, "window": [t0, T], "runs": out}))
+
+
+def accuracy_leg(ns, inputs, stream, local, line):
+    """Runs to t = 9: PS random 256^3 FP32 and FP64, RK4 + 2/3 384^3 FP32 (same kmax = 128).
+    Returns E(9), eps(9) of each run, the error index of the PS run against RK4 and of FP32
+    against FP64, and the simulated time per second of both schemes with the index beside it."""
+    import torch
+
+    from paper_2603_08892_gb300 import analysis
+
+    runs = {}
+    for name, N, scheme, prec in (("ps_fp32", N_PS, ns.RK2_PS_RANDOM, ns.FP32),
+                                  ("ps_fp64", N_PS, ns.RK2_PS_RANDOM, ns.FP64),
+                                  ("rk4_fp32", N_RK4, ns.RK4, ns.FP32)):
+        dtn = dt_for(N)
+        nsteps = int(round(T_END / dtn))
+        with ns.Solver(N, NU, KMAX, scheme=scheme, precision=prec, device=local,
+                       stream=stream.cuda_stream, seed=SEED) as r:
+            r.set_velocity(inputs.taylor_green(N))
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            r.step(dtn, nsteps)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            t, _ = r.time()
+            E, eps = r.energy()
+            spec = tuple(r.spectrum(k, 130) for k in (1, 2, 3))
+        runs[name] = {"N": N, "steps": nsteps, "t": t, "E": E, "eps": eps,
+                      "gpu_s": e0.elapsed_time(e1) / 1000.0, "spec": spec}
+    ps, ps64, rk = runs["ps_fp32"], runs["ps_fp64"], runs["rk4_fp32"]
+    err_rk4 = analysis.error_index([ps["spec"]], [rk["spec"]], KMAX)
+    err_64 = analysis.error_index([ps["spec"]], [ps64["spec"]], KMAX)
+    sim_ps = line["sim_time_per_s"]
+    sim_rk = line.get("rk4_two_thirds", {}).get("sim_time_per_s", T_END / rk["gpu_s"])
+    out = {"t_end": T_END,
+           "error_index_vs_rk4_pct": err_rk4,
+           "error_index_fp32_vs_fp64_pct": err_64,
+           "E9": {k: v["E"] for k, v in runs.items()},
+           "eps9": {k: v["eps"] for k, v in runs.items()},
+           "E9_fp32_vs_fp64_rel": abs(ps["E"] - ps64["E"]) / ps64["E"],
+           "steps_to_t9": {k: v["steps"] for k, v in runs.items()},
+           "gpu_s_to_t9": {k: v["gpu_s"] for k, v in runs.items()},
+           "sim_time_per_s": {"ps_fp32_256": sim_ps, "rk4_fp32_384": sim_rk},
+           "sim_time_speedup_vs_rk4": sim_ps / sim_rk,
+           "what": "PS random 256^3 FP32 delivers sim_time_speedup_vs_rk4 times the simulated "
+                   "time per second of RK4 + 2/3 at 384^3 (same kmax), at a spectral error "
+                   "index error_index_vs_rk4_pct (%) against it at t = 9"}
+    return out
 
 
 def timed_steps(ns, s, dt, K, stream):
@@ -440,6 +516,12 @@ def main():
         line["sim_time_speedup_vs_rk4"] = line["sim_time_per_s"] / line["rk4_two_thirds"]["sim_time_per_s"]
         r.close()
 
+    # accuracy beside the speed (config 2): the 256^3 Rogallo run in FP32 and FP64 and the 384^3
+    # RK4 + 2/3 run to t = 9 (the Taylor-Green dissipation peak), the spectral error index of
+    # Sec. 3.4 (Eq. quality, Appendix A) of the 1D spectra at t = 9
+    if rank == 0 and world == 1 and not args.no_accuracy:
+        line["accuracy_t9"] = accuracy_leg(ns, inputs, stream, local, line)
+
     # batched ensemble: 64 Taylor-Green members with 1% perturbations, 16 each of
     # N = 32, 64, 96, 128, Rogallo RK2 FP32, one persistent launch per call
     if args.batch_steps > 0:
@@ -482,20 +564,30 @@ def main():
     s.step_diag(dt, 1)  # allocates the series buffers outside the timed region
     barrier(world)
     torch.cuda.synchronize()
+    u_out = torch.empty((3, N_PS, N_PS, N_PS), dtype=torch.float64, pin_memory=True).numpy()
+    s.get_velocity(u_out)  # (warm-up of the read-back path)
+    barrier(world)
+    torch.cuda.synchronize()
     t0 = time.perf_counter()
     s.set_velocity(u0)  # synchronises
     t1 = time.perf_counter()
     Es, epss = s.step_diag(dt, Ke)
     t2 = time.perf_counter()
-    el = reduce_max(t2 - t0, world)
+    s.get_velocity(u_out)  # the final velocity back to pinned host memory (synchronises)
+    t3 = time.perf_counter()
+    el = reduce_max(t3 - t0, world)
     h2d = (3 * N_PS ** 3 * 8 + Ke * 48) / Ke  # the FP64 field once, the shift vectors per step
+    d2h = (Ke * 16 + 3 * N_PS ** 3 * 8) / Ke  # E and eps per step, the FP64 field once
     line["e2e"] = {"value": world * Ke / el, "unit": "steps/s", "h2d_bytes_per_step": h2d,
-                   "d2h_bytes_per_step": 16, "set_velocity_ms": (t1 - t0) * 1000.0,
+                   "d2h_bytes_per_step": d2h, "set_velocity_ms": (t1 - t0) * 1000.0,
                    "step_diag_ms_per_step": (t2 - t1) * 1000.0 / Ke,
-                   "finite": bool(np.all(np.isfinite(Es)) and np.all(np.isfinite(epss))),
-                   "what": "ns_set_velocity(pinned host 3x256^3 f64) once + ns_step_diag(dt, %d): E and eps "
+                   "get_velocity_ms": (t3 - t2) * 1000.0,
+                   "finite": bool(np.all(np.isfinite(Es)) and np.all(np.isfinite(epss))
+                                  and np.all(np.isfinite(u_out))),
+                   "what": "ns_set_velocity(pinned host 3x256^3 f64) + ns_step_diag(dt, %d): E and eps "
                            "of every step written by the device into mapped pinned host memory as "
-                           "it is produced; %d steps" % (Ke, Ke)}
+                           "it is produced + ns_get_velocity(final field to pinned host f64); %d steps"
+                           % (Ke, Ke)}
     # the same with a host round trip every step: ns_step(dt, 1) then ns_energy
     Ks = min(Ke, 200)
     s.set_velocity(u0)
@@ -510,10 +602,27 @@ def main():
     s.close()
 
     if rank == 0 and world == 1 and not args.no_cpu:
-        rate, n, el = cpu_oracle_rate(budget_s=40.0, max_steps=2)
-        line["cpu_baseline"] = {"value": rate, "unit": "steps/s", "cores": 1, "kind": "oracle",
+        rate, n, el, S_ref = cpu_oracle_rate(budget_s=40.0, max_steps=3)
+        cores, model = host_cores()
+        line["cpu_baseline"] = {"value": rate, "unit": "steps/s", "cores": cores, "kind": "oracle",
+                                "cpu_model": model,
                                 "sample": "%d whole 256^3 Rogallo steps of the FP64 NumPy oracle "
-                                          "(single-threaded pocketfft), %.1f s" % (n, el)}
+                                          "(3D transforms by scipy.fft on %d threads), %.1f s"
+                                          % (n, cores, el)}
+        # the sampled oracle steps double as a parity check of the benchmarked kernels: the
+        # same steps on the GPU (FP32 and FP64) from the same field, whole-state relative L2
+        errs = {}
+        for prec, name in ((ns.FP32, "fp32"), (ns.FP64, "fp64")):
+            with ns.Solver(N_PS, NU, KMAX, scheme=ns.RK2_PS_RANDOM, precision=prec, device=local,
+                           seed=SEED) as g:
+                g.set_velocity(inputs.taylor_green(N_PS))
+                g.step(dt, n)
+                got = g.get_state()
+            errs["rogallo_%d_steps_256_%s" % (n, name)] = float(
+                np.linalg.norm(got - S_ref) / np.linalg.norm(S_ref))
+        line["precision_errors"] = {
+            "vs": "FP64 oracle, the cpu_baseline sample's steps, whole state, relative L2",
+            "bounds": {"fp32_per_step": 2e-5, "fp64_per_step": 1e-12}, **errs}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -165,8 +165,12 @@ class Solver:
         assert u.shape == (3, self.N, self.N, self.N)
         self._check(_set_velocity(self._h, _ptr(u)))
 
-    def get_velocity(self):
-        u = np.empty((3, self.N, self.N, self.N))
+    def get_velocity(self, out=None):
+        """The physical velocity float64 [3, N, N, N]; `out` (C-contiguous float64, e.g. a view
+        of pinned host memory) receives it when given."""
+        u = np.empty((3, self.N, self.N, self.N)) if out is None else out
+        if u.dtype != np.float64 or not u.flags["C_CONTIGUOUS"] or u.shape != (3, self.N, self.N, self.N):
+            raise ValueError("out must be C-contiguous float64 of shape (3, N, N, N)")
         self._check(_get_velocity(self._h, _ptr(u)))
         return u
 
