@@ -165,6 +165,29 @@ enum { NS_LOSS_DISSIPATION = 0, NS_LOSS_ENERGY = 1 };
 int ns_vjp(ns_ctx* ctx, const double* u0, int nsteps, double dt, int ckpt_every, int loss,
            double* loss_out, double* grad_u0_out);
 
+/* Gradient of any loss of the final velocity u(T) with respect to u0 (no counterpart in the
+ * paper): the same forward and reverse sweeps as ns_vjp, the reverse sweep seeded with the
+ * caller's cotangent gT = dL/du(T) (host [3][N][N][N] FP64, gradient for the physical dot
+ * product); its cotangent of S_T is N^3 P T F(gT) (F the forward transform with the 1/N^3
+ * factor, whose adjoint for the full-spectrum product is F^{-1} / N^3).  Writes dL/du0 to
+ * grad_u0_out (host [3][N][N][N] FP64).  Errors as ns_vjp. */
+int ns_vjp_state(ns_ctx* ctx, const double* u0, int nsteps, double dt, int ckpt_every,
+                 const double* gT, double* grad_u0_out);
+
+/* The same in two calls on device buffers, for a reverse-mode autodiff caller: u0, uT, gT and
+ * grad_u0 are device pointers to [3][N][N][N] reals in the context's precision (float for
+ * NS_FP32, double for NS_FP64), caller owned and not aliased with each other.
+ * ns_tape_forward: sets the state from u0 (truncated and projected), runs nsteps steps of size
+ * dt keeping the state every ckpt_every steps on the device (the tape), and writes u(T) to uT.
+ * ns_tape_backward: the reverse sweep of the last ns_tape_forward, seeded with gT = dL/du(T)
+ * or, when gT is NULL, with the built-in `loss` (NS_LOSS_*) of the final state; writes
+ * dL/du0 to grad_u0.  It can be called again on the same tape.  NS_ERR_STATE without a tape
+ * (none recorded, or one invalidated by ns_vjp, ns_vjp_state or ns_set_forcing).  Both are
+ * ordered on the context's stream and synchronise it before returning; the caller makes its
+ * own writes to u0 / gT complete before the call. */
+int ns_tape_forward(ns_ctx* ctx, const void* u0, int nsteps, double dt, int ckpt_every, void* uT);
+int ns_tape_backward(ns_ctx* ctx, const void* gT, int loss, void* grad_u0);
+
 /* Kinetic energy E = (1/2) sum_k |uh|^2 and dissipation eps = nu sum_k k^2 |uh|^2 (full
  * spectrum sums, Sec. 3.4; FP64 states in FP64, FP32 states with each mode's terms in FP32,
  * compensated per-thread sums and FP64 across threads; fixed order, so repeatable).

@@ -19,7 +19,9 @@ Forcing O(S) = a(S) f with a the root of smaller modulus of a^2 (dt/2)<f,f> + a 
 b = Re<S, f>_w:  da/db = -|a| / sqrt(b^2 + 4 c eps), so the adjoint of S -> O(S) maps rho to
 (da/db) Re<f, rho>_w f.
 
-Loss: L = eps(S_T) = nu <S, k^2 S>_w, gradient 2 nu k^2 S.
+Loss: L = eps(S_T) = nu <S, k^2 S>_w, gradient 2 nu k^2 S.  A loss of the physical velocity
+u(T) = F^{-1}(S_T) with gradient g = dL/du(T) has the cotangent (F^{-1})^* g = N^3 F(g) of S_T,
+restricted to the truncated, divergence-free states by T and P (both self-adjoint).
 """
 import numpy as np
 
@@ -89,15 +91,9 @@ def dissipation_grad(S, nu):
     return 2.0 * nu * (KX * KX + KY * KY + KZ * KZ) * S
 
 
-def grad_final_dissipation(u0, nsteps, dt, prob, seed, forcing=None, ckpt_every=10,
-                           approx=False):
-    """L = eps(S_T) after nsteps RK2 phase-shift random steps from u0 (physical) and dL/du0.
-
-    Forward states are kept only every ckpt_every steps and recomputed segment by segment
-    in the backward sweep.  Returns (L, grad) with grad a physical field [3, N, N, N]
-    (gradient with respect to the physical dot product).
-    """
-    from .diagnostics import dissipation
+def _reverse(u0, nsteps, dt, prob, seed, forcing, ckpt_every, approx, seed_lam):
+    """Forward sweep from u0 with checkpoints, then the reverse sweep from the cotangent
+    seed_lam(S_T); returns (S_T, dL/du0 for the physical dot product)."""
     from .schemes import step_ps_random
 
     N = prob.N
@@ -115,8 +111,7 @@ def grad_final_dissipation(u0, nsteps, dt, prob, seed, forcing=None, ckpt_every=
         times.append(t)
         if (n + 1) % ckpt_every == 0:
             ckpt[n + 1] = S.copy()
-    L = dissipation(S, prob.nu)
-    lam = dissipation_grad(S, prob.nu)
+    lam = seed_lam(S)
     for seg0 in sorted([k for k in ckpt if k < nsteps], reverse=True):
         seg1 = min(seg0 + ckpt_every, nsteps)
         states = [ckpt[seg0]]
@@ -125,5 +120,31 @@ def grad_final_dissipation(u0, nsteps, dt, prob, seed, forcing=None, ckpt_every=
         for n in range(seg1 - 1, seg0 - 1, -1):
             lam = step_ps_random_vjp(states[n - seg0], lam, dt, prob, shift(n), times[n], forcing)
     mask = sp.truncation_mask(N, prob.kmax, prob.kind)
-    grad = sp.inverse(sp.project(lam * mask)) / float(N) ** 3
-    return L, grad
+    return S, sp.inverse(sp.project(lam * mask)) / float(N) ** 3
+
+
+def grad_final_state(u0, gT, nsteps, dt, prob, seed, forcing=None, ckpt_every=10, approx=False):
+    """dL/du0 of a loss of the final velocity u(T) whose gradient is gT = dL/du(T)
+    (physical [3, N, N, N]); the cotangent of S_T is N^3 P T F(gT) (module doc)."""
+    N = prob.N
+    mask = sp.truncation_mask(N, prob.kmax, prob.kind)
+
+    def seed_lam(S):
+        return sp.project(sp.forward(gT) * mask) * float(N) ** 3
+
+    return _reverse(u0, nsteps, dt, prob, seed, forcing, ckpt_every, approx, seed_lam)[1]
+
+
+def grad_final_dissipation(u0, nsteps, dt, prob, seed, forcing=None, ckpt_every=10,
+                           approx=False):
+    """L = eps(S_T) after nsteps RK2 phase-shift random steps from u0 (physical) and dL/du0.
+
+    Forward states are kept only every ckpt_every steps and recomputed segment by segment
+    in the backward sweep.  Returns (L, grad) with grad a physical field [3, N, N, N]
+    (gradient with respect to the physical dot product).
+    """
+    from .diagnostics import dissipation
+
+    S, grad = _reverse(u0, nsteps, dt, prob, seed, forcing, ckpt_every, approx,
+                       lambda S_: dissipation_grad(S_, prob.nu))
+    return dissipation(S, prob.nu), grad

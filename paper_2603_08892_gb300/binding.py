@@ -76,6 +76,10 @@ _set_time = _sig("ns_set_time", ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_in
 _device_state = _sig("ns_device_state", ctypes.c_int,
                      [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(ctypes.c_int)])
 _model_bytes = _sig("ns_model_bytes_per_step", ctypes.c_double, [_vp])
+_vjp_state = _sig("ns_vjp_state", ctypes.c_int, [_vp, _dp, ctypes.c_int, ctypes.c_double, ctypes.c_int, _dp, _dp])
+_tape_forward = _sig("ns_tape_forward", ctypes.c_int,
+                     [_vp, _vp, ctypes.c_int, ctypes.c_double, ctypes.c_int, _vp])
+_tape_backward = _sig("ns_tape_backward", ctypes.c_int, [_vp, _vp, ctypes.c_int, _vp])
 _fma_peak = _sig("ns_fma_peak", ctypes.c_int, [ctypes.c_int, ctypes.c_int, _dp])
 _nl1d = _sig("ns_nl1d", ctypes.c_int, [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                          ctypes.c_int, _dp, _dp])
@@ -109,7 +113,8 @@ EXPORTED = ["ns_init", "ns_init_ex", "ns_init_error", "ns_destroy", "ns_last_err
             "ns_set_forcing", "ns_step", "ns_step_cfl", "ns_step_diag", "ns_set_shifts",
             "ns_checkpoint_save", "ns_checkpoint_load", "ns_nonlinear", "ns_energy",
             "ns_energy_spectrum", "ns_energy_flux", "ns_time", "ns_set_time", "ns_device_state",
-            "ns_model_bytes_per_step", "ns_nl1d", "ns_fma_peak", "ns_profile", "ns_profile_read", "ns_nonlinear_noalloc", "ns_vjp", "ns_batch_init", "ns_batch_destroy", "ns_batch_last_error",
+            "ns_model_bytes_per_step", "ns_nl1d", "ns_fma_peak", "ns_profile", "ns_profile_read", "ns_nonlinear_noalloc", "ns_vjp", "ns_vjp_state",
+            "ns_tape_forward", "ns_tape_backward", "ns_batch_init", "ns_batch_destroy", "ns_batch_last_error",
             "ns_batch_member", "ns_batch_set_velocity", "ns_batch_get_state", "ns_batch_step",
             "ns_batch_energy", "ns_batch_set_spin_limit", "ns_batch_test_stall", "ns_batch_grid"]
 
@@ -271,6 +276,22 @@ class Solver:
 
     def model_bytes_per_step(self):
         return _model_bytes(self._h)
+
+    def vjp_state(self, u0, nsteps, dt, gT, ckpt_every=10):
+        """dL/du0 of a loss of u(T) whose gradient dL/du(T) is gT (see ns_vjp_state)."""
+        u = np.ascontiguousarray(u0, dtype=np.float64)
+        g = np.ascontiguousarray(gT, dtype=np.float64)
+        out = np.empty_like(u)
+        self._check(_vjp_state(self._h, _ptr(u), nsteps, dt, ckpt_every, _ptr(g), _ptr(out)))
+        return out
+
+    def tape_forward(self, u0_ptr, nsteps, dt, ckpt_every, uT_ptr):
+        """ns_tape_forward on device pointers (reals of the context's precision)."""
+        self._check(_tape_forward(self._h, _vp(u0_ptr), nsteps, dt, ckpt_every, _vp(uT_ptr)))
+
+    def tape_backward(self, gT_ptr, grad_ptr, loss=LOSS_DISSIPATION):
+        """ns_tape_backward on device pointers; gT_ptr None seeds with the built-in loss."""
+        self._check(_tape_backward(self._h, _vp(gT_ptr) if gT_ptr else None, loss, _vp(grad_ptr)))
 
     def vjp(self, u0, nsteps, dt, ckpt_every=10, loss=LOSS_DISSIPATION):
         """(L, dL/du0) of the loss on the state after nsteps steps from u0 (see ns_vjp)."""

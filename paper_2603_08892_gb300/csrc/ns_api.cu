@@ -208,6 +208,10 @@ struct SolverBase {
   virtual void buffers(double dt, NsCtxBuffers* b) = 0;
   virtual void vjp(const double* u0, int nsteps, double dt, int ckpt, int loss, double* L,
                    double* grad) = 0;
+  virtual void vjp_state(const double* u0, int nsteps, double dt, int ckpt, const double* gT,
+                         double* grad) = 0;
+  virtual void tape_forward(const void* u0, int nsteps, double dt, int ckpt, void* uT) = 0;
+  virtual void tape_backward(const void* gT, int loss, void* grad) = 0;
   virtual void profile(int on) = 0;
   virtual void profile_read(int k, double* ms, int64_t* n, int64_t* launches) = 0;
 };
@@ -413,6 +417,8 @@ struct Solver : SolverBase {
       allow(k2.pencil, k2.smP5);
       allow(k2.pencil1, k2.smP1);
       allow(k2.pencil1e, k2.smP1);
+      allow(k2.pencil1r[0], k2.smP1);
+      allow(k2.pencil1r[1], k2.smP1);
       allow(k2.pencil2, k2.smP5);
       allow(k2.yinv, k2.smYI);
       allow(k2.yfwd, k2.smY);
@@ -691,7 +697,10 @@ struct Solver : SolverBase {
   void pencil(const PencilArgs<T>& a) {
     cudaEvent_t e = prof_begin(NS_PROF_PENCIL);
     if (use2)
-      (a.nF == 1 && a.nOut == 1   ? (a.epart ? k2.pencil1e : k2.pencil1)
+      (a.nF == 1 && a.nOut == 1   ? (a.epart                  ? k2.pencil1e
+                                     : a.mode == MODE_ROG_1 ? k2.pencil1r[0]
+                                     : a.mode == MODE_ROG_2 ? k2.pencil1r[1]
+                                                            : k2.pencil1)
        : a.nF == 2 && a.nOut == 2 ? k2.pencil2
                                   : k2.pencil)<<<(M / k2.TX) * N, k2.NTP,
                                                   (a.nF == 1 && a.nOut == 1) ? k2.smP1
@@ -875,6 +884,7 @@ struct Solver : SolverBase {
   void set_forcing(int kind, double kfmin, double kfmax, double eps, double tcorr,
                    uint64_t seed) override {
     carry_step = -1;  // the mixed fields / state / forcing record change here
+    tape.valid = false;  // a recorded adjoint run used the previous forcing
     fkind = kind;
     if (kind == NS_FORCE_NONE) return;
     fkmin = kfmin; fkmax = kfmax; feps = eps; ftcorr = tcorr; fseed = seed;
@@ -1278,13 +1288,11 @@ struct Solver : SolverBase {
     }
   }
 
-  void set_velocity(const double* u) override {
-    carry_step = -1;  // the mixed fields / state / forcing record change here
-    const size_t n = 3 * (size_t)N * N * N;
-    T* rin = reinterpret_cast<T*>(mixed[0]);  // 5 N^3 reals >= 3 N^3
-    to_device(u, rin, n);
+  // physical reals [3][N][N][N] of T on the device -> wscale P T F(u) (unnormalised r2c of
+  // x and y, z in the pencil; projection, truncation and k = 0 removed) into dst
+  void r2c_project(const T* rin, cpx<T>* dst, double wscale) {
     SlabArgs<T> a = slab_args();
-    a.rio = rin;
+    a.rio = const_cast<T*>(rin);
     a.Ft = Ft[0];
     a.xmode = XMODE_R2C;
     for (int z0 = 0; z0 < N; z0 += G) {
@@ -1296,22 +1304,17 @@ struct Solver : SolverBase {
     LAUNCH_CHECK();
     PencilArgs<T> p = pencil_args(MODE_PROJECT);
     p.shell = nullptr;
-    p.nF = 1; p.F[0] = Ft[0]; p.wF[0] = (T)(1.0 / ((double)N * N * N));
+    p.nF = 1; p.F[0] = Ft[0]; p.wF[0] = (T)wscale;
+    p.state = dst;
     pencil(p);
-    sync_check();
   }
-
-  void get_velocity(double* u) override { to_physical(state, u); }
-
-  // spectral [3][N][N][M] -> physical host [3][N][N][N] (inverse z, y, x transforms)
-  void to_physical(const cpx<T>* src, double* u) {
-    carry_step = -1;  // the mixed fields / state / forcing record change here
+  // spectral src -> physical reals [3][N][N][N] of T on the device (inverse z, y, x)
+  void c2r(const cpx<T>* src, T* rout) {
     PencilArgs<T> p = pencil_args(MODE_INIT);
     p.shell = nullptr;
     p.src = src;
     p.nOut = 1; p.out[0] = mixed[0];
     pencil(p);
-    T* rout = reinterpret_cast<T*>(Ft[0]);  // 3 N^3 reals
     SlabArgs<T> a = slab_args();
     a.mixed = mixed[0];
     a.rio = rout;
@@ -1323,6 +1326,23 @@ struct Solver : SolverBase {
       k_xrow<T><<<(a.G * N + RX - 1) / RX, bdX, smX, st>>>(a);
     }
     LAUNCH_CHECK();
+  }
+
+  void set_velocity(const double* u) override {
+    carry_step = -1;  // the mixed fields / state / forcing record change here
+    T* rin = reinterpret_cast<T*>(mixed[0]);  // 5 N^3 reals >= 3 N^3
+    to_device(u, rin, 3 * (size_t)N * N * N);
+    r2c_project(rin, state, 1.0 / ((double)N * N * N));
+    sync_check();
+  }
+
+  void get_velocity(double* u) override { to_physical(state, u); }
+
+  // spectral [3][N][N][M] -> physical host [3][N][N][N] (inverse z, y, x transforms)
+  void to_physical(const cpx<T>* src, double* u) {
+    carry_step = -1;  // the mixed fields / state / forcing record change here
+    T* rout = reinterpret_cast<T*>(Ft[0]);  // 3 N^3 reals
+    c2r(src, rout);
     to_host(rout, u, 3 * (size_t)N * N * N);
     sync_check();
   }
@@ -1486,25 +1506,24 @@ struct Solver : SolverBase {
     LAUNCH_CHECK();
   }
 
-  void vjp(const double* u0, int nsteps, double dt, int ckpt, int loss, double* Lout,
-           double* grad) override {
-    carry_step = -1;  // the mixed fields / state / forcing record change here
+  // Work vectors and tables of an adjoint run of nsteps steps with a checkpoint every ckpt
+  // steps (kept by the context; a tape_forward leaves them for tape_backward).
+  struct Tape {
+    bool valid = false;
+    int nsteps = 0, ckpt = 0;
+    double dt = 0.0;
+  } tape;
+  void adj_alloc(int nsteps, int ckpt) {
     const size_t vb = 3 * F1 * sizeof(cpx<T>);
-    const int nseg_states = ckpt;
     const int nck = (nsteps + ckpt - 1) / ckpt + 1;
-    const int nvec = 12 + nseg_states + nck;
+    const int nvec = 12 + ckpt + nck + 1;  // work, segment states, checkpoints, S_T
     if ((int)adj.size() < nvec) {
-      for (int i = 0; i < 2; ++i) {
-      if (ss[i]) cudaStreamDestroy(ss[i]);
-      if (ev_join[i]) cudaEventDestroy(ev_join[i]);
-    }
-    if (ev_fork) cudaEventDestroy(ev_fork);
-    for (auto* p : adj) cudaFree(p);
+      for (auto* p : adj) cudaFree(p);
       adj.assign(nvec, nullptr);
       for (int i = 0; i < nvec; ++i) CUDA_TRY(cudaMalloc(&adj[i], vb));
-      if (!mixedB) CUDA_TRY(cudaMalloc(&mixedB, 5 * F1 * sizeof(cpx<T>)));
-      if (!FtB) CUDA_TRY(cudaMalloc(&FtB, 3 * F1 * sizeof(cpx<T>)));
     }
+    if (!mixedB) CUDA_TRY(cudaMalloc(&mixedB, 5 * F1 * sizeof(cpx<T>)));
+    if (!FtB) CUDA_TRY(cudaMalloc(&FtB, 3 * F1 * sizeof(cpx<T>)));
     if (fkind != NS_FORCE_NONE) {
       cudaFree(shS); cudaFree(shR); cudaFree(ftab);
       shS = shR = ftab = nullptr;
@@ -1512,22 +1531,10 @@ struct Solver : SolverBase {
       CUDA_TRY(cudaMalloc(&shR, 3 * (size_t)fDn() * sizeof(cpx<T>)));
       CUDA_TRY(cudaMalloc(&ftab, 3 * (size_t)fDn() * sizeof(cpx<T>)));
     }
-    cpx<T>* N0 = vec(0);
-    cpx<T>* N1 = vec(1);
-    cpx<T>* S1 = vec(2);
-    cpx<T>* lam = vec(3);
-    cpx<T>* mu = vec(4);
-    cpx<T>* rho = vec(5);
-    cpx<T>* sig = vec(6);
-    cpx<T>* rs = vec(7);
-    cpx<T>* J = vec(8);
-    cpx<T>* tA = vec(9);
-    cpx<T>* tB = vec(10);
-    cpx<T>* tmp = vec(11);
-    cpx<T>** seg = &adj[12];
-    cpx<T>** ck = &adj[12 + nseg_states];
-
-    set_velocity(u0);
+  }
+  // shift tables of steps 0 .. nsteps-1 (context seed, step counter from 0), forcing record
+  // over [0, nsteps dt]; the step times
+  std::vector<double> adj_tables(int nsteps, double dt) {
     set_dt(dt);
     const double dx = 2.0 * M_PI / N;
     const bool approx = c->p.scheme == NS_RK2_PS_APPROX;
@@ -1542,39 +1549,68 @@ struct Solver : SolverBase {
     std::vector<double> times(nsteps + 1, 0.0);
     for (int n = 0; n < nsteps; ++n) times[n + 1] = times[n] + dt;
     if (fkind != NS_FORCE_NONE) prepare_forcing(0.0, times[nsteps]);
-
-    auto fwd = [&](const cpx<T>* S0, cpx<T>* Sout, int n) {
-      nl_eval(S0, shift_tab(2 * n), N0);
-      add_forcing(S0, times[n], N0);
-      ew(EW_ROG_S1, S0, N0, nullptr, S1);
-      nl_eval(S1, shift_tab(2 * n + 1), N1);
-      add_forcing(S1, times[n] + dt, N1);
-      ew(EW_ROG_SN, S0, N0, N1, Sout);
-    };
-
-    // forward sweep with checkpoints every ckpt steps
+    return times;
+  }
+  // one forward step of the adjoint's scheme (the same arithmetic as the stepping kernels,
+  // as separate evaluations): S0 -> Sout, stage state in S1
+  void adj_step(const cpx<T>* S0, cpx<T>* Sout, int n, double dt, const std::vector<double>& times) {
+    cpx<T>* N0 = vec(0);
+    cpx<T>* N1 = vec(1);
+    cpx<T>* S1 = vec(2);
+    nl_eval(S0, shift_tab(2 * n), N0);
+    add_forcing(S0, times[n], N0);
+    ew(EW_ROG_S1, S0, N0, nullptr, S1);
+    nl_eval(S1, shift_tab(2 * n + 1), N1);
+    add_forcing(S1, times[n] + dt, N1);
+    ew(EW_ROG_SN, S0, N0, N1, Sout);
+  }
+  // forward sweep from `state` with the state kept every ckpt steps; leaves state = S_T
+  void adj_forward(int nsteps, double dt, int ckpt) {
+    carry_step = -1;  // the mixed fields / state / forcing record change here
+    adj_alloc(nsteps, ckpt);
+    const std::vector<double> times = adj_tables(nsteps, dt);
+    const size_t vb = 3 * F1 * sizeof(cpx<T>);
+    cpx<T>* tmp = vec(11);
+    cpx<T>** ck = &adj[12 + ckpt];
     CUDA_TRY(cudaMemcpyAsync(ck[0], state, vb, cudaMemcpyDeviceToDevice, st));
     CUDA_TRY(cudaMemcpyAsync(tmp, state, vb, cudaMemcpyDeviceToDevice, st));
     for (int n = 0; n < nsteps; ++n) {
-      fwd(tmp, tmp, n);
-      if ((n + 1) % ckpt == 0 && n + 1 < nsteps) {
+      adj_step(tmp, tmp, n, dt, times);
+      if ((n + 1) % ckpt == 0 && n + 1 < nsteps)
         CUDA_TRY(cudaMemcpyAsync(ck[(n + 1) / ckpt], tmp, vb, cudaMemcpyDeviceToDevice, st));
-      }
     }
     CUDA_TRY(cudaMemcpyAsync(state, tmp, vb, cudaMemcpyDeviceToDevice, st));
-    double E, eps;
-    energy(&E, &eps);
-    *Lout = loss == NS_LOSS_ENERGY ? E : eps;
-    if (loss == NS_LOSS_ENERGY)
-      ew(EW_SCALE, state, nullptr, nullptr, lam, 1.0);
-    else
-      ew(EW_LOSS, state, nullptr, nullptr, lam, c->p.nu);
-
-    // reverse sweep, segment by segment, recomputing the forward states of the segment
+    CUDA_TRY(cudaMemcpyAsync(adj[12 + ckpt + (nsteps + ckpt - 1) / ckpt + 1], tmp, vb,
+                             cudaMemcpyDeviceToDevice, st));  // S_T of the tape
+    tape.valid = true;
+    tape.nsteps = nsteps;
+    tape.ckpt = ckpt;
+    tape.dt = dt;
+    c->t = times[nsteps];
+    c->step = nsteps;
+  }
+  // reverse sweep: lam holds the cotangent of S_T on entry and that of S_0 on exit; the
+  // states of each segment are recomputed from its checkpoint
+  void adj_reverse(cpx<T>* lam) {
+    const int nsteps = tape.nsteps, ckpt = tape.ckpt;
+    const double dt = tape.dt;
+    const std::vector<double> times = adj_tables(nsteps, dt);  // (the tables may have changed)
+    const size_t vb = 3 * F1 * sizeof(cpx<T>);
+    cpx<T>* N0 = vec(0);
+    cpx<T>* S1 = vec(2);
+    cpx<T>* mu = vec(4);
+    cpx<T>* rho = vec(5);
+    cpx<T>* sig = vec(6);
+    cpx<T>* rs = vec(7);
+    cpx<T>* J = vec(8);
+    cpx<T>* tA = vec(9);
+    cpx<T>* tB = vec(10);
+    cpx<T>** seg = &adj[12];
+    cpx<T>** ck = &adj[12 + ckpt];
     for (int seg0 = ((nsteps - 1) / ckpt) * ckpt; seg0 >= 0; seg0 -= ckpt) {
       const int seg1 = seg0 + ckpt < nsteps ? seg0 + ckpt : nsteps;
       CUDA_TRY(cudaMemcpyAsync(seg[0], ck[seg0 / ckpt], vb, cudaMemcpyDeviceToDevice, st));
-      for (int n = seg0; n < seg1 - 1; ++n) fwd(seg[n - seg0], seg[n - seg0 + 1], n);
+      for (int n = seg0; n < seg1 - 1; ++n) adj_step(seg[n - seg0], seg[n - seg0 + 1], n, dt, times);
       for (int n = seg1 - 1; n >= seg0; --n) {
         const cpx<T>* S0 = seg[n - seg0];
         const cpx<T>* ta = shift_tab(2 * n);
@@ -1592,12 +1628,73 @@ struct Solver : SolverBase {
         ew(EW_LAMBDA, lam, mu, J, lam);
       }
     }
+  }
+  // cotangent of S_T of a built-in loss of the final state S (E: S; eps: 2 nu k^2 S)
+  void adj_loss_seed(int loss, const cpx<T>* S, cpx<T>* lam) {
+    if (loss == NS_LOSS_ENERGY)
+      ew(EW_SCALE, S, nullptr, nullptr, lam, 1.0);
+    else
+      ew(EW_LOSS, S, nullptr, nullptr, lam, c->p.nu);
+  }
+
+  void vjp(const double* u0, int nsteps, double dt, int ckpt, int loss, double* Lout,
+           double* grad) override {
+    set_velocity(u0);
+    adj_forward(nsteps, dt, ckpt);
+    cpx<T>* lam = vec(3);
+    double E, eps;
+    energy(&E, &eps);
+    *Lout = loss == NS_LOSS_ENERGY ? E : eps;
+    adj_loss_seed(loss, state, lam);
+    adj_reverse(lam);
     // dL/du0 = F^{-1}(lambda_0) / N^3 (the initial truncation and projection are
     // self-adjoint and lambda_0 already lies in their range)
+    cpx<T>* tmp = vec(11);
     ew(EW_SCALE, lam, nullptr, nullptr, tmp, 1.0 / ((double)N * N * N));
     to_physical(tmp, grad);
-    c->t = times[nsteps];
-    c->step = nsteps;
+    tape.valid = false;  // the work vectors were reused for the output
+  }
+
+  // Gradient of a loss on the final velocity u(T) = F^{-1}(S_T), given gT = dL/du(T): the
+  // cotangent of S_T is N^3 P T F(gT) (F: forward transform with the 1/N^3 factor; its
+  // adjoint for <a,b> = sum_k Re(conj(a).b) over the full spectrum is F^{-1} / N^3).
+  void vjp_state(const double* u0, int nsteps, double dt, int ckpt, const double* gT,
+                 double* grad) override {
+    set_velocity(u0);
+    adj_forward(nsteps, dt, ckpt);
+    cpx<T>* lam = vec(3);
+    T* rin = reinterpret_cast<T*>(mixed[0]);
+    to_device(gT, rin, 3 * (size_t)N * N * N);
+    r2c_project(rin, lam, 1.0);
+    adj_reverse(lam);
+    cpx<T>* tmp = vec(11);
+    ew(EW_SCALE, lam, nullptr, nullptr, tmp, 1.0 / ((double)N * N * N));
+    to_physical(tmp, grad);
+    tape.valid = false;
+  }
+
+  // device-buffer forms (the autograd path): u0, uT [3][N][N][N] reals of T on the device
+  void tape_forward(const void* u0, int nsteps, double dt, int ckpt, void* uT) override {
+    carry_step = -1;
+    r2c_project(static_cast<const T*>(u0), state, 1.0 / ((double)N * N * N));
+    adj_forward(nsteps, dt, ckpt);
+    c2r(state, static_cast<T*>(uT));
+    sync_check();
+  }
+  // gT: the cotangent of u(T) (device reals of T), or null for the built-in loss `loss`
+  void tape_backward(const void* gT, int loss, void* grad) override {
+    if (!tape.valid) throw NsError{NS_ERR_STATE, "no adjoint tape: call ns_tape_forward first"};
+    carry_step = -1;
+    cpx<T>* lam = vec(3);
+    if (gT)
+      r2c_project(static_cast<const T*>(gT), lam, 1.0);
+    else
+      adj_loss_seed(loss, adj[12 + tape.ckpt + (tape.nsteps + tape.ckpt - 1) / tape.ckpt + 1], lam);
+    adj_reverse(lam);
+    cpx<T>* tmp = vec(11);
+    ew(EW_SCALE, lam, nullptr, nullptr, tmp, 1.0 / ((double)N * N * N));
+    c2r(tmp, static_cast<T*>(grad));
+    sync_check();
   }
 
   void energy(double* E, double* eps) override {
@@ -2041,6 +2138,43 @@ int ns_vjp(ns_ctx* c, const double* u0, int nsteps, double dt, int ckpt_every, i
       return fail(c, NS_ERR_INVALID_ARG, "need nsteps >= 1, ckpt_every >= 1, dt > 0 and a known loss");
     c->solver->vjp(u0, nsteps, dt, ckpt_every, loss, loss_out, grad_u0_out);
     c->have_state = true;
+    return (int)NS_OK;
+  });
+}
+
+int ns_vjp_state(ns_ctx* c, const double* u0, int nsteps, double dt, int ckpt_every,
+                 const double* gT, double* grad_u0_out) {
+  return guarded(c, [&]() {
+    if (!u0 || !gT || !grad_u0_out) return fail(c, NS_ERR_INVALID_ARG, "NULL argument");
+    if (c->p.scheme != NS_RK2_PS_RANDOM && c->p.scheme != NS_RK2_PS_APPROX)
+      return fail(c, NS_ERR_INVALID_ARG, "ns_vjp_state supports the RK2 phase-shift random/approx schemes");
+    if (nsteps < 1 || ckpt_every < 1 || !(dt > 0.0))
+      return fail(c, NS_ERR_INVALID_ARG, "need nsteps >= 1, ckpt_every >= 1 and dt > 0");
+    c->solver->vjp_state(u0, nsteps, dt, ckpt_every, gT, grad_u0_out);
+    c->have_state = true;
+    return (int)NS_OK;
+  });
+}
+
+int ns_tape_forward(ns_ctx* c, const void* u0, int nsteps, double dt, int ckpt_every, void* uT) {
+  return guarded(c, [&]() {
+    if (!u0 || !uT) return fail(c, NS_ERR_INVALID_ARG, "NULL argument");
+    if (c->p.scheme != NS_RK2_PS_RANDOM && c->p.scheme != NS_RK2_PS_APPROX)
+      return fail(c, NS_ERR_INVALID_ARG, "ns_tape_forward supports the RK2 phase-shift random/approx schemes");
+    if (nsteps < 1 || ckpt_every < 1 || !(dt > 0.0))
+      return fail(c, NS_ERR_INVALID_ARG, "need nsteps >= 1, ckpt_every >= 1 and dt > 0");
+    c->solver->tape_forward(u0, nsteps, dt, ckpt_every, uT);
+    c->have_state = true;
+    return (int)NS_OK;
+  });
+}
+
+int ns_tape_backward(ns_ctx* c, const void* gT, int loss, void* grad_u0) {
+  return guarded(c, [&]() {
+    if (!grad_u0) return fail(c, NS_ERR_INVALID_ARG, "NULL argument");
+    if (!gT && loss != NS_LOSS_DISSIPATION && loss != NS_LOSS_ENERGY)
+      return fail(c, NS_ERR_INVALID_ARG, "unknown loss");
+    c->solver->tape_backward(gT, loss, grad_u0);
     return (int)NS_OK;
   });
 }

@@ -227,6 +227,15 @@ struct PencilOutSrc {
   }
 };
 
+// 1 / k^2 of the projection: FP32 uses the fast division intrinsic (within 2 ulp, far below
+// the FP32 path's per-step error), FP64 the correctly rounded division.
+template <typename T>
+__device__ __forceinline__ T recip_k2(int k2);
+template <>
+__device__ __forceinline__ float recip_k2<float>(int k2) { return __fdividef(1.0f, (float)k2); }
+template <>
+__device__ __forceinline__ double recip_k2<double>(int k2) { return 1.0 / (double)k2; }
+
 // ---- spectral stage at one mode (Sec. 4.1, 4.2, 6.1) ----------------------------------
 // nv: de-shifted, weighted transform of u x omega at the mode: N(0) = 0, truncation T,
 // Leray projection P, then the forcing term O (added on the modes of the forcing table).
@@ -238,7 +247,7 @@ __device__ __forceinline__ void project_point(const PencilArgs<T>& a, int kx, in
   if (keep) {
     const cpx<T> v0 = nv[0], v1 = nv[1], v2 = nv[2];
     const T fx = (T)kx, fy = (T)ky, fz = (T)kz;
-    const T ik2 = T(1) / (T)k2;
+    const T ik2 = recip_k2<T>(k2);
     const cpx<T> kd = mk<T>(fx * v0.x + fy * v1.x + fz * v2.x, fx * v0.y + fy * v1.y + fz * v2.y);
     nv[0] = v0 - (fx * ik2) * kd;
     nv[1] = v1 - (fy * ik2) * kd;
@@ -257,12 +266,13 @@ __device__ __forceinline__ void project_point(const PencilArgs<T>& a, int kx, in
 // RK stage combine of component c at one mode (modes of PencilMode).  s0: the value read
 // from src (INIT), acc (RK4_4) or state (all other modes); s1: acc for RK4_2 / RK4_3.
 // Performs the mode's global writes and returns S_next.
+// mode: the pencil's stage (a.mode, or a compile-time constant in the specialised kernels)
 template <typename T, class MP>
 __device__ __forceinline__ cpx<T> stage_combine(const PencilArgs<T>& a, int c, size_t g, cpx<T> n,
-                                                cpx<T> s0, cpx<T> s1, T E1, T Eh) {
+                                                cpx<T> s0, cpx<T> s1, T E1, T Eh, int mode) {
   const T dt = a.dt, hdt = T(0.5) * a.dt;
   (void)c;
-  switch (a.mode) {
+  switch (mode) {
     case MODE_INIT:
       return s0;
     case MODE_RK2_1:
@@ -405,10 +415,12 @@ __device__ __forceinline__ void tile_energy_store(double* epart, T e, T d) {
 // transformed in place (the last stage de-shifting and weighting), then one pass per mode
 // applies N(0) = 0, truncation, projection and forcing and the RK stage combine of all three
 // components, leaving S_next (shifted for the output when there is one output) in the tiles.
-template <typename T, int N, class MP, bool EP>
+// MC: the stage mode fixed at compile time (-1: a.mode at run time)
+template <typename T, int N, class MP, bool EP, int MC = -1>
 __device__ __forceinline__ void pencil_spectral_one(const PencilArgs<T>& a, cpx<T>* buf, cpx<T>* tws,
                                                     int iy, int x0, int nOut, bool tz, T& eacc,
                                                     T& dacc) {
+  const int mode = MC >= 0 ? MC : a.mode;
   using C = K2Cfg<T, N>;
   constexpr int M = N / 2, TX = C::TX, NT = C::NTP, tile = lf_rows<T, C::TX>(N) * TX;
   constexpr int PER = (tile + NT - 1) / NT;
@@ -418,8 +430,8 @@ __device__ __forceinline__ void pencil_spectral_one(const PencilArgs<T>& a, cpx<
   const bool act = threadIdx.x < NT;
   const int line = threadIdx.x % TX, kx = x0 + line;
   const int iz0 = threadIdx.x / TX;
-  const bool rd0 = a.mode != MODE_NL && a.mode != MODE_PROJECT;
-  const cpx<T>* base0 = a.mode == MODE_RK4_4 ? a.acc : a.state;
+  const bool rd0 = mode != MODE_NL && mode != MODE_PROJECT;
+  const cpx<T>* base0 = mode == MODE_RK4_4 ? a.acc : a.state;
   if (!tz)
     for (int c = 0; c < 3; ++c) stage_col_tile<T, N, TX, NT>(buf + c * tile, a.F[0] + c * fstride, iy, x0);
   cp_async_commit();
@@ -445,7 +457,7 @@ __device__ __forceinline__ void pencil_spectral_one(const PencilArgs<T>& a, cpx<
   const bool pre = nOut == 1 && a.osh[0] != nullptr;
   cpx<T> oxy = mk<T>(1, 0);
   if (pre) oxy = MP::ld(&a.osh[0][kx]) * MP::ld(&a.osh[0][N + iy]);
-  const bool useE = a.mode != MODE_INIT && a.mode != MODE_NL && a.mode != MODE_PROJECT;
+  const bool useE = mode != MODE_INIT && mode != MODE_NL && mode != MODE_PROJECT;
   T e1xy = 1, ehxy = 1;
   if (useE) {
     e1xy = a.ifac[kx] * a.ifac[iy];
@@ -457,7 +469,7 @@ __device__ __forceinline__ void pencil_spectral_one(const PencilArgs<T>& a, cpx<
   }
   if (act) {
     constexpr int CHK = PER < NS_PENCIL_CHK ? PER : NS_PENCIL_CHK;  // modes whose state loads are in flight together
-    const bool rd1 = a.mode == MODE_RK4_2 || a.mode == MODE_RK4_3;
+    const bool rd1 = mode == MODE_RK4_2 || mode == MODE_RK4_3;
     const size_t gxy = (size_t)iy * M + kx;
     for (int i0 = 0; i0 < PER; i0 += CHK) {
       cpx<T> s0[3][CHK];  // (the RK4 accumulator, read by two modes only, is loaded on use)
@@ -498,7 +510,7 @@ __device__ __forceinline__ void pencil_spectral_one(const PencilArgs<T>& a, cpx<
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
           const cpx<T> s1 = rd1 ? MP::ldw(&a.acc[c * fstride + g]) : mk<T>(0, 0);
-          cpx<T> sn = stage_combine<T, MP>(a, c, c * fstride + g, nv[c], s0[c][j], s1, E1, Eh);
+          cpx<T> sn = stage_combine<T, MP>(a, c, c * fstride + g, nv[c], s0[c][j], s1, E1, Eh, mode);
           shell_record<T, MP>(a, c, kx, ky, kz, sn);
           if constexpr (EP) m2 += sn.x * sn.x + sn.y * sn.y;
           if (pre) sn = sn * shz;
@@ -518,7 +530,7 @@ __device__ __forceinline__ void pencil_spectral_one(const PencilArgs<T>& a, cpx<
 // NFC, NOC: the number of inputs and outputs known at compile time (-1: read from the
 // arguments).  (1, 1) is every RK2, Rogallo and RK4 stage, (2, 2) the exact scheme's stage;
 // fixing them keeps those kernels free of register spills.
-template <typename T, int N, class MP, int NFC = -1, int NOC = -1, bool EP = false>
+template <typename T, int N, class MP, int NFC = -1, int NOC = -1, bool EP = false, int MC = -1>
 __device__ __forceinline__ void pencil_tile(const PencilArgs<T>& a, int tile_id, cpx<T>* buf) {
   using C = K2Cfg<T, N>;
   const int nF = NFC >= 0 ? NFC : a.nF, nOut = NOC >= 0 ? NOC : a.nOut;
@@ -544,7 +556,7 @@ __device__ __forceinline__ void pencil_tile(const PencilArgs<T>& a, int tile_id,
   const bool tz = nF > 0 && tt;                               // so its inputs are not transformed
   T eacc = 0, dacc = 0;  // energy sums of the written state (a.epart)
   if constexpr (NFC == 1) {
-    pencil_spectral_one<T, N, MP, EP>(a, buf, tws, iy, x0, nOut, tz, eacc, dacc);
+    pencil_spectral_one<T, N, MP, EP, MC>(a, buf, tws, iy, x0, nOut, tz, eacc, dacc);
   } else {
     const int nFe = tz ? 0 : nF;  // inputs that are transformed
     // 1) inputs: all three components staged asynchronously, then transformed in place
@@ -639,7 +651,7 @@ __device__ __forceinline__ void pencil_tile(const PencilArgs<T>& a, int tile_id,
             Eh = ehxy * a.ifac[N + iz];
           }
           const cpx<T> n = nFe > 0 ? bc(c)[e] : mk<T>(0, 0);
-          cpx<T> sn = stage_combine<T, MP>(a, c, g, n, s0[j], s1[j], E1, Eh);
+          cpx<T> sn = stage_combine<T, MP>(a, c, g, n, s0[j], s1[j], E1, Eh, a.mode);
           shell_record<T, MP>(a, c, kx, ky, kof(iz, N), sn);
           if (a.epart) {
             const int kz = kof(iz, N);
@@ -706,13 +718,14 @@ __device__ __forceinline__ void pencil_tile(const PencilArgs<T>& a, int tile_id,
 // the two-input variant holds 4 shared tiles (3 blocks per SM at most): it is given the
 // registers of 2 resident blocks rather than spill
 // EP: the one-input variant that also stores the tile's energy sums (a.epart non-null)
-template <typename T, int N, int NFC, int NOC, bool EP = false>
+// MC: the stage mode at compile time (the Rogallo stages) or -1 (a.mode)
+template <typename T, int N, int NFC, int NOC, bool EP = false, int MC = -1>
 __global__ void __launch_bounds__(K2Cfg<T, N>::NTP, (NFC == 2 || (NFC == 1 && NS_PENCIL_STAGE_STATE))
                                                          ? cmin(2, K2Cfg<T, N>::MINB_P)
                                                          : K2Cfg<T, N>::MINB_P)
     k2_pencil(PencilArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  pencil_tile<T, N, MemNC, NFC, NOC, EP>(a, blockIdx.x, reinterpret_cast<cpx<T>*>(smem_raw));
+  pencil_tile<T, N, MemNC, NFC, NOC, EP, MC>(a, blockIdx.x, reinterpret_cast<cpx<T>*>(smem_raw));
 }
 
 // ---- slab pass: y transforms --------------------------------------------------------
@@ -1066,6 +1079,7 @@ struct K2Entry {
   void (*pencil)(PencilArgs<T>) = nullptr;   // any number of inputs / outputs
   void (*pencil1)(PencilArgs<T>) = nullptr;  // one input, one output
   void (*pencil1e)(PencilArgs<T>) = nullptr; // same, also storing the tile's energy sums
+  void (*pencil1r[2])(PencilArgs<T>) = {nullptr, nullptr};  // one in, one out: ROG_1, ROG_2
   void (*pencil2)(PencilArgs<T>) = nullptr;  // two inputs, two outputs
   void (*yinv)(SlabArgs<T>) = nullptr;
   void (*yfwd)(SlabArgs<T>) = nullptr;
@@ -1094,6 +1108,11 @@ K2Entry<T> make_k2_entry() {
   // NS_PENCIL_VARIANTS=0 routes every pencil pass through the generic kernel (comparisons)
   e.pencil1 = NS_PENCIL_VARIANTS ? k2_pencil<T, N, 1, 1> : e.pencil;
   e.pencil1e = NS_PENCIL_VARIANTS ? k2_pencil<T, N, 1, 1, true> : e.pencil;
+#ifndef NS_PENCIL_MODE_VARIANTS
+#define NS_PENCIL_MODE_VARIANTS 1
+#endif
+  e.pencil1r[0] = NS_PENCIL_MODE_VARIANTS ? k2_pencil<T, N, 1, 1, false, MODE_ROG_1> : e.pencil1;
+  e.pencil1r[1] = NS_PENCIL_MODE_VARIANTS ? k2_pencil<T, N, 1, 1, false, MODE_ROG_2> : e.pencil1;
   e.pencil2 = NS_PENCIL_VARIANTS ? k2_pencil<T, N, 2, 2> : e.pencil;
   e.yinv = k2_yinv<T, N>;
   e.yfwd = k2_yfwd<T, N>;

@@ -91,3 +91,47 @@ def test_batch_rejects_unsupported_sizes(ns):
     with pytest.raises(ns.NSError) as e:
         ns.Batch([16], [0.01], [8.0], scheme=ns.RK4)
     assert e.value.code == 1
+
+
+def test_batch_graph_reuse_matches_oracle(ns):
+    # two calls with the same nsteps: the second replays the captured CUDA graph; every
+    # member must still follow its oracle trajectory (FP64)
+    Ns = [16, 32, 16]
+    nus = [0.01, 0.005, 0.02]
+    seeds = [11, 12, 13]
+    dts = [0.01, 0.008, 0.012]
+    us = members(Ns, seed0=60)
+    with ns.Batch(Ns, nus, [N / 2 for N in Ns], seeds=seeds, precision=ns.FP64) as b:
+        for i, u in enumerate(us):
+            b.set_velocity(i, u)
+        b.step(dts, 3)
+        b.step(dts, 3)  # same nsteps: graph replay
+        b.step(dts, 3)
+        got = [b.get_state(i) for i in range(len(Ns))]
+    for i, N in enumerate(Ns):
+        prob = sc.Problem(N, nus[i], N / 2)
+        ref, _ = sc.run(osp.set_velocity(us[i], N / 2), dts[i], 9, prob, sc.SCHEME_PS_RANDOM,
+                        seed=seeds[i])
+        assert rel(got[i], ref) < 1e-12, i
+
+
+def test_batch_fp32_members_match_oracle(ns, report):
+    # FP32 members of every size of the ensemble workload against the FP64 oracle
+    Ns = [32, 64, 96, 128]
+    nus = [1 / 1600] * len(Ns)
+    dts = [0.5 * 2 * np.pi / N / 2 for N in Ns]
+    us = [inputs.taylor_green_perturbed(N, 40 + i) for i, N in enumerate(Ns)]
+    with ns.Batch(Ns, nus, [N / 2 for N in Ns], seeds=[20 + i for i in range(len(Ns))],
+                  precision=ns.FP32) as b:
+        for i, u in enumerate(us):
+            b.set_velocity(i, u)
+        b.step(dts, 2)
+        b.step(dts, 2)  # graph replay
+        got = [b.get_state(i) for i in range(len(Ns))]
+    for i, N in enumerate(Ns):
+        prob = sc.Problem(N, nus[i], N / 2)
+        ref, _ = sc.run(osp.set_velocity(us[i], N / 2), dts[i], 4, prob, sc.SCHEME_PS_RANDOM,
+                        seed=20 + i)
+        err = rel(got[i], ref)
+        report("batch_member_N%d_4_steps_fp32" % N, err, 4 * 2e-5)
+        assert err < 4 * 2e-5, i  # four FP32 steps

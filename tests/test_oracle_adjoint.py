@@ -73,3 +73,51 @@ def test_gradient_matches_central_differences(forced):
         Lm, _ = ad.grad_final_dissipation(u0 - h * v, nsteps, dt, prob, 3, f, ckpt_every=100)
         fd = (Lp - Lm) / (2 * h)
         assert abs(fd - float(np.sum(g * v))) < 1e-6 * abs(fd)
+
+
+def test_grad_final_state_central_differences():
+    # L(u0) = sum_x gT . u(T): a linear functional of the final velocity (any loss's gradient
+    # at T enters the reverse sweep this way); FP64 central differences, h = 1e-4
+    from oracle import adjoint as ad
+    from oracle import forcing as fo
+    from oracle import schemes as sc
+    from oracle import spectral as sp
+    from paper_2603_08892_gb300 import inputs
+
+    N, nu, dt, nsteps = 8, 0.02, 0.02, 5
+    prob = sc.Problem(N, nu, N / 2)
+    u0 = inputs.hit_initial(N, 3)
+    rs = np.random.default_rng(4)
+    gT = rs.standard_normal(u0.shape)
+    f = fo.Forcing(N, 2.0, 3.0, 1.0, 0.05, seed=2)
+
+    def L(u):
+        S = sp.set_velocity(u, prob.kmax)
+        for n in range(nsteps):
+            S = sc.step_ps_random(S, dt, prob, __import__("oracle").rng.shift_alpha(9, n, N), n * dt, f)
+        return float(np.sum(gT * sp.inverse(S)))
+
+    g = ad.grad_final_state(u0, gT, nsteps, dt, prob, seed=9, forcing=f, ckpt_every=2)
+    h = 1e-4
+    for _ in range(3):
+        v = rs.standard_normal(u0.shape)
+        fd = (L(u0 + h * v) - L(u0 - h * v)) / (2 * h)
+        assert abs(fd - float(np.sum(g * v))) < 1e-7 * max(1.0, abs(fd))
+
+
+def test_grad_final_state_energy_equals_builtin_energy_gradient():
+    # E(T) = (1/2) mean_x |u(T)|^2 has dE/du(T) = u(T) / N^3; through the state cotangent it
+    # must give the same gradient as seeding the reverse sweep with dE/dS_T = S_T directly
+    from oracle import adjoint as ad
+    from oracle import schemes as sc
+    from oracle import spectral as sp
+    from paper_2603_08892_gb300 import inputs
+
+    N, nu, dt, nsteps = 8, 0.02, 0.02, 4
+    prob = sc.Problem(N, nu, N / 2)
+    u0 = inputs.hit_initial(N, 5)
+    S, _ = sc.run(sp.set_velocity(u0, prob.kmax), dt, nsteps, prob, sc.SCHEME_PS_RANDOM, seed=1)
+    gT = sp.inverse(S) / float(N) ** 3
+    g1 = ad.grad_final_state(u0, gT, nsteps, dt, prob, seed=1, ckpt_every=3)
+    _, g2 = ad._reverse(u0, nsteps, dt, prob, 1, None, 3, False, lambda S_: S_.copy())
+    assert np.abs(g1 - g2).max() < 1e-13 * np.abs(g2).max()
