@@ -272,6 +272,15 @@ int ns_batch_set_spin_limit(ns_batch* b, long long polls);
 int ns_batch_test_stall(ns_batch* b, int on);
 /* CTAs of the last persistent launch (diagnostics). */
 int ns_batch_grid(ns_batch* b);
+/* Schedule of the persistent launch: gran tiles per work-list ticket (the ticket, the
+ * bounded wait and the completion fence are paid once per gran tiles) and ctas_per_sm CTAs
+ * per SM (0: as many as fit).  The first ns_batch_step tunes both on the ensemble (each
+ * candidate times one step; the members' states, times and step counters are saved before
+ * and restored after) unless ns_batch_set_schedule was called, NS_BATCH_SCHEDULE="g,q" is set
+ * or NS_AUTOTUNE=0.  Results do not depend on the schedule.  NS_ERR_INVALID_ARG for gran < 1
+ * or ctas_per_sm < 0. */
+int ns_batch_set_schedule(ns_batch* b, int gran, int ctas_per_sm);
+int ns_batch_schedule(ns_batch* b, int* gran, int* ctas_per_sm);
 
 /* Nonlinear term N~_D(S) like ns_nonlinear, on device buffers, without allocating any device
  * memory.  No counterpart in the paper: it serves callers that cannot call cudaMalloc --

@@ -105,6 +105,9 @@ _batch_energy = _sig("ns_batch_energy", ctypes.c_int, [_vp, _dp, _dp])
 _batch_spin = _sig("ns_batch_set_spin_limit", ctypes.c_int, [_vp, ctypes.c_longlong])
 _batch_stall = _sig("ns_batch_test_stall", ctypes.c_int, [_vp, ctypes.c_int])
 _batch_grid = _sig("ns_batch_grid", ctypes.c_int, [_vp])
+_batch_set_schedule = _sig("ns_batch_set_schedule", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int])
+_batch_schedule = _sig("ns_batch_schedule", ctypes.c_int,
+                       [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)])
 PROF_KINDS = {"k_pencil": 0, "k_yinv": 1, "k_xrow": 2, "k_yfwd": 3, "slab_pass": 4, "k_slabpipe": 5,
               "k_slabcl": 6}
 
@@ -116,7 +119,8 @@ EXPORTED = ["ns_init", "ns_init_ex", "ns_init_error", "ns_destroy", "ns_last_err
             "ns_model_bytes_per_step", "ns_nl1d", "ns_fma_peak", "ns_profile", "ns_profile_read", "ns_nonlinear_noalloc", "ns_vjp", "ns_vjp_state",
             "ns_tape_forward", "ns_tape_backward", "ns_batch_init", "ns_batch_destroy", "ns_batch_last_error",
             "ns_batch_member", "ns_batch_set_velocity", "ns_batch_get_state", "ns_batch_step",
-            "ns_batch_energy", "ns_batch_set_spin_limit", "ns_batch_test_stall", "ns_batch_grid"]
+            "ns_batch_energy", "ns_batch_set_spin_limit", "ns_batch_test_stall", "ns_batch_grid",
+            "ns_batch_set_schedule", "ns_batch_schedule"]
 
 
 class NSError(RuntimeError):
@@ -422,3 +426,12 @@ class Batch:
 
     def grid(self):
         return _batch_grid(self._h)
+
+    def set_schedule(self, gran, ctas_per_sm=0):
+        """Tiles per work-list ticket and CTAs per SM of the persistent launch (no tuning)."""
+        self._check(_batch_set_schedule(self._h, gran, ctas_per_sm))
+
+    def schedule(self):
+        g, q = ctypes.c_int(), ctypes.c_int()
+        self._check(_batch_schedule(self._h, ctypes.byref(g), ctypes.byref(q)))
+        return g.value, q.value

@@ -269,6 +269,9 @@ struct Solver : SolverBase {
   // autotuner where the size has the kernel and the device can hold its clusters
   bool clus = false;
   int cl_var = 1;                  // thread-count variant of the cluster kernel
+  // compiled tile alternatives chosen by the autotuner (K2Cfg variant bits: 1 pencil width,
+  // 2 inverse-y width, 4 x rows, 8 forward-y width; 0 = every default)
+  int vsel = 0;
   int cl_ncl = -1;                 // clusters the device holds at once (-1: not yet queried)
   long long cl_spin = 1ll << 20;   // polls of its bounded TMA wait
   std::vector<std::pair<const void*, CUtensorMap>> cl_maps;  // TMA maps of the mixed buffers
@@ -423,6 +426,13 @@ struct Solver : SolverBase {
       allow(k2.yinv, k2.smYI);
       allow(k2.yfwd, k2.smY);
       allow(k2.xrow, k2.smX);
+      if (k2.has_alt) {
+        allow(k2.alt.pencil1r[0], k2.alt.smP1);
+        allow(k2.alt.pencil1r[1], k2.alt.smP1);
+        allow(k2.alt.yinv, k2.alt.smYI);
+        allow(k2.alt.yfwd, k2.alt.smY);
+        allow(k2.alt.xrow, k2.alt.smX);
+      }
       for (int v = 0; v < 2; ++v)
         if (k2.slabcl[v]) {
           allow(k2.slabcl[v], k2.smCL);
@@ -653,19 +663,28 @@ struct Solver : SolverBase {
       a.scr = scr + (two ? (size_t)(gi & 1) * 6 * G * N * M : 0);  // double-buffered scratch
       cudaEvent_t e = prof_begin(NS_PROF_YINV, s);
       if (use2)
-        k2.yinv<<<dim3(M / k2.TYI, a.G), k2.NTYI, k2.smYI, s>>>(a);
+        if (vsel & 2)
+          k2.alt.yinv<<<dim3(M / k2.alt.TYI, a.G), k2.alt.NTYI, k2.alt.smYI, s>>>(a);
+        else
+          k2.yinv<<<dim3(M / k2.TYI, a.G), k2.NTYI, k2.smYI, s>>>(a);
       else
         k_yinv<T><<<dim3(M / TY, a.G), bdYi, smYi, s>>>(a);
       prof_end(e, s);
       e = prof_begin(NS_PROF_XROW, s);
       if (use2)
-        k2.xrow<<<(a.G * N + k2.RX - 1) / k2.RX, k2.NTX, k2.smX, s>>>(a);
+        if (vsel & 4)
+          k2.alt.xrow<<<(a.G * N + k2.alt.RX - 1) / k2.alt.RX, k2.alt.NTX, k2.alt.smX, s>>>(a);
+        else
+          k2.xrow<<<(a.G * N + k2.RX - 1) / k2.RX, k2.NTX, k2.smX, s>>>(a);
       else
         k_xrow<T><<<(a.G * N + RX - 1) / RX, bdX, smX, s>>>(a);
       prof_end(e, s);
       e = prof_begin(NS_PROF_YFWD, s);
       if (use2)
-        k2.yfwd<<<dim3(M / k2.TY, a.G), k2.NTY, k2.smY, s>>>(a);
+        if (vsel & 8)
+          k2.alt.yfwd<<<dim3(M / k2.alt.TY, a.G), k2.alt.NTY, k2.alt.smY, s>>>(a);
+        else
+          k2.yfwd<<<dim3(M / k2.TY, a.G), k2.NTY, k2.smY, s>>>(a);
       else
         k_yfwd<T><<<dim3(M / TY, a.G), bdYf, smYf, s>>>(a);
       prof_end(e, s);
@@ -696,7 +715,10 @@ struct Solver : SolverBase {
 
   void pencil(const PencilArgs<T>& a) {
     cudaEvent_t e = prof_begin(NS_PROF_PENCIL);
-    if (use2)
+    const bool rog = a.nF == 1 && a.nOut == 1 && !a.epart && (a.mode == MODE_ROG_1 || a.mode == MODE_ROG_2);
+    if (use2 && rog && (vsel & 1))  // the autotuner's alternative pencil width
+      k2.alt.pencil1r[a.mode == MODE_ROG_1 ? 0 : 1]<<<(M / k2.alt.TX) * N, k2.alt.NTP, k2.alt.smP1, st>>>(a);
+    else if (use2)
       (a.nF == 1 && a.nOut == 1   ? (a.epart                  ? k2.pencil1e
                                      : a.mode == MODE_ROG_1 ? k2.pencil1r[0]
                                      : a.mode == MODE_ROG_2 ? k2.pencil1r[1]
@@ -905,6 +927,7 @@ struct Solver : SolverBase {
   // cache file; NS_SLAB_PLANES=g forces a group size, NS_SLAB_STREAMS=1|2 the stream count,
   // NS_SLAB_PIPE=1 the pipeline (ring NS_PIPE_RING, lag NS_PIPE_LAG) and =0 excludes it;
   // NS_SLAB_CLUSTER=1 the cluster pass (thread variant NS_CL_VARIANT) and =0 excludes it;
+  // NS_TILE_VARIANT=bits forces the compiled tile alternatives of the kernel families;
   // NS_PIPE_SPIN bounds its waits, NS_PIPE_TEST_STALL=1 makes them unsatisfiable (test hook).
   static std::string cache_path() {
     const char* e = std::getenv("NS_AUTOTUNE_CACHE");
@@ -1001,6 +1024,9 @@ struct Solver : SolverBase {
     if (const char* e = std::getenv("NS_PIPE_SPIN")) pipe_spin = std::max(1ll, std::atoll(e));
     if (const char* e = std::getenv("NS_PIPE_TEST_STALL")) pipe_stall = std::atoi(e) ? 1 : 0;
     if (const char* e = std::getenv("NS_CL_SPIN")) cl_spin = std::max(1ll, std::atoll(e));
+    // NS_TILE_VARIANT=bits forces the compiled tile alternatives (bits of K2Cfg's variant)
+    const char* fv = std::getenv("NS_TILE_VARIANT");
+    if (fv && *fv) vsel = (use2 && k2.has_alt) ? (std::atoi(fv) & 15) : 0;
     const char* fcl = std::getenv("NS_SLAB_CLUSTER");
     const bool can_cl = use2 && k2.slabcl[0] && !(fcl && std::string(fcl) == "0") && cl_clusters() > 0;
     if (fcl && std::string(fcl) == "1" && can_cl) {  // forced cluster pass (NS_CL_VARIANT 0 or 1)
@@ -1028,12 +1054,20 @@ struct Solver : SolverBase {
     const char* en = std::getenv("NS_AUTOTUNE");
     if (en && std::string(en) == "0") return;
     if (Gmax <= 1 || N < 128) return;  // small grids: one group holds every plane
+    const bool can_alt = use2 && k2.has_alt && !(fv && *fv);
     const std::string path = cache_path(),
-                      key = tune_key() + (can_pipe ? "|g4p" : "|g4") + (can_cl ? "c" + std::to_string(k2.CLS) : "");
+                      key = tune_key() + (can_pipe ? "|g4p" : "|g4") + (can_cl ? "c" + std::to_string(k2.CLS) : "") +
+                            (can_alt ? "|v" + std::to_string(k2.alt.TX) + "," + std::to_string(k2.alt.TYI) + "," +
+                                           std::to_string(k2.alt.RX) + "," + std::to_string(k2.alt.TY)
+                                     : "");
     int g = 0;
-    if (cache_lookup(path, key, &g) && g / 4 >= 1 && g / 4 <= Gmax && ((g & 3) <= 2 || can_cl)) {
-      set_mode(g / 4, g & 3);
-      return;
+    if (cache_lookup(path, key, &g)) {  // value = 4096 vsel + 4 G + mode
+      const int gm = g % 4096, vs = g / 4096;
+      if (gm / 4 >= 1 && gm / 4 <= Gmax && ((gm & 3) <= 2 || can_cl) && (vs == 0 || can_alt)) {
+        set_mode(gm / 4, gm & 3);
+        if (can_alt) vsel = vs;
+        return;
+      }
     }
     std::vector<std::pair<int, int>> cand;  // (G or ring, mode)
     for (int q : {8, 12, 16, 19, 24, 28, 32, 38, 43, 48, 57, 64, 76, 96, 128, 171, 256, 384, 512, 768}) {
@@ -1070,13 +1104,63 @@ struct Solver : SolverBase {
       }
     }
     sync_check();  // a pipeline candidate that gave up reports here
-    prof.on = pon;
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
     pipe = false;
     clus = false;
     set_mode(bestc.first, bestc.second);
-    cache_store(path, key, 4 * bestc.first + bestc.second);
+    // the compiled tile alternatives, one kernel family at a time: the slab kernels in the
+    // chosen slab mode (three-kernel modes only), the pencil on the Rogallo stages
+    if (can_alt) {
+      auto time_slab = [&]() {
+        slab(mixed[0], Ft[0]);
+        CUDA_TRY(cudaEventRecord(e0, st));
+        for (int r = 0; r < 8; ++r) slab(mixed[0], Ft[0]);
+        CUDA_TRY(cudaEventRecord(e1, st));
+        CUDA_TRY(cudaEventSynchronize(e1));
+        float ms = 0;
+        CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+        return ms;
+      };
+      if (!pipe && !clus) {
+        float base = time_slab();
+        for (int bit : {2, 4, 8}) {
+          vsel ^= bit;
+          const float ms = time_slab();
+          if (ms < base) base = ms;
+          else vsel ^= bit;
+        }
+      }
+      // pencil: both Rogallo stages on the work buffers (acc as the state, Ft[0] as the input,
+      // mixed[0] as the output; all recomputed before any step uses them), zero inputs
+      CUDA_TRY(cudaMemsetAsync(acc, 0, 3 * F1 * sizeof(cpx<T>), st));
+      CUDA_TRY(cudaMemsetAsync(Ft[0], 0, 3 * F1 * sizeof(cpx<T>), st));
+      cpx<T>* pout = mixed[0];
+      auto time_pencil = [&]() {
+        PencilArgs<T> a = pencil_args(MODE_ROG_1);
+        a.shell = nullptr;
+        a.state = acc;
+        a.nF = 1; a.F[0] = Ft[0]; a.wF[0] = (T)1;
+        a.nOut = 1; a.out[0] = pout;
+        pencil(a);
+        CUDA_TRY(cudaEventRecord(e0, st));
+        for (int r = 0; r < 8; ++r) {
+          a.mode = (r & 1) ? MODE_ROG_2 : MODE_ROG_1;
+          pencil(a);
+        }
+        CUDA_TRY(cudaEventRecord(e1, st));
+        CUDA_TRY(cudaEventSynchronize(e1));
+        float ms = 0;
+        CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+        return ms;
+      };
+      const float p0 = time_pencil();
+      vsel ^= 1;
+      if (time_pencil() >= p0) vsel ^= 1;
+      sync_check();
+    }
+    prof.on = pon;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cache_store(path, key, 4096 * vsel + 4 * bestc.first + bestc.second);
   }
 
   // ---- schemes ------------------------------------------------------------------------

@@ -2,7 +2,106 @@
 // persistent kernel); the FP64 kernel is compiled in ns_batch_f64.cu.
 #include "ns_batch.cuh"
 
+#include <cstdio>
+#include <cstdlib>
+
 int ns_batch_step_f64(ns_batch* b, const double* dt, int nsteps);
+
+namespace {
+
+int batch_step_any(ns_batch* b, const double* dt, int nsteps) {
+  return b->precision == NS_FP32 ? batch_step_t<float>(b, dt, nsteps) : ns_batch_step_f64(b, dt, nsteps);
+}
+
+// Schedule tuner of the persistent launch: the work-list granularity (tiles per ticket) and
+// the CTAs per SM are timed on this ensemble, one step per candidate after an untimed one;
+// the members' states, times and step counters are saved before and restored after, so the
+// tuning leaves the simulation unchanged.  NS_BATCH_SCHEDULE="gran,ctas_per_sm" forces a
+// schedule; NS_AUTOTUNE=0 keeps the default (1 tile per ticket, as many CTAs as fit).
+int batch_tune(ns_batch* b, const double* dt) {
+  b->tuned = true;
+  if (const char* f = std::getenv("NS_BATCH_SCHEDULE")) {
+    int g = 1, q = 0;
+    if (std::sscanf(f, "%d,%d", &g, &q) >= 1) {
+      b->gran = g > 0 ? g : 1;
+      b->per_sm_req = q > 0 ? q : 0;
+    }
+    return NS_OK;
+  }
+  const char* en = std::getenv("NS_AUTOTUNE");
+  if ((en && std::string(en) == "0") || b->stall) return NS_OK;
+  const int n = b->count;
+  std::vector<NsCtxBuffers> cb(n);
+  std::vector<size_t> bytes(n), off(n + 1, 0);
+  std::vector<double> t0(n);
+  std::vector<int64_t> s0(n);
+  for (int m = 0; m < n; ++m) {
+    int rc = ns_ctx_buffers(b->mem[m], dt[m], &cb[m]);
+    if (rc != NS_OK) return rc;
+    const size_t cs = cb[m].precision == NS_FP32 ? 8 : 16;
+    bytes[m] = 3 * (size_t)cb[m].N * cb[m].N * (cb[m].N / 2) * cs;
+    off[m + 1] = off[m] + bytes[m];
+    ns_time(b->mem[m], &t0[m], &s0[m]);
+  }
+  unsigned char* save = nullptr;
+  if (cudaMalloc(&save, off[n]) != cudaSuccess) {
+    cudaGetLastError();
+    return NS_OK;  // no room to tune: keep the default schedule
+  }
+  for (int m = 0; m < n; ++m)
+    cudaMemcpyAsync(save + off[m], cb[m].state, bytes[m], cudaMemcpyDeviceToDevice, b->st);
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best = 1e30f;
+  int bg = 1, bq = 0, rc = NS_OK;
+  int maxq = 0;
+  {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const size_t smem = b->precision == NS_FP32 ? BCfg<float>::SM : BCfg<double>::SM;
+    const int nt = b->precision == NS_FP32 ? BCfg<float>::NT : BCfg<double>::NT;
+    if (b->precision == NS_FP32)
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&maxq, k_batch<float>, nt, smem);
+    else
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&maxq, k_batch<double>, nt, smem);
+  }
+  for (int g : {1, 2, 4, 8}) {
+    for (int q : {0, 1}) {
+      if (q == 1 && maxq <= 1) continue;
+      b->gran = g;
+      b->per_sm_req = q;
+      rc = batch_step_any(b, dt, 1);  // untimed (graph capture)
+      if (rc != NS_OK) break;
+      cudaEventRecord(e0, b->st);
+      rc = batch_step_any(b, dt, 1);
+      cudaEventRecord(e1, b->st);
+      if (rc != NS_OK) break;
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best) {
+        best = ms;
+        bg = g;
+        bq = q;
+      }
+    }
+    if (rc != NS_OK) break;
+  }
+  for (int m = 0; m < n; ++m) {
+    cudaMemcpyAsync(cb[m].state, save + off[m], bytes[m], cudaMemcpyDeviceToDevice, b->st);
+    ns_set_time(b->mem[m], t0[m], s0[m]);
+  }
+  cudaStreamSynchronize(b->st);
+  cudaFree(save);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  b->gran = bg;
+  b->per_sm_req = bq;
+  return rc;
+}
+
+}  // namespace
 
 extern "C" {
 
@@ -99,8 +198,26 @@ int ns_batch_step(ns_batch* b, const double* dt, int nsteps) {
   if (nsteps == 0) return NS_OK;
   for (int i = 0; i < b->count; ++i)
     if (!(dt[i] > 0.0) || !std::isfinite(dt[i])) return NS_ERR_INVALID_ARG;
-  return b->precision == NS_FP32 ? batch_step_t<float>(b, dt, nsteps)
-                                 : ns_batch_step_f64(b, dt, nsteps);
+  if (!b->tuned) {
+    const int rc = batch_tune(b, dt);
+    if (rc != NS_OK) return rc;
+  }
+  return batch_step_any(b, dt, nsteps);
+}
+
+int ns_batch_set_schedule(ns_batch* b, int gran, int ctas_per_sm) {
+  if (!b || gran < 1 || ctas_per_sm < 0) return NS_ERR_INVALID_ARG;
+  b->gran = gran;
+  b->per_sm_req = ctas_per_sm;
+  b->tuned = true;
+  return NS_OK;
+}
+
+int ns_batch_schedule(ns_batch* b, int* gran, int* ctas_per_sm) {
+  if (!b || !gran || !ctas_per_sm) return NS_ERR_INVALID_ARG;
+  *gran = b->gran;
+  *ctas_per_sm = b->per_sm_req;
+  return NS_OK;
 }
 
 int ns_batch_energy(ns_batch* b, double* E, double* eps) {

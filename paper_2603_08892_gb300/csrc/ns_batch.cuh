@@ -7,9 +7,10 @@
 // Work list.  Every member m advances through the same sequence of passes:
 //   prologue:  TAB (shift tables of step 0), INIT (pencil tiles: shifted state -> mixed)
 //   per step:  TAB, YINV, XROW, YFWD, P1 (ROG_1), YINV, XROW, YFWD, P2 (ROG_2)
-// A pass consists of tiles ("items").  Items are numbered step-major, then pass, then
-// member, then tile, and the CTAs of one persistent launch take them in that order from an
-// atomic ticket counter.  Before running an item of member m, a CTA waits until done[m]
+// A pass consists of tiles ("items"), taken gran tiles per ticket (the work-list granularity:
+// the ticket, the wait and the completion fence are paid once per gran tiles).  Tickets are
+// numbered step-major, then pass, then member, then tile group, and the CTAs of one persistent
+// launch take them in that order from an atomic ticket counter.  Before running an item of member m, a CTA waits until done[m]
 // (the member's count of finished items) covers every item of the member's earlier passes;
 // an item only ever waits for items with smaller tickets, which running CTAs already hold,
 // so the schedule cannot deadlock.  Each wait is bounded (spin_limit polls); on expiry the
@@ -47,7 +48,7 @@ struct BatchMem {
   cpx<T>* tab;            // [3][3N]: alpha_s, beta_s, alpha_{s+1}
   const double* shifts;   // [nsteps + 1][3] alpha of each step of this call
   double dx;
-  int items[kPasses];     // items of each pass
+  int items[kPasses];     // items (tiles) of each pass
   int cum[kPasses + 1];   // items of the member before pass p within a step
   int pro_init;           // INIT items
 };
@@ -65,6 +66,7 @@ struct BatchCtl {
   const int* pro_mem_off;  // [2][nmem + 1]
   long long spin_limit;
   long long stall;  // added to every per-step requirement (test hook)
+  int gran;         // tiles per ticket
 };
 
 template <typename T>
@@ -176,14 +178,16 @@ __global__ void __launch_bounds__(BCfg<T>::NT) k_batch(BatchCtl c, const BatchMe
     __syncthreads();
     const long long tk = s_ticket;
     if (tk >= c.total) break;
-    int pass, m, tile, step;
+    int pass, m, tile, step, ntile;  // tiles [tile, tile + ntile) of the member's pass
     long long need;
     if (tk < c.pro_total) {
       const int pp = tk < c.pro_off[1] ? 0 : 1;
       const int r = (int)(tk - c.pro_off[pp]);
       const int* off = c.pro_mem_off + pp * (c.nmem + 1);
       m = upper_member(off, c.nmem, r);
-      tile = r - __ldg(&off[m]);
+      const int items = pp == 0 ? 1 : mems[m].pro_init;
+      tile = (r - __ldg(&off[m])) * c.gran;
+      ntile = min(c.gran, items - tile);
       pass = pp == 0 ? P_TAB : -1;
       step = 0;
       need = pp == 0 ? 0 : 1;
@@ -196,9 +200,10 @@ __global__ void __launch_bounds__(BCfg<T>::NT) k_batch(BatchCtl c, const BatchMe
       const int r2 = (int)(r - c.pass_off[p]);
       const int* off = c.mem_off + p * (c.nmem + 1);
       m = upper_member(off, c.nmem, r2);
-      tile = r2 - __ldg(&off[m]);
-      pass = p;
       const BatchMem<T>& b0 = mems[m];
+      tile = (r2 - __ldg(&off[m])) * c.gran;
+      ntile = min(c.gran, b0.items[p] - tile);
+      pass = p;
       need = 1 + (long long)b0.pro_init + (long long)step * b0.cum[kPasses] + b0.cum[p] + c.stall;
     }
     if (threadIdx.x == 0) {
@@ -220,18 +225,21 @@ __global__ void __launch_bounds__(BCfg<T>::NT) k_batch(BatchCtl c, const BatchMe
     __syncthreads();
     if (!s_go) break;
     const BatchMem<T>& bm = mems[m];
-    switch (bm.sz) {
-      case 0: run_item<T, 16>(bm, pass, step, c.nsteps, tile, smem); break;
-      case 1: run_item<T, 32>(bm, pass, step, c.nsteps, tile, smem); break;
-      case 2: run_item<T, 48>(bm, pass, step, c.nsteps, tile, smem); break;
-      case 3: run_item<T, 64>(bm, pass, step, c.nsteps, tile, smem); break;
-      case 4: run_item<T, 96>(bm, pass, step, c.nsteps, tile, smem); break;
-      default: run_item<T, 128>(bm, pass, step, c.nsteps, tile, smem); break;
+    for (int q = 0; q < ntile; ++q) {
+      if (q > 0) __syncthreads();  // the previous tile is done with the shared memory
+      switch (bm.sz) {
+        case 0: run_item<T, 16>(bm, pass, step, c.nsteps, tile + q, smem); break;
+        case 1: run_item<T, 32>(bm, pass, step, c.nsteps, tile + q, smem); break;
+        case 2: run_item<T, 48>(bm, pass, step, c.nsteps, tile + q, smem); break;
+        case 3: run_item<T, 64>(bm, pass, step, c.nsteps, tile + q, smem); break;
+        case 4: run_item<T, 96>(bm, pass, step, c.nsteps, tile + q, smem); break;
+        default: run_item<T, 128>(bm, pass, step, c.nsteps, tile + q, smem); break;
+      }
     }
     __syncthreads();
     if (threadIdx.x == 0) {
       __threadfence();
-      atomicAdd(&c.done[m], 1);
+      atomicAdd(&c.done[m], ntile);
     }
   }
 }
@@ -296,6 +304,11 @@ struct ns_batch {
   long long spin_limit = 2000000;
   int stall = 0;
   int grid = 0;
+  int g_gran = -1;
+  // work-list granularity (tiles per ticket) and CTAs per SM (0: as many as fit), chosen by
+  // the tuner at the first step (or forced by ns_batch_set_schedule / NS_BATCH_SCHEDULE)
+  int gran = 1, per_sm_req = 0;
+  bool tuned = false;
 };
 
 namespace {
@@ -372,11 +385,13 @@ int batch_step_t(ns_batch* b, const double* dt, int nsteps) {
   c.nsteps = nsteps;
   long long acc = 0;
   c.pro_off[0] = 0;
+  const int gran = b->gran > 0 ? b->gran : 1;
+  auto tickets = [&](int items) { return (items + gran - 1) / gran; };
   for (int pp = 0; pp < 2; ++pp) {
     int o = 0;
     for (int m = 0; m < n; ++m) {
       off_pro[pp * (n + 1) + m] = o;
-      o += pp == 0 ? 1 : hm[m].pro_init;
+      o += pp == 0 ? 1 : tickets(hm[m].pro_init);
     }
     off_pro[pp * (n + 1) + n] = o;
     acc += o;
@@ -389,7 +404,7 @@ int batch_step_t(ns_batch* b, const double* dt, int nsteps) {
     int o = 0;
     for (int m = 0; m < n; ++m) {
       off_pass[p * (n + 1) + m] = o;
-      o += hm[m].items[p];
+      o += tickets(hm[m].items[p]);
     }
     off_pass[p * (n + 1) + n] = o;
     sacc += o;
@@ -399,6 +414,7 @@ int batch_step_t(ns_batch* b, const double* dt, int nsteps) {
   c.total = c.pro_total + (long long)nsteps * c.step_total;
   c.spin_limit = b->spin_limit;
   c.stall = b->stall ? (1ll << 40) : 0;
+  c.gran = gran;
 
   cudaStream_t st = b->st;
   auto chk = [&](cudaError_t e) {
@@ -429,6 +445,7 @@ int batch_step_t(ns_batch* b, const double* dt, int nsteps) {
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch<T>, BCfg<T>::NT, smem);
   if (per_sm < 1) per_sm = 1;
+  if (b->per_sm_req > 0 && b->per_sm_req < per_sm) per_sm = b->per_sm_req;
   const int grid = nsm * per_sm;
   b->grid = grid;
   // the launch and its counter resets are captured in a CUDA graph once per work-list
@@ -436,7 +453,7 @@ int batch_step_t(ns_batch* b, const double* dt, int nsteps) {
   const BatchMem<T>* dm = (const BatchMem<T>*)b->d_mems;
   bool ok = true;
   if (b->gexec == nullptr || b->g_nsteps != nsteps || b->g_grid != grid ||
-      b->g_spin != b->spin_limit || b->g_stall != b->stall) {
+      b->g_spin != b->spin_limit || b->g_stall != b->stall || b->g_gran != gran) {
     if (b->gexec) cudaGraphExecDestroy(b->gexec);
     b->gexec = nullptr;
     cudaGraph_t g;
@@ -456,6 +473,7 @@ int batch_step_t(ns_batch* b, const double* dt, int nsteps) {
     b->g_grid = grid;
     b->g_spin = b->spin_limit;
     b->g_stall = b->stall;
+    b->g_gran = gran;
   }
   if (ok) ok = chk(cudaGraphLaunch(b->gexec, st));
   int flags[2] = {0, 0};

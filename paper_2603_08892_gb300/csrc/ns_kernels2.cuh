@@ -130,7 +130,16 @@ constexpr int kPencilUnroll = NS_PENCIL_UNROLL;
 #define NS_PENCIL_STAGE_STATE 0
 #endif
 
-template <typename T, int N>
+// The alternative width of a tile (lines per tile): twice the default where that divides
+// the half length m within the cap, else half (down to minw), else the default.
+__host__ __device__ constexpr int alt_width(int w, int m, int cap, int minw) {
+  return (m % (2 * w) == 0 && 2 * w <= cap) ? 2 * w : ((w / 2 >= minw && m % (w / 2) == 0) ? w / 2 : w);
+}
+
+// Tile shapes of size N.  V selects compiled alternatives for the autotuner, one bit per
+// kernel family: bit 0 the pencil width TX, bit 1 the inverse-y width TYI, bit 2 the x-row
+// count RX, bit 3 the forward-y width TY (V = 0: the defaults).
+template <typename T, int N, int V = 0>
 struct K2Cfg {
   static constexpr int M = N / 2;
   static constexpr int CS = (int)sizeof(cpx<T>);
@@ -147,9 +156,10 @@ struct K2Cfg {
 #ifndef NS_YF_LINES
 #define NS_YF_LINES 0
 #endif
-  static constexpr int TX = (NS_PZ_LINES > 0 && M % NS_PZ_LINES == 0 && NS_PZ_LINES % MINW == 0)
-                                ? NS_PZ_LINES
-                                : pick_div(M, cmax(16384 / (N * CS), MINW), 16);
+  static constexpr int TX0 = (NS_PZ_LINES > 0 && M % NS_PZ_LINES == 0 && NS_PZ_LINES % MINW == 0)
+                                 ? NS_PZ_LINES
+                                 : pick_div(M, cmax(16384 / (N * CS), MINW), 16);
+  static constexpr int TX = (V & 1) ? alt_width(TX0, M, 16, MINW) : TX0;
   static constexpr int NTP = round_lines(TX * N / RZ, TX);
   // blocks per SM the register budget must allow (NS_PENCIL_REGS registers per thread;
   // 80 measured best at 256^3 FP32 on GB300 against 96 and 128)
@@ -159,24 +169,27 @@ struct K2Cfg {
   static constexpr int MINB_P = cmax(1, cmin(8, 65536 / (NTP * NS_PENCIL_REGS)));
   // forward y pass: TY columns of N in a tile of about 32 KB (measured at 256^3 FP32: 16
   // columns, 0.133 ms per step against 0.141 for 8)
-  static constexpr int TY = (NS_YF_LINES > 0 && M % NS_YF_LINES == 0 && NS_YF_LINES % MINW == 0)
-                                ? NS_YF_LINES
-                                : pick_div(M, cmax(32768 / (N * CS), MINW), 16);
+  static constexpr int TY0 = (NS_YF_LINES > 0 && M % NS_YF_LINES == 0 && NS_YF_LINES % MINW == 0)
+                                 ? NS_YF_LINES
+                                 : pick_div(M, cmax(32768 / (N * CS), MINW), 16);
+  static constexpr int TY = (V & 8) ? alt_width(TY0, M, 32, MINW) : TY0;
   static constexpr int NTY = round_warps(TY * N / RYF);
   // inverse y pass: 4 shared tiles (3 input slots and a work tile); the width is the one
   // measured best when the tile held 6 (the 5 inputs and the work tile) within 110 KB
 #ifndef NS_YI_LINES
 #define NS_YI_LINES 0
 #endif
-  static constexpr int TYI = (NS_YI_LINES > 0 && M % NS_YI_LINES == 0 && NS_YI_LINES % MINW == 0)
-                                 ? NS_YI_LINES
-                                 : pick_div(M, cmax(110000 / (6 * N * CS), MINW), 16);
+  static constexpr int TYI0 = (NS_YI_LINES > 0 && M % NS_YI_LINES == 0 && NS_YI_LINES % MINW == 0)
+                                  ? NS_YI_LINES
+                                  : pick_div(M, cmax(110000 / (6 * N * CS), MINW), 16);
+  static constexpr int TYI = (V & 2) ? alt_width(TYI0, M, 16, MINW) : TYI0;
   static constexpr int NTYI = round_warps(TYI * N / RYI);
   // x rows: RX rows of M, processed three fields at a time (NS_XR_ROWS overrides RX)
 #ifndef NS_XR_ROWS
 #define NS_XR_ROWS 0
 #endif
-  static constexpr int RX = NS_XR_ROWS > 0 ? NS_XR_ROWS : cmin(cmax(8192 / (M * CS), 1), 16);
+  static constexpr int RX0 = NS_XR_ROWS > 0 ? NS_XR_ROWS : cmin(cmax(8192 / (M * CS), 1), 16);
+  static constexpr int RX = (V & 4) ? (2 * RX0 <= 16 ? 2 * RX0 : cmax(RX0 / 2, 1)) : RX0;
   static constexpr int NTX = round_warps(3 * RX * M / RXR);
   // elements of the x-row tile: 3 RX complex lines of length N (two real rows per line), and
   // the blocks per SM its shared memory allows (the register budget is held to that many)
@@ -416,12 +429,12 @@ __device__ __forceinline__ void tile_energy_store(double* epart, T e, T d) {
 // applies N(0) = 0, truncation, projection and forcing and the RK stage combine of all three
 // components, leaving S_next (shifted for the output when there is one output) in the tiles.
 // MC: the stage mode fixed at compile time (-1: a.mode at run time)
-template <typename T, int N, class MP, bool EP, int MC = -1>
+template <typename T, int N, class MP, bool EP, int MC = -1, int V = 0>
 __device__ __forceinline__ void pencil_spectral_one(const PencilArgs<T>& a, cpx<T>* buf, cpx<T>* tws,
                                                     int iy, int x0, int nOut, bool tz, T& eacc,
                                                     T& dacc) {
   const int mode = MC >= 0 ? MC : a.mode;
-  using C = K2Cfg<T, N>;
+  using C = K2Cfg<T, N, V>;
   constexpr int M = N / 2, TX = C::TX, NT = C::NTP, tile = lf_rows<T, C::TX>(N) * TX;
   constexpr int PER = (tile + NT - 1) / NT;
   constexpr int DZ = NT / TX;
@@ -530,9 +543,10 @@ __device__ __forceinline__ void pencil_spectral_one(const PencilArgs<T>& a, cpx<
 // NFC, NOC: the number of inputs and outputs known at compile time (-1: read from the
 // arguments).  (1, 1) is every RK2, Rogallo and RK4 stage, (2, 2) the exact scheme's stage;
 // fixing them keeps those kernels free of register spills.
-template <typename T, int N, class MP, int NFC = -1, int NOC = -1, bool EP = false, int MC = -1>
+template <typename T, int N, class MP, int NFC = -1, int NOC = -1, bool EP = false, int MC = -1,
+          int V = 0>
 __device__ __forceinline__ void pencil_tile(const PencilArgs<T>& a, int tile_id, cpx<T>* buf) {
-  using C = K2Cfg<T, N>;
+  using C = K2Cfg<T, N, V>;
   const int nF = NFC >= 0 ? NFC : a.nF, nOut = NOC >= 0 ? NOC : a.nOut;
   constexpr int M = N / 2, TX = C::TX, NT = C::NTP, tile = lf_rows<T, C::TX>(N) * TX;
   constexpr int PER = (tile + NT - 1) / NT;  // modes per thread (the last may not exist)
@@ -556,7 +570,7 @@ __device__ __forceinline__ void pencil_tile(const PencilArgs<T>& a, int tile_id,
   const bool tz = nF > 0 && tt;                               // so its inputs are not transformed
   T eacc = 0, dacc = 0;  // energy sums of the written state (a.epart)
   if constexpr (NFC == 1) {
-    pencil_spectral_one<T, N, MP, EP, MC>(a, buf, tws, iy, x0, nOut, tz, eacc, dacc);
+    pencil_spectral_one<T, N, MP, EP, MC, V>(a, buf, tws, iy, x0, nOut, tz, eacc, dacc);
   } else {
     const int nFe = tz ? 0 : nF;  // inputs that are transformed
     // 1) inputs: all three components staged asynchronously, then transformed in place
@@ -718,14 +732,14 @@ __device__ __forceinline__ void pencil_tile(const PencilArgs<T>& a, int tile_id,
 // the two-input variant holds 4 shared tiles (3 blocks per SM at most): it is given the
 // registers of 2 resident blocks rather than spill
 // EP: the one-input variant that also stores the tile's energy sums (a.epart non-null)
-// MC: the stage mode at compile time (the Rogallo stages) or -1 (a.mode)
-template <typename T, int N, int NFC, int NOC, bool EP = false, int MC = -1>
-__global__ void __launch_bounds__(K2Cfg<T, N>::NTP, (NFC == 2 || (NFC == 1 && NS_PENCIL_STAGE_STATE))
-                                                         ? cmin(2, K2Cfg<T, N>::MINB_P)
-                                                         : K2Cfg<T, N>::MINB_P)
+// MC: the stage mode at compile time (the Rogallo stages) or -1 (a.mode); V: tile variant
+template <typename T, int N, int NFC, int NOC, bool EP = false, int MC = -1, int V = 0>
+__global__ void __launch_bounds__(K2Cfg<T, N, V>::NTP, (NFC == 2 || (NFC == 1 && NS_PENCIL_STAGE_STATE))
+                                                            ? cmin(2, K2Cfg<T, N, V>::MINB_P)
+                                                            : K2Cfg<T, N, V>::MINB_P)
     k2_pencil(PencilArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  pencil_tile<T, N, MemNC, NFC, NOC, EP, MC>(a, blockIdx.x, reinterpret_cast<cpx<T>*>(smem_raw));
+  pencil_tile<T, N, MemNC, NFC, NOC, EP, MC, V>(a, blockIdx.x, reinterpret_cast<cpx<T>*>(smem_raw));
 }
 
 // ---- slab pass: y transforms --------------------------------------------------------
@@ -810,15 +824,16 @@ __device__ __forceinline__ void yinv_tile(const SlabArgs<T>& a, int tx, int zg, 
   yinv_field<T, N, 2, MP, TY, NT, true>(a, in, W, zg, x0, sstride, tws);  // u_z in slot 2
 }
 
-template <typename T, int N>
-__global__ void __launch_bounds__(K2Cfg<T, N>::NTYI) k2_yinv(SlabArgs<T> a) {
+template <typename T, int N, int V = 0>
+__global__ void __launch_bounds__(K2Cfg<T, N, V>::NTYI) k2_yinv(SlabArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  yinv_tile<T, N, MemNC>(a, blockIdx.x, blockIdx.y, reinterpret_cast<cpx<T>*>(smem_raw));
+  yinv_tile<T, N, MemNC, K2Cfg<T, N, V>::TYI, K2Cfg<T, N, V>::NTYI>(a, blockIdx.x, blockIdx.y,
+                                                                  reinterpret_cast<cpx<T>*>(smem_raw));
 }
 
-template <typename T, int N, class MP>
+template <typename T, int N, class MP, int V = 0>
 __device__ __forceinline__ void yfwd_tile(const SlabArgs<T>& a, int tx, int zg, cpx<T>* W) {
-  using C = K2Cfg<T, N>;
+  using C = K2Cfg<T, N, V>;
   const int x0 = tx * C::TY, z = a.z0 + zg;
   const size_t sstride = (size_t)a.G * N * (N / 2);
   const size_t fstride = (size_t)N * N * (N / 2);
@@ -831,10 +846,10 @@ __device__ __forceinline__ void yfwd_tile(const SlabArgs<T>& a, int tx, int zg, 
   }
 }
 
-template <typename T, int N>
-__global__ void __launch_bounds__(K2Cfg<T, N>::NTY, 2) k2_yfwd(SlabArgs<T> a) {
+template <typename T, int N, int V = 0>
+__global__ void __launch_bounds__(K2Cfg<T, N, V>::NTY, 2) k2_yfwd(SlabArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  yfwd_tile<T, N, MemNC>(a, blockIdx.x, blockIdx.y, reinterpret_cast<cpx<T>*>(smem_raw));
+  yfwd_tile<T, N, MemNC, V>(a, blockIdx.x, blockIdx.y, reinterpret_cast<cpx<T>*>(smem_raw));
 }
 
 // ---- slab pass: x rows --------------------------------------------------------------
@@ -846,9 +861,9 @@ __global__ void __launch_bounds__(K2Cfg<T, N>::NTY, 2) k2_yfwd(SlabArgs<T> a) {
 // of every row and (f_2 of row q, f_2 of row q + RXh), whose forward transforms P split into
 // F_a[k] = (P[k] + conj(P[N - k])) / 2 and F_b[k] = (P[k] - conj(P[N - k])) / (2 i).  All
 // transforms are unnormalised, as the r2c / c2r pair they replace.
-template <typename T, int N, class MP>
+template <typename T, int N, class MP, int V = 0>
 __device__ __forceinline__ void xrow_tile(const SlabArgs<T>& a, int tile_id, cpx<T>* buf) {
-  using C = K2Cfg<T, N>;
+  using C = K2Cfg<T, N, V>;
   constexpr int M = N / 2, RX = C::RX, NT = C::NTX, RXh = (RX + 1) / 2;
   constexpr int NLI = 3 * RX, NLF = RX + RXh;  // inverse and forward lines
   const WorkTile<T, N, NLI, false> L{buf};     // line p RX + r: pair p of row r
@@ -943,10 +958,10 @@ __device__ __forceinline__ void xrow_tile(const SlabArgs<T>& a, int tile_id, cpx
   }
 }
 
-template <typename T, int N>
-__global__ void __launch_bounds__(K2Cfg<T, N>::NTX, K2Cfg<T, N>::MINB_X) k2_xrow(SlabArgs<T> a) {
+template <typename T, int N, int V = 0>
+__global__ void __launch_bounds__(K2Cfg<T, N, V>::NTX, K2Cfg<T, N, V>::MINB_X) k2_xrow(SlabArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  xrow_tile<T, N, MemNC>(a, blockIdx.x, reinterpret_cast<cpx<T>*>(smem_raw));
+  xrow_tile<T, N, MemNC, V>(a, blockIdx.x, reinterpret_cast<cpx<T>*>(smem_raw));
 }
 
 // ---- slab pipeline: the three slab kernels as one persistent launch -------------------
@@ -1094,7 +1109,22 @@ struct K2Entry {
   size_t smCL = 0;
   int TX = 0, NTP = 0, TY = 0, NTY = 0, TYI = 0, NTYI = 0, RX = 0, NTX = 0;
   size_t smP1 = 0, smP4 = 0, smP5 = 0, smY = 0, smYI = 0, smX = 0;
+  // the autotuner's compiled alternatives (K2Cfg variant 15: every family's other width);
+  // has_alt false when the size has none
+  struct Alt {
+    void (*pencil1r[2])(PencilArgs<T>) = {nullptr, nullptr};
+    void (*yinv)(SlabArgs<T>) = nullptr;
+    void (*yfwd)(SlabArgs<T>) = nullptr;
+    void (*xrow)(SlabArgs<T>) = nullptr;
+    int TX = 0, NTP = 0, TY = 0, NTY = 0, TYI = 0, NTYI = 0, RX = 0, NTX = 0;
+    size_t smP1 = 0, smY = 0, smYI = 0, smX = 0;
+  } alt;
+  bool has_alt = false;
 };
+
+// sizes with compiled alternatives: the FP32 grids of 128^3 and larger
+template <typename T, int N>
+__host__ __device__ constexpr bool k2_has_alt() { return sizeof(T) == 4 && N >= 128; }
 
 template <typename T, int N>
 K2Entry<T> make_k2_entry() {
@@ -1140,6 +1170,21 @@ K2Entry<T> make_k2_entry() {
   e.smP5 = (4 * (size_t)lf_rows<T, C::TX>(N) * C::TX + tw_elems(N)) * sizeof(cpx<T>);  // 4 tiles + twiddles
   e.smY = ((size_t)lf_rows<T, C::TY>(N) * C::TY + tw_elems(N)) * sizeof(cpx<T>);
   e.smX = ((size_t)C::XELEMS + tw_elems(N)) * sizeof(cpx<T>);
+  if constexpr (k2_has_alt<T, N>()) {
+    using A = K2Cfg<T, N, 15>;
+    e.has_alt = true;
+    e.alt.pencil1r[0] = k2_pencil<T, N, 1, 1, false, MODE_ROG_1, 15>;
+    e.alt.pencil1r[1] = k2_pencil<T, N, 1, 1, false, MODE_ROG_2, 15>;
+    e.alt.yinv = k2_yinv<T, N, 15>;
+    e.alt.yfwd = k2_yfwd<T, N, 15>;
+    e.alt.xrow = k2_xrow<T, N, 15>;
+    e.alt.TX = A::TX; e.alt.NTP = A::NTP; e.alt.TY = A::TY; e.alt.NTY = A::NTY;
+    e.alt.TYI = A::TYI; e.alt.NTYI = A::NTYI; e.alt.RX = A::RX; e.alt.NTX = A::NTX;
+    e.alt.smYI = (4 * (size_t)lf_rows<T, A::TYI>(N) * A::TYI + tw_elems(N)) * sizeof(cpx<T>);
+    e.alt.smP1 = (3 * (size_t)lf_rows<T, A::TX>(N) * A::TX + tw_elems(N)) * sizeof(cpx<T>);
+    e.alt.smY = ((size_t)lf_rows<T, A::TY>(N) * A::TY + tw_elems(N)) * sizeof(cpx<T>);
+    e.alt.smX = ((size_t)A::XELEMS + tw_elems(N)) * sizeof(cpx<T>);
+  }
   return e;
 }
 

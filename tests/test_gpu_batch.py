@@ -135,3 +135,42 @@ def test_batch_fp32_members_match_oracle(ns, report):
         err = rel(got[i], ref)
         report("batch_member_N%d_4_steps_fp32" % N, err, 4 * 2e-5)
         assert err < 4 * 2e-5, i  # four FP32 steps
+
+
+@pytest.mark.parametrize("sched", [(1, 0), (4, 0), (8, 1)])
+def test_batch_schedules_give_identical_results(ns, sched):
+    # the work-list granularity and CTAs per SM change the order of the work, not the result
+    Ns = [32, 64, 16]
+    us = members(Ns, seed0=70)
+    out = []
+    for s in ((1, 0), sched):
+        with ns.Batch(Ns, [0.01] * 3, [N / 2 for N in Ns], seeds=[1, 2, 3], precision=ns.FP32) as b:
+            b.set_schedule(*s)
+            for i, u in enumerate(us):
+                b.set_velocity(i, u)
+            b.step([0.01] * 3, 3)
+            out.append([b.get_state(i) for i in range(3)])
+    for a, c in zip(*out):
+        assert np.array_equal(a, c)
+
+
+def test_batch_tuner_leaves_the_states_unchanged(ns):
+    # the first step tunes the schedule on the ensemble and restores the states it touched
+    Ns = [32, 64]
+    us = members(Ns, seed0=80)
+    ref = []
+    with ns.Batch(Ns, [0.01] * 2, [N / 2 for N in Ns], seeds=[5, 6], precision=ns.FP64) as b:
+        b.set_schedule(1, 0)
+        for i, u in enumerate(us):
+            b.set_velocity(i, u)
+        b.step([0.01] * 2, 2)
+        ref = [b.get_state(i) for i in range(2)]
+    with ns.Batch(Ns, [0.01] * 2, [N / 2 for N in Ns], seeds=[5, 6], precision=ns.FP64) as b:
+        for i, u in enumerate(us):
+            b.set_velocity(i, u)
+        b.step([0.01] * 2, 2)  # tunes first
+        got = [b.get_state(i) for i in range(2)]
+        g, q = b.schedule()
+        assert g in (1, 2, 4, 8) and q in (0, 1)
+    for a, c in zip(ref, got):
+        assert np.array_equal(a, c)

@@ -78,3 +78,30 @@ def test_cluster_slab_many_steps_and_cfl(ns, monkeypatch, tmp_path):
             t, n = s.time()
             dts.append(t)
     assert abs(dts[0] - dts[1]) < 1e-7 * dts[1]
+
+
+@pytest.mark.parametrize("N", [128, 256])
+def test_tile_variants_match_oracle(ns, report, monkeypatch, tmp_path, N):
+    # every compiled tile alternative the autotuner may choose (pencil width, inverse-y width,
+    # x rows, forward-y width), forced on, against the oracle and the defaults
+    u = inputs.random_solenoidal(N, 900 + N, kcut=N / 2, energy_total=0.5)
+    monkeypatch.setenv("NS_SLAB_CLUSTER", "0")
+    monkeypatch.setenv("NS_AUTOTUNE_CACHE", str(tmp_path / "tune.json"))
+    dt = 0.5 * math.pi / N
+    states = {}
+    for v in (0, 15):
+        monkeypatch.setenv("NS_TILE_VARIANT", str(v))
+        with ns.Solver(N, NU, N / 2, scheme=ns.RK2_PS_RANDOM, precision=ns.FP32, seed=12345) as s:
+            s.set_velocity(u)
+            s.step(dt, 1)
+            states[v] = s.get_state()
+    old = osp.set_fft_workers(8)
+    try:
+        ref = sc.step_ps_random(osp.set_velocity(u, N / 2), dt, sc.Problem(N, NU, N / 2),
+                                orng.shift_alpha(12345, 0, N))
+    finally:
+        osp.set_fft_workers(old)
+    err = rel(states[15], ref)
+    report("tile_alternatives_rogallo_step_N%d_fp32" % N, err, 2e-5)
+    assert err < 2e-5
+    assert rel(states[15], states[0]) < 1e-6
