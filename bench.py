@@ -63,6 +63,8 @@ def parse():
                     help="steps of the 64-member ensemble leg (0: skip)")
     ap.add_argument("--quality", action="store_true",
                     help="run the accuracy study at kmax = 108 instead (spectral error vs speedup)")
+    ap.add_argument("--quality-cfl", action="store_true",
+                    help="with --quality: adaptive CFL steps (0.4 for the RK2 family, 1.0 for RK4)")
     return ap.parse_args()
 
 
@@ -242,13 +244,18 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
-def run_quality(local):
+def run_quality(local, adaptive=False):
     """Accuracy / speed study at kmax = 108 (Sec. 5, Fig. quality, supplementary Table
     tab:quality): Taylor-Green Re = 1600 to t = 12 with the spectral error index (Eq. quality)
     of the 1D spectra over the window t = 7 .. 12 around the dissipation peak (t_end = t_start
     + 5), sampled at integer times, against RK4 at N = 324, C_t = 2/3.  FP32, time step
     1 / ceil(1 / (0.25 dx)) (CFL 0.5 reading, integer times on steps).  Speedup = GPU time of
-    the reference run / GPU time of the run (stepping only, CUDA events)."""
+    the reference run / GPU time of the run (stepping only, CUDA events).
+
+    adaptive: every step from the CFL condition of the velocity its first evaluation forms
+    (ns_step_cfl; the paper's coefficients, 0.4 for the RK2 family and 1.0 for RK4, Sec. 2),
+    each step capped so that the run lands on the integer sampling times; the GPU time is the
+    sum of the steps' event times (the host turnaround between the one-step calls excluded)."""
     import torch
 
     from paper_2603_08892_gb300 import analysis
@@ -268,30 +275,47 @@ def run_quality(local):
     for name, N, scheme, trunc in cases:
         dt = 1.0 / math.ceil(1.0 / (0.25 * 2 * math.pi / N))
         per = int(round(1.0 / dt))
+        cfl = 1.0 if scheme == ns.RK4 else 0.4
         stream = torch.cuda.Stream()
         with ns.Solver(N, 1.0 / 1600, kmax, scheme=scheme, truncation=trunc, precision=ns.FP32,
                        stream=stream.cuda_stream, seed=12345) as s:
             s.set_velocity(inputs.taylor_green(N))
-            spec, ms = [], 0.0
+            spec, ms, nst = [], 0.0, 0
             for j in range(1, T + 1):
-                e0 = torch.cuda.Event(enable_timing=True)
-                e1 = torch.cuda.Event(enable_timing=True)
-                torch.cuda.synchronize()
-                e0.record(stream)
-                s.step(dt, per)
-                e1.record(stream)
-                torch.cuda.synchronize()
-                ms += e0.elapsed_time(e1)
+                if adaptive:
+                    t, _ = s.time()
+                    while t < j - 1e-12:
+                        e0 = torch.cuda.Event(enable_timing=True)
+                        e1 = torch.cuda.Event(enable_timing=True)
+                        e0.record(stream)
+                        s.step_cfl(cfl, j - t, 1)
+                        e1.record(stream)
+                        e1.synchronize()
+                        ms += e0.elapsed_time(e1)
+                        nst += 1
+                        t, _ = s.time()
+                else:
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    torch.cuda.synchronize()
+                    e0.record(stream)
+                    s.step(dt, per)
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                    ms += e0.elapsed_time(e1)
+                    nst += per
                 if j >= t0:
                     spec.append(tuple(s.spectrum(k, 112) for k in (1, 2, 3)))
             E, eps = s.energy()
         if ref_spec is None:
             ref_spec, ref_ms = spec, ms
-        out.append({"run": name, "N": N, "steps": T * per, "dt": dt, "gpu_s": ms / 1000.0,
+        out.append({"run": name, "N": N, "steps": nst, "dt": (T / nst) if adaptive else dt,
+                    "cfl": cfl if adaptive else None, "gpu_s": ms / 1000.0,
                     "speedup": ref_ms / ms, "error_pct": analysis.error_index(spec, ref_spec, kmax),
                     "E_end": E, "eps_end": eps})
         print(json.dumps(out[-1]), flush=True)
-    print(json.dumps({"study": "quality", "kmax": kmax, "Re": 1600, "window": [t0, T], "runs": out}))
+    print(json.dumps({"study": "quality", "adaptive_cfl": adaptive, "kmax": kmax, "Re": 1600,
+                      "window": [t0, T], "runs": out}))
 
 
 def accuracy_leg(ns, inputs, stream, local, line):
@@ -365,7 +389,7 @@ def main():
         return
     if args.quality:
         if rank == 0:
-            run_quality(local)
+            run_quality(local, adaptive=args.quality_cfl)
         return
     import numpy as np
     import torch

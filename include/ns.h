@@ -305,6 +305,34 @@ int ns_batch_schedule(ns_batch* b, int* gran, int* ctas_per_sm);
 int ns_nonlinear_noalloc(const void* state, void* out, int N, double kmax, int truncation,
                          const double* delta, void* stream);
 
+/* ---- Rank-range passes of a single field split over P ranks (Sec. 2: the slab
+ * decomposition of a distributed 3D FFT, as in the paper's FFTW-MPI runs) --------------------
+ * A rank holds the ky rows [lo, hi) of the spectral and pencil-pass fields (all z or kz) and
+ * the planes [lo, hi) of the slab pass (all y or ky).  One nonlinear evaluation is
+ *   ns_rank_pencil(INIT, delta, own ky rows)   state -> mixed fields u, d_z u_x, d_z u_y
+ *   exchange 1 (all-to-all: the mixed fields, ky rows -> z planes)
+ *   ns_rank_slab(own z planes)                 mixed -> FFT_xy(u x omega)
+ *   exchange 2 (all-to-all back: z planes -> ky rows)
+ *   ns_rank_pencil(NL, delta, own ky rows)     -> T P e^{-ik.delta} FFT(u x omega)
+ * with the host exchanges in between (ns_rank_copy moves blocks between the context's buffers
+ * and host memory).  Each call runs the single-field kernels on its range only, on the
+ * context's stream, and synchronises it before returning.  No counterpart of the API in the
+ * paper; the arithmetic is that of ns_nonlinear. */
+enum { NS_BUF_STATE = 0, NS_BUF_MIXED = 1, NS_BUF_FT = 2, NS_BUF_NL = 3 };
+enum { NS_RANK_INIT = 0, NS_RANK_NL = 1 };
+/* Copies block [lo, hi) of axis `axis` of buffer `buf` (STATE [3][N][N][N/2], MIXED [5][..],
+ * FT [3][..], NL [3][..]; complex [field][z or kz][ky][kx]) to (to_device = 0) or from host
+ * FP64 (re, im) memory laid out as [F][hi-lo][N][N/2] (axis 0: z or kz planes) or
+ * [F][N][hi-lo][N/2] (axis 1: ky rows).  NS_ERR_INVALID_ARG for a NULL host pointer, an
+ * unknown buffer or axis, or a range outside [0, N). */
+int ns_rank_copy(ns_ctx* ctx, int buf, int axis, int lo, int hi, int to_device, double* host);
+/* The pencil pass on the ky rows [ky_lo, ky_hi), shift delta (host double[3], radians):
+ * NS_RANK_INIT from the state to the mixed fields, NS_RANK_NL from FT to NL. */
+int ns_rank_pencil(ns_ctx* ctx, int kind, const double* delta, int ky_lo, int ky_hi);
+/* The slab pass on the planes [z_lo, z_hi): MIXED -> FT (the same plane-group kernels as a
+ * whole-field pass). */
+int ns_rank_slab(ns_ctx* ctx, int z_lo, int z_hi);
+
 /* Bytes moved to/from HBM per time step by the algorithmic two-pass model (one slab and
  * one pencil pass per evaluation), for roofline reporting. */
 double ns_model_bytes_per_step(ns_ctx* ctx);

@@ -76,6 +76,12 @@ _set_time = _sig("ns_set_time", ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_in
 _device_state = _sig("ns_device_state", ctypes.c_int,
                      [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(ctypes.c_int)])
 _model_bytes = _sig("ns_model_bytes_per_step", ctypes.c_double, [_vp])
+_rank_copy = _sig("ns_rank_copy", ctypes.c_int,
+                  [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp])
+_rank_pencil = _sig("ns_rank_pencil", ctypes.c_int, [_vp, ctypes.c_int, _dp, ctypes.c_int, ctypes.c_int])
+_rank_slab = _sig("ns_rank_slab", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int])
+BUF_STATE, BUF_MIXED, BUF_FT, BUF_NL = 0, 1, 2, 3
+RANK_INIT, RANK_NL = 0, 1
 _vjp_state = _sig("ns_vjp_state", ctypes.c_int, [_vp, _dp, ctypes.c_int, ctypes.c_double, ctypes.c_int, _dp, _dp])
 _tape_forward = _sig("ns_tape_forward", ctypes.c_int,
                      [_vp, _vp, ctypes.c_int, ctypes.c_double, ctypes.c_int, _vp])
@@ -116,7 +122,7 @@ EXPORTED = ["ns_init", "ns_init_ex", "ns_init_error", "ns_destroy", "ns_last_err
             "ns_set_forcing", "ns_step", "ns_step_cfl", "ns_step_diag", "ns_set_shifts",
             "ns_checkpoint_save", "ns_checkpoint_load", "ns_nonlinear", "ns_energy",
             "ns_energy_spectrum", "ns_energy_flux", "ns_time", "ns_set_time", "ns_device_state",
-            "ns_model_bytes_per_step", "ns_nl1d", "ns_fma_peak", "ns_profile", "ns_profile_read", "ns_nonlinear_noalloc", "ns_vjp", "ns_vjp_state",
+            "ns_model_bytes_per_step", "ns_nl1d", "ns_fma_peak", "ns_profile", "ns_profile_read", "ns_nonlinear_noalloc", "ns_vjp", "ns_vjp_state", "ns_rank_copy", "ns_rank_pencil", "ns_rank_slab",
             "ns_tape_forward", "ns_tape_backward", "ns_batch_init", "ns_batch_destroy", "ns_batch_last_error",
             "ns_batch_member", "ns_batch_set_velocity", "ns_batch_get_state", "ns_batch_step",
             "ns_batch_energy", "ns_batch_set_spin_limit", "ns_batch_test_stall", "ns_batch_grid",
@@ -280,6 +286,25 @@ class Solver:
 
     def model_bytes_per_step(self):
         return _model_bytes(self._h)
+
+    def rank_get(self, buf, axis, lo, hi):
+        """Block [lo, hi) of axis 0 (z / kz planes) or 1 (ky rows) of a buffer, complex128."""
+        N, F = self.N, 5 if buf == BUF_MIXED else 3
+        shape = (F, hi - lo, N, N // 2) if axis == 0 else (F, N, hi - lo, N // 2)
+        out = np.empty(shape, dtype=np.complex128)
+        self._check(_rank_copy(self._h, buf, axis, lo, hi, 0, out.ctypes.data_as(_dp)))
+        return out
+
+    def rank_set(self, buf, axis, lo, hi, block):
+        b = np.ascontiguousarray(block, dtype=np.complex128)
+        self._check(_rank_copy(self._h, buf, axis, lo, hi, 1, b.ctypes.data_as(_dp)))
+
+    def rank_pencil(self, kind, delta, lo, hi):
+        d = np.ascontiguousarray(delta, dtype=np.float64)
+        self._check(_rank_pencil(self._h, kind, _ptr(d), lo, hi))
+
+    def rank_slab(self, lo, hi):
+        self._check(_rank_slab(self._h, lo, hi))
 
     def vjp_state(self, u0, nsteps, dt, gT, ckpt_every=10):
         """dL/du0 of a loss of u(T) whose gradient dL/du(T) is gT (see ns_vjp_state)."""

@@ -211,6 +211,9 @@ struct SolverBase {
   virtual void vjp_state(const double* u0, int nsteps, double dt, int ckpt, const double* gT,
                          double* grad) = 0;
   virtual void tape_forward(const void* u0, int nsteps, double dt, int ckpt, void* uT) = 0;
+  virtual void rank_copy(int which, int axis, int lo, int hi, bool to_dev, double* host) = 0;
+  virtual void rank_pencil(int kind, const double* delta, int lo, int hi) = 0;
+  virtual void rank_slab(int lo, int hi) = 0;
   virtual void tape_backward(const void* gT, int loss, void* grad) = 0;
   virtual void profile(int on) = 0;
   virtual void profile_read(int k, double* ms, int64_t* n, int64_t* launches) = 0;
@@ -483,6 +486,7 @@ struct Solver : SolverBase {
     if (ev_fork) cudaEventDestroy(ev_fork);
     for (auto* p : adj) cudaFree(p);
     cudaFree(mixedB); cudaFree(FtB); cudaFree(shS); cudaFree(shR); cudaFree(ftab);
+    cudaFree(rank_stg);
     for (auto& r : prof.rec) {
       cudaEventDestroy(r.second.first);
       cudaEventDestroy(r.second.second);
@@ -605,6 +609,37 @@ struct Solver : SolverBase {
     prof_end(e);
   }
 
+  // the three slab kernels on the plane group (a.z0, a.G) on stream s
+  void slab_group(const SlabArgs<T>& a, cudaStream_t s) {
+    cudaEvent_t e = prof_begin(NS_PROF_YINV, s);
+    if (use2)
+      if (vsel & 2)
+        k2.alt.yinv<<<dim3(M / k2.alt.TYI, a.G), k2.alt.NTYI, k2.alt.smYI, s>>>(a);
+      else
+        k2.yinv<<<dim3(M / k2.TYI, a.G), k2.NTYI, k2.smYI, s>>>(a);
+    else
+      k_yinv<T><<<dim3(M / TY, a.G), bdYi, smYi, s>>>(a);
+    prof_end(e, s);
+    e = prof_begin(NS_PROF_XROW, s);
+    if (use2)
+      if (vsel & 4)
+        k2.alt.xrow<<<(a.G * N + k2.alt.RX - 1) / k2.alt.RX, k2.alt.NTX, k2.alt.smX, s>>>(a);
+      else
+        k2.xrow<<<(a.G * N + k2.RX - 1) / k2.RX, k2.NTX, k2.smX, s>>>(a);
+    else
+      k_xrow<T><<<(a.G * N + RX - 1) / RX, bdX, smX, s>>>(a);
+    prof_end(e, s);
+    e = prof_begin(NS_PROF_YFWD, s);
+    if (use2)
+      if (vsel & 8)
+        k2.alt.yfwd<<<dim3(M / k2.alt.TY, a.G), k2.alt.NTY, k2.alt.smY, s>>>(a);
+      else
+        k2.yfwd<<<dim3(M / k2.TY, a.G), k2.NTY, k2.smY, s>>>(a);
+    else
+      k_yfwd<T><<<dim3(M / TY, a.G), bdYf, smYf, s>>>(a);
+    prof_end(e, s);
+  }
+
   // slab pass over every plane group: mixed (5 fields) -> Ft (3 fields)
   void slab(const cpx<T>* mix, cpx<T>* out, bool umax = false) {
     SlabArgs<T> a = slab_args();
@@ -661,33 +696,7 @@ struct Solver : SolverBase {
       a.z0 = z0;
       a.G = (z0 + G <= N) ? G : N - z0;
       a.scr = scr + (two ? (size_t)(gi & 1) * 6 * G * N * M : 0);  // double-buffered scratch
-      cudaEvent_t e = prof_begin(NS_PROF_YINV, s);
-      if (use2)
-        if (vsel & 2)
-          k2.alt.yinv<<<dim3(M / k2.alt.TYI, a.G), k2.alt.NTYI, k2.alt.smYI, s>>>(a);
-        else
-          k2.yinv<<<dim3(M / k2.TYI, a.G), k2.NTYI, k2.smYI, s>>>(a);
-      else
-        k_yinv<T><<<dim3(M / TY, a.G), bdYi, smYi, s>>>(a);
-      prof_end(e, s);
-      e = prof_begin(NS_PROF_XROW, s);
-      if (use2)
-        if (vsel & 4)
-          k2.alt.xrow<<<(a.G * N + k2.alt.RX - 1) / k2.alt.RX, k2.alt.NTX, k2.alt.smX, s>>>(a);
-        else
-          k2.xrow<<<(a.G * N + k2.RX - 1) / k2.RX, k2.NTX, k2.smX, s>>>(a);
-      else
-        k_xrow<T><<<(a.G * N + RX - 1) / RX, bdX, smX, s>>>(a);
-      prof_end(e, s);
-      e = prof_begin(NS_PROF_YFWD, s);
-      if (use2)
-        if (vsel & 8)
-          k2.alt.yfwd<<<dim3(M / k2.alt.TY, a.G), k2.alt.NTY, k2.alt.smY, s>>>(a);
-        else
-          k2.yfwd<<<dim3(M / k2.TY, a.G), k2.NTY, k2.smY, s>>>(a);
-      else
-        k_yfwd<T><<<dim3(M / TY, a.G), bdYf, smYf, s>>>(a);
-      prof_end(e, s);
+      slab_group(a, s);
     }
     if (two) {
       for (int i = 0; i < 2; ++i) {
@@ -713,25 +722,100 @@ struct Solver : SolverBase {
     return a;
   }
 
-  void pencil(const PencilArgs<T>& a) {
+  // the pencil pass over the ky rows [a.iy0, a.iy0 + rows) (rows < 0: every row)
+  void pencil(const PencilArgs<T>& a, int rows = -1) {
     cudaEvent_t e = prof_begin(NS_PROF_PENCIL);
+    const int R = rows < 0 ? N : rows;
     const bool rog = a.nF == 1 && a.nOut == 1 && !a.epart && (a.mode == MODE_ROG_1 || a.mode == MODE_ROG_2);
     if (use2 && rog && (vsel & 1))  // the autotuner's alternative pencil width
-      k2.alt.pencil1r[a.mode == MODE_ROG_1 ? 0 : 1]<<<(M / k2.alt.TX) * N, k2.alt.NTP, k2.alt.smP1, st>>>(a);
+      k2.alt.pencil1r[a.mode == MODE_ROG_1 ? 0 : 1]<<<(M / k2.alt.TX) * R, k2.alt.NTP, k2.alt.smP1, st>>>(a);
     else if (use2)
       (a.nF == 1 && a.nOut == 1   ? (a.epart                  ? k2.pencil1e
                                      : a.mode == MODE_ROG_1 ? k2.pencil1r[0]
                                      : a.mode == MODE_ROG_2 ? k2.pencil1r[1]
                                                             : k2.pencil1)
        : a.nF == 2 && a.nOut == 2 ? k2.pencil2
-                                  : k2.pencil)<<<(M / k2.TX) * N, k2.NTP,
+                                  : k2.pencil)<<<(M / k2.TX) * R, k2.NTP,
                                                   (a.nF == 1 && a.nOut == 1) ? k2.smP1
                                                   : (a.nF > 1 || a.nOut > 1) ? k2.smP5
                                                                              : k2.smP4, st>>>(a);
     else
-      k_pencil<T><<<(M / TX) * N, bdP, smP, st>>>(a);
+      k_pencil<T><<<(M / TX) * R, bdP, smP, st>>>(a);
     prof_end(e);
     LAUNCH_CHECK();
+  }
+
+  // ---- rank-range passes of a field decomposed over ranks (Sec. 2: the distributed 3D FFT's
+  // transposes); the exchanges between them are the caller's
+  cpx<T>* rank_stg = nullptr;  // contiguous block staging (5 fields at most)
+  cpx<T>* rank_buf(int which) {
+    switch (which) {
+      case NS_BUF_STATE: return state;
+      case NS_BUF_MIXED: return mixed[0];
+      case NS_BUF_FT: return Ft[0];
+      default: return acc;  // NS_BUF_NL
+    }
+  }
+  int rank_fields(int which) const { return which == NS_BUF_MIXED ? 5 : 3; }
+  // block [lo, hi) of the z (or kz) axis (axis 0) or the ky axis (axis 1) of buffer `which`
+  // between the device and host FP64 (re, im): axis 0 [F][hi-lo][N][M], axis 1 [F][N][hi-lo][M]
+  void rank_copy(int which, int axis, int lo, int hi, bool to_dev, double* host) override {
+    carry_step = -1;
+    const int F = rank_fields(which), n = hi - lo;
+    const size_t cs = sizeof(cpx<T>);
+    if (!rank_stg) CUDA_TRY(cudaMalloc(&rank_stg, 5 * F1 * cs));
+    cpx<T>* d = rank_buf(which);
+    const size_t count = (size_t)F * N * n * M;  // complex values of the block
+    size_t width, height, dpitch;
+    cpx<T>* base;
+    if (axis == 0) {  // F rows of n N M values, field pitch N N M
+      width = (size_t)n * N * M * cs; height = F; dpitch = F1 * cs; base = d + (size_t)lo * N * M;
+    } else {          // F N rows of n M values, row pitch N M
+      width = (size_t)n * M * cs; height = (size_t)F * N; dpitch = (size_t)N * M * cs; base = d + (size_t)lo * M;
+    }
+    if (to_dev) {
+      to_device(host, reinterpret_cast<T*>(rank_stg), 2 * count);
+      CUDA_TRY(cudaMemcpy2DAsync(base, dpitch, rank_stg, width, width, height, cudaMemcpyDeviceToDevice, st));
+      CUDA_TRY(cudaStreamSynchronize(st));
+    } else {
+      CUDA_TRY(cudaMemcpy2DAsync(rank_stg, width, base, dpitch, width, height, cudaMemcpyDeviceToDevice, st));
+      to_host(reinterpret_cast<const T*>(rank_stg), host, 2 * count);
+      sync_check();
+    }
+  }
+  // pencil pass on the ky rows [lo, hi): NS_RANK_INIT: state -> mixed (shifted by delta);
+  // NS_RANK_NL: Ft -> the shifted, de-shifted, truncated, projected nonlinear term (NL buffer)
+  void rank_pencil(int kind, const double* delta, int lo, int hi) override {
+    carry_step = -1;
+    std::vector<double> sh(delta, delta + 3);
+    upload_shifts(sh);
+    PencilArgs<T> p = pencil_args(kind == NS_RANK_INIT ? MODE_INIT : MODE_NL);
+    p.shell = nullptr;
+    p.iy0 = lo;
+    if (kind == NS_RANK_INIT) {
+      p.src = state;
+      p.nOut = 1; p.osh[0] = shift_tab(0); p.out[0] = mixed[0];
+    } else {
+      p.nF = 1; p.F[0] = Ft[0]; p.dsh[0] = shift_tab(0); p.wF[0] = (T)(1.0 / ((double)N * N * N));
+      p.acc = acc;
+    }
+    pencil(p, hi - lo);
+    sync_check();
+  }
+  // slab pass on the planes [lo, hi): mixed -> Ft (the three slab kernels, plane groups of G)
+  void rank_slab(int lo, int hi) override {
+    carry_step = -1;
+    SlabArgs<T> a = slab_args();
+    a.mixed = mixed[0];
+    a.Ft = Ft[0];
+    a.xmode = XMODE_NONLINEAR;
+    for (int z0 = lo; z0 < hi; z0 += G) {
+      a.z0 = z0;
+      a.G = (z0 + G <= hi) ? G : hi - z0;
+      slab_group(a, st);
+    }
+    LAUNCH_CHECK();
+    sync_check();
   }
 
   // the pencil pass that writes a step's new state; with diagnostics on, also E and eps of that
@@ -2259,6 +2343,39 @@ int ns_tape_backward(ns_ctx* c, const void* gT, int loss, void* grad_u0) {
     if (!gT && loss != NS_LOSS_DISSIPATION && loss != NS_LOSS_ENERGY)
       return fail(c, NS_ERR_INVALID_ARG, "unknown loss");
     c->solver->tape_backward(gT, loss, grad_u0);
+    return (int)NS_OK;
+  });
+}
+
+int ns_rank_copy(ns_ctx* c, int buf, int axis, int lo, int hi, int to_device, double* host) {
+  return guarded(c, [&]() {
+    if (!host) return fail(c, NS_ERR_INVALID_ARG, "NULL argument");
+    if (buf < NS_BUF_STATE || buf > NS_BUF_NL || (axis != 0 && axis != 1) || lo < 0 || hi <= lo ||
+        hi > c->p.N)
+      return fail(c, NS_ERR_INVALID_ARG, "need a known buffer, axis 0 or 1 and 0 <= lo < hi <= N");
+    c->solver->rank_copy(buf, axis, lo, hi, to_device != 0, host);
+    if (to_device && buf == NS_BUF_STATE) c->have_state = true;
+    return (int)NS_OK;
+  });
+}
+
+int ns_rank_pencil(ns_ctx* c, int kind, const double* delta, int ky_lo, int ky_hi) {
+  return guarded(c, [&]() {
+    if (!delta) return fail(c, NS_ERR_INVALID_ARG, "NULL argument");
+    if ((kind != NS_RANK_INIT && kind != NS_RANK_NL) || ky_lo < 0 || ky_hi <= ky_lo || ky_hi > c->p.N)
+      return fail(c, NS_ERR_INVALID_ARG, "need a known pass kind and 0 <= ky_lo < ky_hi <= N");
+    for (int i = 0; i < 3; ++i)
+      if (!std::isfinite(delta[i])) return fail(c, NS_ERR_INVALID_ARG, "non-finite shift");
+    c->solver->rank_pencil(kind, delta, ky_lo, ky_hi);
+    return (int)NS_OK;
+  });
+}
+
+int ns_rank_slab(ns_ctx* c, int z_lo, int z_hi) {
+  return guarded(c, [&]() {
+    if (z_lo < 0 || z_hi <= z_lo || z_hi > c->p.N)
+      return fail(c, NS_ERR_INVALID_ARG, "need 0 <= z_lo < z_hi <= N");
+    c->solver->rank_slab(z_lo, z_hi);
     return (int)NS_OK;
   });
 }

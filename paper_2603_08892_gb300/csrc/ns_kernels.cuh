@@ -116,6 +116,7 @@ struct PencilArgs {
   cpx<T>* out[2];        // [5][N][N][M]
   int* err;
   double* epart;         // [tiles][2]: sums of w |S|^2 and w k^2 |S|^2 of the written state, or null
+  int iy0;               // first ky row of the launch (rank-range passes; 0 for a whole field)
 };
 
 template <typename T>
@@ -149,8 +150,8 @@ __global__ void __launch_bounds__(512) k_pencil(PencilArgs<T> a) {
   cpx<T>* buf = reinterpret_cast<cpx<T>*>(smem_raw);
   const int N = a.N, M = a.M, TX = a.TX;
   const int ntx = M / TX;
-  const int iy = blockIdx.x / ntx;
-  const int x0 = (blockIdx.x - iy * ntx) * TX;
+  const int iy = a.iy0 + blockIdx.x / ntx;
+  const int x0 = (blockIdx.x % ntx) * TX;
   const int tile = N * TX;
   cpx<T>* b[4] = {buf, buf + tile, buf + 2 * tile, buf + 3 * tile};
   const size_t fstride = (size_t)N * N * M;

@@ -556,7 +556,7 @@ __device__ __forceinline__ void pencil_tile(const PencilArgs<T>& a, int tile_id,
   cpx<T>* b3 = buf + 3 * tile;
   cpx<T>* tws = buf + (NFC == 1 && NS_PENCIL_STAGE_STATE ? 6 : pencil_tiles<T, N>(nF, nOut)) * tile;
   constexpr int ntx = M / TX;
-  const int iy = tile_id / ntx;
+  const int iy = a.iy0 + tile_id / ntx;  // (iy0: first ky row of a rank-range launch)
   const int x0 = (tile_id % ntx) * TX;
   const size_t fstride = (size_t)N * N * M;
   const int ky = kof(iy, N);

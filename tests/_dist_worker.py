@@ -88,3 +88,49 @@ def replica_timing(rank, world, port):
         bench.barrier(world)
     finally:
         dist.destroy_process_group()
+
+
+def decomposed_nonlinear_gpu(rank, world, port, prec):
+    """The same decomposed evaluation on the GPU: every rank runs the library's kernels on its
+    ranges (pencil pass on its ky rows, slab pass on its z planes) on one shared device, the
+    two all-to-all exchanges of the mixed fields and of the transformed products go through
+    gloo on host copies.  Compared with the single-process oracle and with one context's
+    whole-field evaluation."""
+    import math
+
+    import torch
+
+    from oracle import nonlinear as onl
+    from oracle import spectral as osp
+    from paper_2603_08892_gb300 import binding as ns
+    from paper_2603_08892_gb300 import decomp, inputs
+
+    _init(rank, world, port)
+    try:
+        torch.cuda.set_device(0)
+        N = 32
+        kmax = N / 2
+        dx = 2 * math.pi / N
+        delta = [0.3 * dx, 0.55 * dx, 0.8 * dx]
+        S = osp.set_velocity(inputs.random_solenoidal(N, 3, kcut=N / 2), kmax)
+        lo, hi = decomp.blocks(N, world)[rank]
+        with ns.Solver(N, 0.0, kmax, precision=prec) as s:
+            s.rank_set(ns.BUF_STATE, 1, lo, hi, S[:, :, lo:hi, :])  # own ky rows only
+            s.rank_pencil(ns.RANK_INIT, delta, lo, hi)
+            mixed = s.rank_get(ns.BUF_MIXED, 1, lo, hi)
+            slab = decomp.pencil_to_slab(torch.from_numpy(mixed)).numpy()
+            s.rank_set(ns.BUF_MIXED, 0, lo, hi, slab)
+            s.rank_slab(lo, hi)
+            ft = s.rank_get(ns.BUF_FT, 0, lo, hi)
+            back = decomp.slab_to_pencil(torch.from_numpy(ft)).numpy()
+            s.rank_set(ns.BUF_FT, 1, lo, hi, back)
+            s.rank_pencil(ns.RANK_NL, delta, lo, hi)
+            got = s.rank_get(ns.BUF_NL, 1, lo, hi)
+        with ns.Solver(N, 0.0, kmax, precision=prec) as s1:
+            whole = s1.nonlinear(delta, S)[:, :, lo:hi, :]
+        ref = onl.nonlinear(S, delta, kmax)[:, :, lo:hi, :]
+        err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+        assert err < (1e-12 if prec == 1 else 2e-5), err
+        assert np.linalg.norm(got - whole) <= (1e-14 if prec == 1 else 1e-6) * np.linalg.norm(whole)
+    finally:
+        dist.destroy_process_group()
