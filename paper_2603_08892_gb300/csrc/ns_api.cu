@@ -273,7 +273,7 @@ struct Solver : SolverBase {
   bool clus = false;
   int cl_var = 1;                  // thread-count variant of the cluster kernel
   // compiled tile alternatives chosen by the autotuner (K2Cfg variant bits: 1 pencil width,
-  // 2 inverse-y width, 4 x rows, 8 forward-y width; 0 = every default)
+  // 2 inverse-y width, 4 x rows, 8 forward-y width, 16 pencil at 64 registers; 0 = defaults)
   int vsel = 0;
   int cl_ncl = -1;                 // clusters the device holds at once (-1: not yet queried)
   long long cl_spin = 1ll << 20;   // polls of its bounded TMA wait
@@ -432,6 +432,8 @@ struct Solver : SolverBase {
       if (k2.has_alt) {
         allow(k2.alt.pencil1r[0], k2.alt.smP1);
         allow(k2.alt.pencil1r[1], k2.alt.smP1);
+        allow(k2.pencil1r64[0], k2.smP1);
+        allow(k2.pencil1r64[1], k2.smP1);
         allow(k2.alt.yinv, k2.alt.smYI);
         allow(k2.alt.yfwd, k2.alt.smY);
         allow(k2.alt.xrow, k2.alt.smX);
@@ -729,6 +731,8 @@ struct Solver : SolverBase {
     const bool rog = a.nF == 1 && a.nOut == 1 && !a.epart && (a.mode == MODE_ROG_1 || a.mode == MODE_ROG_2);
     if (use2 && rog && (vsel & 1))  // the autotuner's alternative pencil width
       k2.alt.pencil1r[a.mode == MODE_ROG_1 ? 0 : 1]<<<(M / k2.alt.TX) * R, k2.alt.NTP, k2.alt.smP1, st>>>(a);
+    else if (use2 && rog && (vsel & 16))  // the alternative register budget
+      k2.pencil1r64[a.mode == MODE_ROG_1 ? 0 : 1]<<<(M / k2.TX) * R, k2.NTP, k2.smP1, st>>>(a);
     else if (use2)
       (a.nF == 1 && a.nOut == 1   ? (a.epart                  ? k2.pencil1e
                                      : a.mode == MODE_ROG_1 ? k2.pencil1r[0]
@@ -1110,7 +1114,7 @@ struct Solver : SolverBase {
     if (const char* e = std::getenv("NS_CL_SPIN")) cl_spin = std::max(1ll, std::atoll(e));
     // NS_TILE_VARIANT=bits forces the compiled tile alternatives (bits of K2Cfg's variant)
     const char* fv = std::getenv("NS_TILE_VARIANT");
-    if (fv && *fv) vsel = (use2 && k2.has_alt) ? (std::atoi(fv) & 15) : 0;
+    if (fv && *fv) vsel = (use2 && k2.has_alt) ? (std::atoi(fv) & 31) : 0;
     const char* fcl = std::getenv("NS_SLAB_CLUSTER");
     const bool can_cl = use2 && k2.slabcl[0] && !(fcl && std::string(fcl) == "0") && cl_clusters() > 0;
     if (fcl && std::string(fcl) == "1" && can_cl) {  // forced cluster pass (NS_CL_VARIANT 0 or 1)
@@ -1142,7 +1146,7 @@ struct Solver : SolverBase {
     const std::string path = cache_path(),
                       key = tune_key() + (can_pipe ? "|g4p" : "|g4") + (can_cl ? "c" + std::to_string(k2.CLS) : "") +
                             (can_alt ? "|v" + std::to_string(k2.alt.TX) + "," + std::to_string(k2.alt.TYI) + "," +
-                                           std::to_string(k2.alt.RX) + "," + std::to_string(k2.alt.TY)
+                                           std::to_string(k2.alt.RX) + "," + std::to_string(k2.alt.TY) + ",p64"
                                      : "");
     int g = 0;
     if (cache_lookup(path, key, &g)) {  // value = 4096 vsel + 4 G + mode
@@ -1236,9 +1240,17 @@ struct Solver : SolverBase {
         CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
         return ms;
       };
-      const float p0 = time_pencil();
-      vsel ^= 1;
-      if (time_pencil() >= p0) vsel ^= 1;
+      float pbest = time_pencil();
+      for (int bit : {1, 16}) {  // the pencil alternatives are exclusive
+        vsel ^= bit;
+        const float ms = time_pencil();
+        if (ms < pbest) {
+          pbest = ms;
+          vsel &= ~(bit == 1 ? 16 : 1);
+        } else {
+          vsel ^= bit;
+        }
+      }
       sync_check();
     }
     prof.on = pon;

@@ -138,7 +138,8 @@ __host__ __device__ constexpr int alt_width(int w, int m, int cap, int minw) {
 
 // Tile shapes of size N.  V selects compiled alternatives for the autotuner, one bit per
 // kernel family: bit 0 the pencil width TX, bit 1 the inverse-y width TYI, bit 2 the x-row
-// count RX, bit 3 the forward-y width TY (V = 0: the defaults).
+// count RX, bit 3 the forward-y width TY, bit 4 the pencil's register budget (64: one more
+// resident block) (V = 0: the defaults).
 template <typename T, int N, int V = 0>
 struct K2Cfg {
   static constexpr int M = N / 2;
@@ -166,7 +167,8 @@ struct K2Cfg {
 #ifndef NS_PENCIL_REGS
 #define NS_PENCIL_REGS 80
 #endif
-  static constexpr int MINB_P = cmax(1, cmin(8, 65536 / (NTP * NS_PENCIL_REGS)));
+  // (variant bit 16: the pencil held to 64 registers, one more resident block)
+  static constexpr int MINB_P = cmax(1, cmin(8, 65536 / (NTP * ((V & 16) ? 64 : NS_PENCIL_REGS))));
   // forward y pass: TY columns of N in a tile of about 32 KB (measured at 256^3 FP32: 16
   // columns, 0.133 ms per step against 0.141 for 8)
   static constexpr int TY0 = (NS_YF_LINES > 0 && M % NS_YF_LINES == 0 && NS_YF_LINES % MINW == 0)
@@ -1119,6 +1121,7 @@ struct K2Entry {
     int TX = 0, NTP = 0, TY = 0, NTY = 0, TYI = 0, NTYI = 0, RX = 0, NTX = 0;
     size_t smP1 = 0, smY = 0, smYI = 0, smX = 0;
   } alt;
+  void (*pencil1r64[2])(PencilArgs<T>) = {nullptr, nullptr};  // variant 16 (64 registers)
   bool has_alt = false;
 };
 
@@ -1184,6 +1187,8 @@ K2Entry<T> make_k2_entry() {
     e.alt.smP1 = (3 * (size_t)lf_rows<T, A::TX>(N) * A::TX + tw_elems(N)) * sizeof(cpx<T>);
     e.alt.smY = ((size_t)lf_rows<T, A::TY>(N) * A::TY + tw_elems(N)) * sizeof(cpx<T>);
     e.alt.smX = ((size_t)A::XELEMS + tw_elems(N)) * sizeof(cpx<T>);
+    e.pencil1r64[0] = k2_pencil<T, N, 1, 1, false, MODE_ROG_1, 16>;
+    e.pencil1r64[1] = k2_pencil<T, N, 1, 1, false, MODE_ROG_2, 16>;
   }
   return e;
 }

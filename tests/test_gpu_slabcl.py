@@ -89,7 +89,7 @@ def test_tile_variants_match_oracle(ns, report, monkeypatch, tmp_path, N):
     monkeypatch.setenv("NS_AUTOTUNE_CACHE", str(tmp_path / "tune.json"))
     dt = 0.5 * math.pi / N
     states = {}
-    for v in (0, 15):
+    for v in (0, 15, 16):
         monkeypatch.setenv("NS_TILE_VARIANT", str(v))
         with ns.Solver(N, NU, N / 2, scheme=ns.RK2_PS_RANDOM, precision=ns.FP32, seed=12345) as s:
             s.set_velocity(u)
@@ -105,3 +105,4 @@ def test_tile_variants_match_oracle(ns, report, monkeypatch, tmp_path, N):
     report("tile_alternatives_rogallo_step_N%d_fp32" % N, err, 2e-5)
     assert err < 2e-5
     assert rel(states[15], states[0]) < 1e-6
+    assert rel(states[16], ref) < 2e-5 and rel(states[16], states[0]) < 1e-6
