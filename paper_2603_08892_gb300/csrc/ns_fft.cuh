@@ -48,6 +48,31 @@ __device__ __forceinline__ cpx<T> mul_conj(cpx<T> a, cpx<T> b) {
   return mk(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
 }
 
+// Packed single-precision pairs: on sm_100 and later one instruction adds (or fuses a
+// multiply-add into) both halves of a complex value, each half rounded exactly as the scalar
+// operation.  The FP32 butterflies below use them for their pure additions (NS_PACKED_F32=0
+// keeps the scalar forms).
+#ifndef NS_PACKED_F32
+#define NS_PACKED_F32 1
+#endif
+__device__ __forceinline__ float2 as_f2(cpx<float> a) { return make_float2(a.x, a.y); }
+__device__ __forceinline__ cpx<float> as_c(float2 a) { return mk<float>(a.x, a.y); }
+__device__ __forceinline__ cpx<float> padd(cpx<float> a, cpx<float> b) {
+  return as_c(__fadd2_rn(as_f2(a), as_f2(b)));
+}
+// a - b as fma(b, -1, a): one rounding, the same value as the subtraction
+__device__ __forceinline__ cpx<float> psub(cpx<float> a, cpx<float> b) {
+  return as_c(__ffma2_rn(as_f2(b), make_float2(-1.f, -1.f), as_f2(a)));
+}
+// r b, r real
+__device__ __forceinline__ cpx<float> pmul(float r, cpx<float> b) {
+  return as_c(__fmul2_rn(make_float2(r, r), as_f2(b)));
+}
+// a + r b, r real (one rounding per half)
+__device__ __forceinline__ cpx<float> pfma(float r, cpx<float> b, cpx<float> a) {
+  return as_c(__ffma2_rn(make_float2(r, r), as_f2(b), as_f2(a)));
+}
+
 // read-only cached load of a complex value
 __device__ __forceinline__ cpx<float> ldg(const cpx<float>* p) {
   float2 v = __ldg(reinterpret_cast<const float2*>(p));
@@ -131,6 +156,53 @@ struct DFT<T, 8> {
     v[7] = e[3] - o3;
   }
 };
+
+#if NS_PACKED_F32
+// FP32 forms of the 2-, 4- and 8-point DFTs above with the additions packed; the products by
+// s i stay scalar (a swap of the halves, folded into the additions that use them).
+template <>
+struct DFT<float, 2> {
+  static __device__ __forceinline__ void run(cpx<float>* v, float) {
+    const cpx<float> a = v[0], b = v[1];
+    v[0] = padd(a, b);
+    v[1] = psub(a, b);
+  }
+};
+
+template <>
+struct DFT<float, 4> {
+  static __device__ __forceinline__ void run(cpx<float>* v, float s) {
+    const cpx<float> a = v[0], b = v[1], c = v[2], d = v[3];
+    const cpx<float> p0 = padd(a, c), p1 = psub(a, c), q0 = padd(b, d), t = psub(b, d);
+    v[0] = padd(p0, q0);
+    v[2] = psub(p0, q0);
+    v[1] = mk<float>(p1.x - s * t.y, p1.y + s * t.x);  // p1 + s i t
+    v[3] = mk<float>(p1.x + s * t.y, p1.y - s * t.x);  // p1 - s i t
+  }
+};
+
+template <>
+struct DFT<float, 8> {
+  static __device__ __forceinline__ void run(cpx<float>* v, float s) {
+    const float r2 = 0.70710678118654752440f;
+    cpx<float> e[4] = {v[0], v[2], v[4], v[6]};
+    cpx<float> o[4] = {v[1], v[3], v[5], v[7]};
+    DFT<float, 4>::run(e, s);
+    DFT<float, 4>::run(o, s);
+    // w8^1 o1 = r2 (o1 + s i o1), w8^3 o3 = r2 (s i o3 - o3), w8^2 o2 = s i o2
+    const cpx<float> t1 = mk<float>(o[1].x - s * o[1].y, o[1].y + s * o[1].x);
+    const cpx<float> t3 = mk<float>(-s * o[3].y - o[3].x, s * o[3].x - o[3].y);
+    v[0] = padd(e[0], o[0]);
+    v[4] = psub(e[0], o[0]);
+    v[1] = pfma(r2, t1, e[1]);
+    v[5] = pfma(-r2, t1, e[1]);
+    v[3] = pfma(r2, t3, e[3]);
+    v[7] = pfma(-r2, t3, e[3]);
+    v[2] = mk<float>(e[2].x - s * o[2].y, e[2].y + s * o[2].x);
+    v[6] = mk<float>(e[2].x + s * o[2].y, e[2].y - s * o[2].x);
+  }
+};
+#endif
 
 // Butterflies held per thread per stage (R * KB <= 16 values in registers).
 template <int R>

@@ -76,6 +76,52 @@ struct DFT<T, 16> {
   }
 };
 
+#if NS_PACKED_F32
+// FP32 form with packed additions (the 4-point DFTs above); the s i twiddle of a[2][2] is
+// folded into the additions of its column
+template <>
+struct DFT<float, 16> {
+  static __device__ __forceinline__ void run(cpx<float>* v, float s) {
+    const float c8 = 0.92387953251128675613f, s8 = 0.38268343236508977173f;
+    const float r2 = 0.70710678118654752440f;
+    cpx<float> a[4][4];
+#pragma unroll
+    for (int n1 = 0; n1 < 4; ++n1) {
+      cpx<float> q[4] = {v[n1], v[n1 + 4], v[n1 + 8], v[n1 + 12]};
+      DFT<float, 4>::run(q, s);
+#pragma unroll
+      for (int k2 = 0; k2 < 4; ++k2) a[n1][k2] = q[k2];
+    }
+    a[1][1] = a[1][1] * mk<float>(c8, s * s8);
+    a[1][2] = pmul(r2, mk<float>(a[1][2].x - s * a[1][2].y, a[1][2].y + s * a[1][2].x));
+    a[1][3] = a[1][3] * mk<float>(s8, s * c8);
+    a[2][1] = pmul(r2, mk<float>(a[2][1].x - s * a[2][1].y, a[2][1].y + s * a[2][1].x));
+    a[2][3] = pmul(r2, mk<float>(-a[2][3].x - s * a[2][3].y, s * a[2][3].x - a[2][3].y));
+    a[3][1] = a[3][1] * mk<float>(s8, s * c8);
+    a[3][2] = pmul(r2, mk<float>(-a[3][2].x - s * a[3][2].y, s * a[3][2].x - a[3][2].y));
+    a[3][3] = a[3][3] * mk<float>(-c8, -s * s8);
+#pragma unroll
+    for (int k2 = 0; k2 < 4; ++k2) {
+      const cpx<float> x0 = a[0][k2], x1 = a[1][k2], x3 = a[3][k2];
+      cpx<float> p0, p1;
+      if (k2 == 2) {  // x2 = s i a[2][2]
+        const cpx<float> y = a[2][2];
+        p0 = mk<float>(x0.x - s * y.y, x0.y + s * y.x);
+        p1 = mk<float>(x0.x + s * y.y, x0.y - s * y.x);
+      } else {
+        p0 = padd(x0, a[2][k2]);
+        p1 = psub(x0, a[2][k2]);
+      }
+      const cpx<float> q0 = padd(x1, x3), t = psub(x1, x3);
+      v[k2] = padd(p0, q0);
+      v[8 + k2] = psub(p0, q0);
+      v[4 + k2] = mk<float>(p1.x - s * t.y, p1.y + s * t.x);
+      v[12 + k2] = mk<float>(p1.x + s * t.y, p1.y - s * t.x);
+    }
+  }
+};
+#endif
+
 // Line-fast tiles [e][line] of W lines.  When a row is narrower than the 32 banks of shared
 // memory, rows 8 apart share banks (the radix-8 first stage writes rows 8 j + r); NS_LF_PAD=1
 // inserts one empty row after every 8 (element row e at row lf_row(e) of lf_rows(n)).  Off by
