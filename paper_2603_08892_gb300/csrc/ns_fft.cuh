@@ -68,6 +68,20 @@ __device__ __forceinline__ cpx<float> psub(cpx<float> a, cpx<float> b) {
 __device__ __forceinline__ cpx<float> pmul(float r, cpx<float> b) {
   return as_c(__fmul2_rn(make_float2(r, r), as_f2(b)));
 }
+// a w as two packed operations: a.x (w.x, w.y) + a.y (-w.y, w.x) (NS_PACKED_CMUL)
+#ifndef NS_PACKED_CMUL
+#define NS_PACKED_CMUL 0
+#endif
+__device__ __forceinline__ cpx<float> pcmul(cpx<float> a, cpx<float> w) {
+  return as_c(__ffma2_rn(make_float2(a.y, a.y), make_float2(-w.y, w.x),
+                         __fmul2_rn(make_float2(a.x, a.x), as_f2(w))));
+}
+template <typename T>
+__device__ __forceinline__ cpx<T> tw_mul(cpx<T> a, cpx<T> w) { return a * w; }
+#if NS_PACKED_CMUL
+template <>
+__device__ __forceinline__ cpx<float> tw_mul<float>(cpx<float> a, cpx<float> w) { return pcmul(a, w); }
+#endif
 // a + r b, r real (one rounding per half)
 __device__ __forceinline__ cpx<float> pfma(float r, cpx<float> b, cpx<float> a) {
   return as_c(__ffma2_rn(make_float2(r, r), as_f2(b), as_f2(a)));

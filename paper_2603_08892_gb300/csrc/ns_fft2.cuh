@@ -186,19 +186,19 @@ __device__ __forceinline__ void stage_twiddles(cpx<T>* w, const cpx<T>* __restri
   } else if constexpr (R == 4) {
     w[1] = ld(1);
     w[2] = ld(2);
-    w[3] = w[1] * w[2];
+    w[3] = tw_mul(w[1], w[2]);
   } else if constexpr ((R == 8 || R == 16) && NS_TW_PRODUCTS) {
     w[1] = ld(1);
     w[2] = ld(2);
     w[4] = ld(4);
-    w[3] = w[1] * w[2];
-    w[5] = w[1] * w[4];
-    w[6] = w[2] * w[4];
-    w[7] = w[3] * w[4];
+    w[3] = tw_mul(w[1], w[2]);
+    w[5] = tw_mul(w[1], w[4]);
+    w[6] = tw_mul(w[2], w[4]);
+    w[7] = tw_mul(w[3], w[4]);
     if constexpr (R == 16) {
       w[8] = ld(8);
 #pragma unroll
-      for (int r = 9; r < 16; ++r) w[r] = w[r - 8] * w[8];
+      for (int r = 9; r < 16; ++r) w[r] = tw_mul(w[r - 8], w[8]);
     }
   } else {
 #pragma unroll
@@ -239,7 +239,7 @@ __device__ __forceinline__ void cstage(const Src& src, const Dst& dst, const cpx
       cpx<T> w[R];
       stage_twiddles<T, R>(w, tw, base, -s);
 #pragma unroll
-      for (int r = 1; r < R; ++r) v[r] = v[r] * w[r];
+      for (int r = 1; r < R; ++r) v[r] = tw_mul(v[r], w[r]);
     }
     DFT<T, R>::run(v, s);
   };

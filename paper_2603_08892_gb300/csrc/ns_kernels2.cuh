@@ -42,8 +42,13 @@ struct MemNC {
   static __device__ __forceinline__ cpx<T> ldw(const cpx<T>* p) { return *p; }
   template <typename T>
   static __device__ __forceinline__ void st(cpx<T>* p, cpx<T> v) { *p = v; }
+  // two consecutive FP32 modes (16-byte aligned)
+  static __device__ __forceinline__ float4 ld2(const cpx<float>* p) { return __ldg(reinterpret_cast<const float4*>(p)); }
+  static __device__ __forceinline__ void st2(cpx<float>* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
 };
 struct MemCG {
+  static __device__ __forceinline__ float4 ld2(const cpx<float>* p) { return __ldcg(reinterpret_cast<const float4*>(p)); }
+  static __device__ __forceinline__ void st2(cpx<float>* p, float4 v) { __stcg(reinterpret_cast<float4*>(p), v); }
   static __device__ __forceinline__ cpx<float> ld(const cpx<float>* p) {
     const float2 v = __ldcg(reinterpret_cast<const float2*>(p));
     return mk<float>(v.x, v.y);
@@ -855,6 +860,9 @@ __global__ void __launch_bounds__(K2Cfg<T, N, V>::NTY, 2) k2_yfwd(SlabArgs<T> a)
 }
 
 // ---- slab pass: x rows --------------------------------------------------------------
+#ifndef NS_XROW_PAIRS
+#define NS_XROW_PAIRS 1
+#endif
 // One tile: RX consecutive rows (plane, y) of the group.  Each row holds the half spectra
 // (kx < N/2, the Nyquist mode zero) of 6 real fields, and two real rows share one complex line
 // of length N: the line of fields a and b is z = a + i b, whose full spectrum is
@@ -877,6 +885,45 @@ __device__ __forceinline__ void xrow_tile(const SlabArgs<T>& a, int tile_id, cpx
   const int nr = min(RX, rows_total - r0);
   const size_t sstride = (size_t)a.G * N * M;
 
+  // FP32 with NT a multiple of M / 2: every thread keeps one pair of modes (k, k + 1) and
+  // walks lines, so the loads and stores are 16 bytes wide and its indices loop-invariant
+  constexpr int H = M / 2;
+  constexpr bool PAIR = NS_XROW_PAIRS && sizeof(T) == 4 && NT % H == 0;
+  constexpr int GP = PAIR ? NT / H : 1;  // lines in flight per pass of the block
+  const int kp2 = 2 * (threadIdx.x % H), g0 = threadIdx.x / H;
+  if constexpr (PAIR) {
+    // 1) item (line = p RX + row, k pair): modes k, k + 1 of fields 2p and 2p + 1 give Z[k],
+    //    Z[k + 1], Z[N - k], Z[N - k - 1] of the line (k = 0: Z[0] from the real parts and
+    //    Z[M] = 0); all loads first, rows past the end of the group are zero
+    constexpr int KC = (NLI + GP - 1) / GP;
+    float4 xa[KC], xb[KC];
+#pragma unroll
+    for (int c = 0; c < KC; ++c) {
+      const int line = g0 + c * GP, p = line / RX, row = line % RX;
+      xa[c] = xb[c] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (act && (NLI % GP == 0 || line < NLI) && row < nr) {
+        const cpx<float>* src = reinterpret_cast<const cpx<float>*>(a.scr) + 2 * p * sstride + (size_t)(r0 + row) * M + kp2;
+        xa[c] = MP::ld2(src);
+        xb[c] = MP::ld2(src + sstride);
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < KC; ++c) {
+      const int line = g0 + c * GP;
+      if (act && (NLI % GP == 0 || line < NLI)) {
+        const float4 A = xa[c], B = xb[c];
+        if (kp2 == 0) {
+          L.put(line, 0, mk<T>(A.x, B.x));
+          L.put(line, M, mk<T>(0, 0));
+        } else {
+          L.put(line, kp2, mk<T>(A.x - B.y, A.y + B.x));
+          L.put(line, N - kp2, mk<T>(A.x + B.y, B.x - A.y));
+        }
+        L.put(line, kp2 + 1, mk<T>(A.z - B.w, A.w + B.z));
+        L.put(line, N - kp2 - 1, mk<T>(A.z + B.w, B.z - A.w));
+      }
+    }
+  } else {
   // 1) item (p, row, k) reads mode k of fields 2p and 2p + 1 and writes Z[k] and Z[N - k] of
   //    line p RX + row (k = 0: Z[0] from the real parts and Z[M] = 0).  Every load is issued
   //    before any store; rows past the end of the group are zero.
@@ -910,6 +957,7 @@ __device__ __forceinline__ void xrow_tile(const SlabArgs<T>& a, int tile_id, cpx
         L.put(line, N - k, mk<T>(A.x + B.y, B.x - A.y));  // conj(A) + i conj(B)
       }
     }
+  }
   }
   __syncthreads();
   // 2) the 3 RX inverse transforms in one in-place call
@@ -945,7 +993,25 @@ __device__ __forceinline__ void xrow_tile(const SlabArgs<T>& a, int tile_id, cpx
   cfft_ip<T, N, 1, NLF, NT, false, -1, true, C::RXR>(WorkTile<T, N, NLF, false>{buf}, buf, tws);
   __syncthreads();
 
-  // 5) split and store: item (line, k), k < M
+  // 5) split and store: item (line, k), k < M (pairs of modes in the FP32 layout above)
+  if constexpr (PAIR) {
+#pragma unroll
+    for (int c = 0; c < (NLF + GP - 1) / GP; ++c) {
+      const int line = g0 + c * GP;
+      if (!act || (NLF % GP != 0 && line >= NLF)) break;
+      const cpx<T> P0 = L.get(line, kp2), Q0 = L.get(line, kp2 == 0 ? 0 : N - kp2);
+      const cpx<T> P1 = L.get(line, kp2 + 1), Q1 = L.get(line, N - kp2 - 1);
+      const float4 Fa = make_float4(0.5f * (P0.x + Q0.x), 0.5f * (P0.y - Q0.y), 0.5f * (P1.x + Q1.x), 0.5f * (P1.y - Q1.y));
+      const float4 Fb = make_float4(0.5f * (P0.y + Q0.y), 0.5f * (Q0.x - P0.x), 0.5f * (P1.y + Q1.y), 0.5f * (Q1.x - P1.x));
+      const bool own = line < RX;
+      const int ra = own ? line : line - RX, rb = own ? line : line - RX + RXh;
+      const int fa = own ? 0 : 2, fb = own ? 1 : 2;
+      cpx<float>* scr = reinterpret_cast<cpx<float>*>(a.scr);
+      if (ra < nr) MP::st2(&scr[fa * sstride + (size_t)(r0 + ra) * M + kp2], Fa);
+      if (rb < nr) MP::st2(&scr[fb * sstride + (size_t)(r0 + rb) * M + kp2], Fb);
+    }
+    return;
+  }
   constexpr int NO = NLF * M;
   for (int i = threadIdx.x; act && i < NO; i += NT) {
     const int line = i / M, k = i % M;
