@@ -39,6 +39,16 @@ template <typename T>
 __device__ __forceinline__ cpx<T> operator*(T s, cpx<T> a) { return mk(s * a.x, s * a.y); }
 template <typename T>
 __device__ __forceinline__ cpx<T> conjg(cpx<T> a) { return mk(a.x, -a.y); }
+// Complex product in one fixed rounding order (the a.y products rounded, then one fused
+// multiply-add per part), the same bits wherever it is compiled: used where two kernels must
+// form the same value (the shifted fields carried from a step's last pass and the same fields
+// formed again from the state).
+__device__ __forceinline__ cpx<float> cmul_fixed(cpx<float> a, cpx<float> b) {
+  return mk<float>(__fmaf_rn(a.x, b.x, -__fmul_rn(a.y, b.y)), __fmaf_rn(a.x, b.y, __fmul_rn(a.y, b.x)));
+}
+__device__ __forceinline__ cpx<double> cmul_fixed(cpx<double> a, cpx<double> b) {
+  return mk<double>(__fma_rn(a.x, b.x, -__dmul_rn(a.y, b.y)), __fma_rn(a.x, b.y, __dmul_rn(a.y, b.x)));
+}
 // multiply by s*i (s = +1 or -1)
 template <typename T>
 __device__ __forceinline__ cpx<T> mul_si(cpx<T> a, T s) { return mk(-s * a.y, s * a.x); }

@@ -230,7 +230,7 @@ struct SmTile {  // shared [e][line]
 };
 template <class MP, typename T>
 __device__ __forceinline__ cpx<T> phase3p(const cpx<T>* tab, int N, int ix, int iy, int iz) {
-  return (MP::ld(&tab[ix]) * MP::ld(&tab[N + iy])) * MP::ld(&tab[2 * N + iz]);
+  return cmul_fixed(cmul_fixed(MP::ld(&tab[ix]), MP::ld(&tab[N + iy])), MP::ld(&tab[2 * N + iz]));
 }
 // pencil output: shift, optional i kz factor, from a shared component tile
 template <typename T, int N, int W, class MP>
@@ -241,7 +241,7 @@ struct PencilOutSrc {
   bool deriv;
   __device__ __forceinline__ cpx<T> get(int line, int e) const {
     cpx<T> v = s[lf_idx<T, W>(e, line)];
-    if (sh) v = v * phase3p<MP>(sh, N, x0 + line, iy, e);
+    if (sh) v = cmul_fixed(v, phase3p<MP>(sh, N, x0 + line, iy, e));
     if (deriv) v = mul_si(v, (T)kof(e, N));
     return v;
   }
@@ -476,7 +476,7 @@ __device__ __forceinline__ void pencil_spectral_one(const PencilArgs<T>& a, cpx<
 
   const bool pre = nOut == 1 && a.osh[0] != nullptr;
   cpx<T> oxy = mk<T>(1, 0);
-  if (pre) oxy = MP::ld(&a.osh[0][kx]) * MP::ld(&a.osh[0][N + iy]);
+  if (pre) oxy = cmul_fixed(MP::ld(&a.osh[0][kx]), MP::ld(&a.osh[0][N + iy]));
   const bool useE = mode != MODE_INIT && mode != MODE_NL && mode != MODE_PROJECT;
   T e1xy = 1, ehxy = 1;
   if (useE) {
@@ -525,7 +525,7 @@ __device__ __forceinline__ void pencil_spectral_one(const PencilArgs<T>& a, cpx<
           Eh = ehxy * a.ifac[N + iz];
         }
         cpx<T> shz = oxy;
-        if (pre) shz = oxy * MP::ld(&a.osh[0][2 * N + iz]);
+        if (pre) shz = cmul_fixed(oxy, MP::ld(&a.osh[0][2 * N + iz]));
         T m2 = 0;  // |S|^2 of the written state (EP: final stages with a.epart)
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
@@ -533,7 +533,7 @@ __device__ __forceinline__ void pencil_spectral_one(const PencilArgs<T>& a, cpx<
           cpx<T> sn = stage_combine<T, MP>(a, c, c * fstride + g, nv[c], s0[c][j], s1, E1, Eh, mode);
           shell_record<T, MP>(a, c, kx, ky, kz, sn);
           if constexpr (EP) m2 += sn.x * sn.x + sn.y * sn.y;
-          if (pre) sn = sn * shz;
+          if (pre) sn = cmul_fixed(sn, shz);
           buf[c * tile + e] = sn;
         }
         if constexpr (EP) {
@@ -635,7 +635,7 @@ __device__ __forceinline__ void pencil_tile(const PencilArgs<T>& a, int tile_id,
 
     // 2b) stage combine per component, the state of the thread's modes loaded together
     cpx<T> oxy = mk<T>(1, 0);
-    if (pre) oxy = MP::ld(&a.osh[0][kx]) * MP::ld(&a.osh[0][N + iy]);
+    if (pre) oxy = cmul_fixed(MP::ld(&a.osh[0][kx]), MP::ld(&a.osh[0][N + iy]));
     const bool useE = a.mode != MODE_INIT && a.mode != MODE_NL && a.mode != MODE_PROJECT;
     T e1xy = 1, ehxy = 1;
     if (useE) {
@@ -680,7 +680,7 @@ __device__ __forceinline__ void pencil_tile(const PencilArgs<T>& a, int tile_id,
             eacc += wm;
             dacc += wm * (T)(kx * kx + ky * ky + kz * kz);
           }
-          if (pre) sn = sn * (oxy * MP::ld(&a.osh[0][2 * N + iz]));
+          if (pre) sn = cmul_fixed(sn, cmul_fixed(oxy, MP::ld(&a.osh[0][2 * N + iz])));
           bc(c)[e] = sn;
         }
       }
