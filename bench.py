@@ -547,7 +547,8 @@ def main():
         line["accuracy_t9"] = accuracy_leg(ns, inputs, stream, local, line)
 
     # batched ensemble: 64 Taylor-Green members with 1% perturbations, 16 each of
-    # N = 32, 64, 96, 128, Rogallo RK2 FP32, one persistent launch per call
+    # N = 32, 64, 96, 128, Rogallo RK2 FP32, schedule chosen by the batch's tuner (one
+    # persistent launch per call, or one grid launch per pass and size class)
     if args.batch_steps > 0:
         Ns = [32] * 16 + [64] * 16 + [96] * 16 + [128] * 16
         dts = [0.5 * (2 * math.pi / n) / 2.0 for n in Ns]
@@ -566,12 +567,16 @@ def main():
         torch.cuda.synchronize()
         msb = reduce_max(e0.elapsed_time(e1), world)
         Eb, _ = b.energy()
+        gran, qsm = b.schedule()
         model = sum(44.0 * n ** 3 * 4.0 for n in Ns)
         line["batched_ensemble"] = {
             "members": len(Ns), "sizes": "16 x {32, 64, 96, 128}", "steps": Kb,
             "member_steps_per_s": world * len(Ns) * Kb / (msb / 1000.0),
             "ensemble_steps_per_s": world * Kb / (msb / 1000.0), "ms_per_step": msb / Kb,
-            "launches_per_call": 1, "persistent_ctas": b.grid(),
+            "schedule": {"kind": "grid" if gran == 0 else "persistent", "tiles_per_ticket": gran,
+                         "ctas_per_sm": qsm},
+            "launches_per_call": 4 * (2 + 9 * Kb) if gran == 0 else 1,
+            "persistent_ctas": b.grid(),
             "gcells_per_s": world * sum(n ** 3 for n in Ns) * Kb / (msb / 1000.0) / 1e9,
             "model_bytes_per_step": model,
             "frac_hbm": (model / (msb / Kb / 1000.0) / 1e9) / hbm,

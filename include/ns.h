@@ -241,12 +241,16 @@ int ns_profile(ns_ctx* ctx, int enable);
 int ns_profile_read(ns_ctx* ctx, int kind, double* total_ms, int64_t* timed, int64_t* launches);
 
 /* ---- Batched ensembles (no counterpart in the paper) -----------------------------------
- * Independent simulations of uneven N advanced together by ONE persistent kernel launch per
- * ns_batch_step call (captured in a CUDA graph and replayed), each member running the RK2
+ * Independent simulations of uneven N advanced together, each member running the RK2
  * phase-shift random (Rogallo, Sec. 4.2) or approx scheme exactly as a single context does.
- * The CTAs of the launch take (step, pass, member, tile) work items in order from an atomic
- * counter and wait, with a bounded spin, until the member's earlier passes are complete;
- * an expired wait ends the launch with NS_ERR_TIMEOUT instead of hanging.
+ * Two schedules of the same tile bodies (the tuner picks one; the results are the same bits):
+ *  - persistent: ONE kernel launch per ns_batch_step call (captured in a CUDA graph and
+ *    replayed) whose CTAs take (step, pass, member, tile) work items in order from an atomic
+ *    counter and wait, with a bounded spin, until the member's earlier passes are complete;
+ *    an expired wait ends the launch with NS_ERR_TIMEOUT instead of hanging;
+ *  - grid (gran 0): every pass of each size class is one ordinary grid launch (tiles x the
+ *    class's members) on a stream of its own, the classes overlapping; nothing waits on the
+ *    device.
  * Supported member sizes: N in {16, 32, 48, 64, 96, 128}; spherical truncation. */
 typedef struct ns_batch ns_batch;
 /* count members (1..1024) with sizes N[i], viscosities nu[i], truncation kmax[i] and shift
@@ -272,13 +276,13 @@ int ns_batch_set_spin_limit(ns_batch* b, long long polls);
 int ns_batch_test_stall(ns_batch* b, int on);
 /* CTAs of the last persistent launch (diagnostics). */
 int ns_batch_grid(ns_batch* b);
-/* Schedule of the persistent launch: gran tiles per work-list ticket (the ticket, the
+/* Schedule: gran tiles per work-list ticket of the persistent launch (the ticket, the
  * bounded wait and the completion fence are paid once per gran tiles) and ctas_per_sm CTAs
- * per SM (0: as many as fit).  The first ns_batch_step tunes both on the ensemble (each
- * candidate times one step; the members' states, times and step counters are saved before
- * and restored after) unless ns_batch_set_schedule was called, NS_BATCH_SCHEDULE="g,q" is set
- * or NS_AUTOTUNE=0.  Results do not depend on the schedule.  NS_ERR_INVALID_ARG for gran < 1
- * or ctas_per_sm < 0. */
+ * per SM (0: as many as fit); gran 0 selects the grid schedule (ctas_per_sm unused).  The
+ * first ns_batch_step tunes both on the ensemble (each candidate times one step; the
+ * members' states, times and step counters are saved before and restored after) unless
+ * ns_batch_set_schedule was called, NS_BATCH_SCHEDULE="g,q" is set or NS_AUTOTUNE=0.
+ * Results do not depend on the schedule.  NS_ERR_INVALID_ARG for gran < 0 or ctas_per_sm < 0. */
 int ns_batch_set_schedule(ns_batch* b, int gran, int ctas_per_sm);
 int ns_batch_schedule(ns_batch* b, int* gran, int* ctas_per_sm);
 

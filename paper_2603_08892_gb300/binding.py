@@ -453,7 +453,8 @@ class Batch:
         return _batch_grid(self._h)
 
     def set_schedule(self, gran, ctas_per_sm=0):
-        """Tiles per work-list ticket and CTAs per SM of the persistent launch (no tuning)."""
+        """Tiles per work-list ticket and CTAs per SM of the persistent launch (no tuning);
+        gran 0: the grid schedule (one launch per pass and size class)."""
         self._check(_batch_set_schedule(self._h, gran, ctas_per_sm))
 
     def schedule(self):

@@ -23,7 +23,7 @@ int batch_tune(ns_batch* b, const double* dt) {
   if (const char* f = std::getenv("NS_BATCH_SCHEDULE")) {
     int g = 1, q = 0;
     if (std::sscanf(f, "%d,%d", &g, &q) >= 1) {
-      b->gran = g > 0 ? g : 1;
+      b->gran = g >= 0 ? g : 1;
       b->per_sm_req = q > 0 ? q : 0;
     }
     return NS_OK;
@@ -66,9 +66,9 @@ int batch_tune(ns_batch* b, const double* dt) {
     else
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&maxq, k_batch<double>, nt, smem);
   }
-  for (int g : {1, 2, 4, 8}) {
+  for (int g : {0, 1, 2, 4, 8}) {  // 0: the grid schedule (one launch per pass and size class)
     for (int q : {0, 1}) {
-      if (q == 1 && maxq <= 1) continue;
+      if (q == 1 && (maxq <= 1 || g == 0)) continue;
       b->gran = g;
       b->per_sm_req = q;
       rc = batch_step_any(b, dt, 1);  // untimed (graph capture)
@@ -167,6 +167,12 @@ int ns_batch_destroy(ns_batch* b) {
   cudaFree(b->d_done);
   cudaFree(b->d_flags);
   cudaFree(b->d_tab);
+  cudaFree(b->d_cls);
+  for (int z = 0; z < kNumSizes; ++z) {
+    if (b->cls_st[z]) cudaStreamDestroy(b->cls_st[z]);
+    if (b->ev_join[z]) cudaEventDestroy(b->ev_join[z]);
+  }
+  if (b->ev_fork) cudaEventDestroy(b->ev_fork);
   if (b->own_stream) cudaStreamDestroy(b->st);  // members were given the stream, not its ownership
   delete b;
   return NS_OK;
@@ -206,7 +212,7 @@ int ns_batch_step(ns_batch* b, const double* dt, int nsteps) {
 }
 
 int ns_batch_set_schedule(ns_batch* b, int gran, int ctas_per_sm) {
-  if (!b || gran < 1 || ctas_per_sm < 0) return NS_ERR_INVALID_ARG;
+  if (!b || gran < 0 || ctas_per_sm < 0) return NS_ERR_INVALID_ARG;
   b->gran = gran;
   b->per_sm_req = ctas_per_sm;
   b->tuned = true;

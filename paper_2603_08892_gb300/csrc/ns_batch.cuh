@@ -17,6 +17,12 @@
 // kernel records NS_ERR_TIMEOUT in a device flag, raises an abort flag that every other
 // waiter also polls, and returns.  Data produced by other CTAs of the launch is read with
 // L2-coherent loads (.cg), never through L1 or the read-only path.
+//
+// Grid schedule (gran = 0).  The same items without a work list: the members of each size
+// class run on a stream of their own, and every pass of the class is one ordinary grid launch
+// (blockIdx.x the tile, blockIdx.y the member within the class) with the block shape and
+// shared memory of that size alone.  Stream order separates the passes, so nothing waits on
+// the device; the classes overlap one another.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -107,41 +113,26 @@ __device__ __forceinline__ int upper_member(const int* off, int n, int r) {
   return lo;
 }
 
+// shift tables exp(i k delta) (Sec. 4.2, Eq. shift_operator_3d) in FP64 of the member's step
+// (slots alpha_s, beta_s = alpha_s + dx / 2, alpha_{s+1})
 template <typename T, int N>
-__device__ __noinline__ void run_item(const BatchMem<T>& bm, int pass, int step, int nsteps,
-                                      int tile, cpx<T>* smem) {
-  using C = K2Cfg<T, N>;
-  constexpr int M = N / 2;
-  const int NN = N;
-  if (pass == P_TAB) {
-    // shift tables exp(i k delta) (Sec. 4.2, Eq. shift_operator_3d) in FP64
-    for (int i = threadIdx.x; i < 9 * NN; i += blockDim.x) {
-      const int slot = i / (3 * NN), rem = i % (3 * NN), d = rem / NN, k = rem % NN;
-      const int s = slot == 2 ? step + 1 : step;
-      double delta = s <= nsteps ? bm.shifts[3 * s + d] : 0.0;
-      if (slot == 1) delta += 0.5 * bm.dx;
-      double sn, cs;
-      sincos((double)kof(k, NN) * delta, &sn, &cs);
-      MemCG::st(&bm.tab[i], mk<T>((T)cs, (T)sn));
-    }
-    return;
+__device__ __forceinline__ void batch_tab(const BatchMem<T>& bm, int step, int nsteps) {
+  for (int i = threadIdx.x; i < 9 * N; i += blockDim.x) {
+    const int slot = i / (3 * N), rem = i % (3 * N), d = rem / N, k = rem % N;
+    const int s = slot == 2 ? step + 1 : step;
+    double delta = s <= nsteps ? bm.shifts[3 * s + d] : 0.0;
+    if (slot == 1) delta += 0.5 * bm.dx;
+    double sn, cs;
+    sincos((double)kof(k, N) * delta, &sn, &cs);
+    MemCG::st(&bm.tab[i], mk<T>((T)cs, (T)sn));
   }
-  if (pass == P_Y1 || pass == P_Y2) {
-    constexpr int ntx = M / C::TYI;
-    yinv_tile<T, N, MemCG>(bm.sa, tile % ntx, tile / ntx, smem);
-    return;
-  }
-  if (pass == P_X1 || pass == P_X2) {
-    xrow_tile<T, N, MemCG>(bm.sa, tile, smem);
-    return;
-  }
-  if (pass == P_F1 || pass == P_F2) {
-    constexpr int ntx = M / C::TY;
-    yfwd_tile<T, N, MemCG>(bm.sa, tile % ntx, tile / ntx, smem);
-    return;
-  }
-  // pencil passes: INIT (pass < 0), P1, P2
+}
+
+// arguments of a pencil pass: INIT (pass < 0), P1 (ROG_1) or P2 (ROG_2)
+template <typename T>
+__device__ __forceinline__ PencilArgs<T> batch_pencil_args(const BatchMem<T>& bm, int pass, int step, int nsteps) {
   PencilArgs<T> a = bm.pa;
+  const int NN = bm.N;
   const cpx<T>* ta = bm.tab;
   const cpx<T>* tb = bm.tab + 3 * NN;
   const cpx<T>* tc = bm.tab + 6 * NN;
@@ -164,7 +155,34 @@ __device__ __noinline__ void run_item(const BatchMem<T>& bm, int pass, int step,
     a.nOut = step + 1 < nsteps ? 1 : 0;
     a.osh[0] = tc;
   }
-  pencil_tile<T, N, MemCG>(a, tile, smem);
+  return a;
+}
+
+template <typename T, int N>
+__device__ __noinline__ void run_item(const BatchMem<T>& bm, int pass, int step, int nsteps,
+                                      int tile, cpx<T>* smem) {
+  using C = K2Cfg<T, N>;
+  constexpr int M = N / 2;
+  if (pass == P_TAB) {
+    batch_tab<T, N>(bm, step, nsteps);
+    return;
+  }
+  if (pass == P_Y1 || pass == P_Y2) {
+    constexpr int ntx = M / C::TYI;
+    yinv_tile<T, N, MemCG>(bm.sa, tile % ntx, tile / ntx, smem);
+    return;
+  }
+  if (pass == P_X1 || pass == P_X2) {
+    xrow_tile<T, N, MemCG>(bm.sa, tile, smem);
+    return;
+  }
+  if (pass == P_F1 || pass == P_F2) {
+    constexpr int ntx = M / C::TY;
+    yfwd_tile<T, N, MemCG>(bm.sa, tile % ntx, tile / ntx, smem);
+    return;
+  }
+  // pencil passes: INIT (pass < 0), P1, P2
+  pencil_tile<T, N, MemCG>(batch_pencil_args(bm, pass, step, nsteps), tile, smem);
 }
 
 template <typename T>
@@ -244,6 +262,47 @@ __global__ void __launch_bounds__(BCfg<T>::NT) k_batch(BatchCtl c, const BatchMe
   }
 }
 
+// The grid schedule's kernels, one per kind of pass: tile blockIdx.x of member
+// cls[blockIdx.y] (a member of size N), each with only its own tile body and the block shape
+// of the single-context kernel of that body (the same arithmetic as the persistent kernel's
+// items, so every schedule gives the same bits).
+template <typename T, int N>
+__global__ void __launch_bounds__(128) k_bgrid_tab(const BatchMem<T>* __restrict__ mems, const int* __restrict__ cls,
+                                                   int step, int nsteps) {
+  batch_tab<T, N>(mems[__ldg(&cls[blockIdx.y])], step, nsteps);
+}
+template <typename T, int N>
+__global__ void __launch_bounds__(K2Cfg<T, N>::NTP) k_bgrid_pencil(const BatchMem<T>* __restrict__ mems,
+                                                                  const int* __restrict__ cls, int pass, int step,
+                                                                  int nsteps) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const BatchMem<T>& bm = mems[__ldg(&cls[blockIdx.y])];
+  pencil_tile<T, N, MemNC>(batch_pencil_args(bm, pass, step, nsteps), (int)blockIdx.x,
+                           reinterpret_cast<cpx<T>*>(smem_raw));
+}
+template <typename T, int N>
+__global__ void __launch_bounds__(K2Cfg<T, N>::NTYI) k_bgrid_yinv(const BatchMem<T>* __restrict__ mems,
+                                                                 const int* __restrict__ cls) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int ntx = (N / 2) / K2Cfg<T, N>::TYI;
+  yinv_tile<T, N, MemNC>(mems[__ldg(&cls[blockIdx.y])].sa, (int)blockIdx.x % ntx, (int)blockIdx.x / ntx,
+                         reinterpret_cast<cpx<T>*>(smem_raw));
+}
+template <typename T, int N>
+__global__ void __launch_bounds__(K2Cfg<T, N>::NTX, K2Cfg<T, N>::MINB_X) k_bgrid_xrow(
+    const BatchMem<T>* __restrict__ mems, const int* __restrict__ cls) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  xrow_tile<T, N, MemNC>(mems[__ldg(&cls[blockIdx.y])].sa, (int)blockIdx.x, reinterpret_cast<cpx<T>*>(smem_raw));
+}
+template <typename T, int N>
+__global__ void __launch_bounds__(K2Cfg<T, N>::NTY, 2) k_bgrid_yfwd(const BatchMem<T>* __restrict__ mems,
+                                                                   const int* __restrict__ cls) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int ntx = (N / 2) / K2Cfg<T, N>::TY;
+  yfwd_tile<T, N, MemNC>(mems[__ldg(&cls[blockIdx.y])].sa, (int)blockIdx.x % ntx, (int)blockIdx.x / ntx,
+                         reinterpret_cast<cpx<T>*>(smem_raw));
+}
+
 template <typename T, int N>
 void member_items(int* items, int* pro_init) {
   using C = K2Cfg<T, N>;
@@ -270,6 +329,57 @@ void items_for(int N, int* items, int* pro) {
     case 64: member_items<T, 64>(items, pro); break;
     case 96: member_items<T, 96>(items, pro); break;
     default: member_items<T, 128>(items, pro); break;
+  }
+}
+
+// every pass of nsteps steps (and the prologue) of the nc members cls[0 .. nc) of size N on
+// stream cs; returns the first launch error
+template <typename T, int N>
+cudaError_t launch_class(const BatchMem<T>* dm, const int* cls, int nc, int nsteps, cudaStream_t cs) {
+  using C = K2Cfg<T, N>;
+  constexpr int M = N / 2;
+  const size_t cz = sizeof(cpx<T>), tw = (size_t)tw_elems(N);
+  const size_t smP = (3 * (size_t)lf_rows<T, C::TX>(N) * C::TX + tw) * cz;
+  const size_t smYI = (4 * (size_t)lf_rows<T, C::TYI>(N) * C::TYI + tw) * cz;
+  const size_t smY = ((size_t)lf_rows<T, C::TY>(N) * C::TY + tw) * cz;
+  const size_t smX = ((size_t)C::XELEMS + tw) * cz;
+  static bool attr = false;  // (per template instance: the opt-in sizes set before the first launch)
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_bgrid_pencil<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smP);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_bgrid_yinv<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smYI);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_bgrid_yfwd<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smY);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_bgrid_xrow<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smX);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  const int pen = (M / C::TX) * N, yi = (M / C::TYI) * N, yf = (M / C::TY) * N;
+  const int xr = (N * N + C::RX - 1) / C::RX;
+  k_bgrid_tab<T, N><<<dim3(1, nc), 128, 0, cs>>>(dm, cls, 0, nsteps);
+  k_bgrid_pencil<T, N><<<dim3(pen, nc), C::NTP, smP, cs>>>(dm, cls, -1, 0, nsteps);
+  for (int s = 0; s < nsteps; ++s) {
+    k_bgrid_tab<T, N><<<dim3(1, nc), 128, 0, cs>>>(dm, cls, s, nsteps);
+    for (int h = 0; h < 2; ++h) {  // the two stages: slab pass, then the pencil pass P1 / P2
+      k_bgrid_yinv<T, N><<<dim3(yi, nc), C::NTYI, smYI, cs>>>(dm, cls);
+      k_bgrid_xrow<T, N><<<dim3(xr, nc), C::NTX, smX, cs>>>(dm, cls);
+      k_bgrid_yfwd<T, N><<<dim3(yf, nc), C::NTY, smY, cs>>>(dm, cls);
+      k_bgrid_pencil<T, N><<<dim3(pen, nc), C::NTP, smP, cs>>>(dm, cls, h == 0 ? P_P1 : P_P2, s, nsteps);
+    }
+  }
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_class_any(int sz, const BatchMem<T>* dm, const int* cls, int nc, int nsteps, cudaStream_t cs) {
+  switch (sz) {
+    case 0: return launch_class<T, 16>(dm, cls, nc, nsteps, cs);
+    case 1: return launch_class<T, 32>(dm, cls, nc, nsteps, cs);
+    case 2: return launch_class<T, 48>(dm, cls, nc, nsteps, cs);
+    case 3: return launch_class<T, 64>(dm, cls, nc, nsteps, cs);
+    case 4: return launch_class<T, 96>(dm, cls, nc, nsteps, cs);
+    default: return launch_class<T, 128>(dm, cls, nc, nsteps, cs);
   }
 }
 
@@ -309,6 +419,10 @@ struct ns_batch {
   // the tuner at the first step (or forced by ns_batch_set_schedule / NS_BATCH_SCHEDULE)
   int gran = 1, per_sm_req = 0;
   bool tuned = false;
+  // grid schedule (gran 0): member indices grouped by size class, one stream per class
+  int* d_cls = nullptr;
+  cudaStream_t cls_st[kNumSizes] = {};
+  cudaEvent_t ev_fork = nullptr, ev_join[kNumSizes] = {};
 };
 
 namespace {
@@ -430,6 +544,40 @@ int batch_step_t(ns_batch* b, const double* dt, int nsteps) {
       !chk(cudaMemcpyAsync(b->d_off + kPasses * (kMaxMembers + 1), off_pro.data(), off_pro.size() * sizeof(int),
                            cudaMemcpyHostToDevice, st))) {
     return NS_ERR_CUDA;
+  }
+  if (b->gran == 0) {  // grid schedule
+    std::vector<int> cls;
+    int start[kNumSizes + 1];
+    for (int z = 0; z < kNumSizes; ++z) {
+      start[z] = (int)cls.size();
+      for (int m = 0; m < n; ++m)
+        if (hm[m].sz == z) cls.push_back(m);
+    }
+    start[kNumSizes] = (int)cls.size();
+    if (!b->d_cls && !chk(cudaMalloc(&b->d_cls, kMaxMembers * sizeof(int)))) return NS_ERR_OOM;
+    if (!b->ev_fork && !chk(cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming))) return NS_ERR_CUDA;
+    if (!chk(cudaMemcpyAsync(b->d_cls, cls.data(), cls.size() * sizeof(int), cudaMemcpyHostToDevice, st)) ||
+        !chk(cudaMemsetAsync(b->d_flags, 0, 2 * sizeof(int), st)) || !chk(cudaEventRecord(b->ev_fork, st)))
+      return NS_ERR_CUDA;
+    const BatchMem<T>* dmg = (const BatchMem<T>*)b->d_mems;
+    for (int z = 0; z < kNumSizes; ++z) {
+      const int nc = start[z + 1] - start[z];
+      if (nc == 0) continue;
+      if (!b->cls_st[z] && (!chk(cudaStreamCreateWithFlags(&b->cls_st[z], cudaStreamNonBlocking)) ||
+                            !chk(cudaEventCreateWithFlags(&b->ev_join[z], cudaEventDisableTiming))))
+        return NS_ERR_CUDA;
+      if (!chk(cudaStreamWaitEvent(b->cls_st[z], b->ev_fork, 0)) ||
+          !chk(launch_class_any<T>(z, dmg, b->d_cls + start[z], nc, nsteps, b->cls_st[z])) ||
+          !chk(cudaEventRecord(b->ev_join[z], b->cls_st[z])) || !chk(cudaStreamWaitEvent(st, b->ev_join[z], 0)))
+        return NS_ERR_CUDA;
+    }
+    b->grid = 0;
+    int flags[2] = {0, 0};
+    if (!chk(cudaMemcpyAsync(flags, b->d_flags, 2 * sizeof(int), cudaMemcpyDeviceToHost, st)) ||
+        !chk(cudaStreamSynchronize(st)))
+      return NS_ERR_CUDA;
+    for (int m = 0; m < n; ++m) ns_ctx_advance(b->mem[m], dt[m], nsteps);
+    return NS_OK;
   }
   c.next = b->d_next;
   c.done = b->d_done;
