@@ -540,6 +540,13 @@ struct Solver : SolverBase {
     memset(&a, 0, sizeof(a));
     a.N = N; a.M = M; a.py = py; a.px = px; a.tw = tw; a.scr = scr;
     a.TY = TY; a.RX = RX; a.err = d_err;
+    // Ft modes no pencil tile reads are left unwritten (every pencil instance of this size
+    // skips the same truncated tiles; the widest tile decides)
+    if (use2 && NS_FT_SKIP) {
+      a.skip_tx = std::max(k2.TX, k2.has_alt ? k2.alt.TX : 0);
+      a.trunc = c->p.truncation; a.K2max = c->K2max; a.Kimax = c->Kimax;
+      a.fK = fkind != NS_FORCE_NONE ? fK : -1;
+    }
     return a;
   }
 

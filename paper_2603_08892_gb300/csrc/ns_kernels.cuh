@@ -315,6 +315,10 @@ struct SlabArgs {
   int* err;
   void* umax;           // or null: max_x |u_i(x)| of the velocity rows, i = 0..2, folded in
                         // with atomicMax on the IEEE bits (unsigned / unsigned long long [3])
+  // modes of Ft no pencil pass reads (skip_tx > 0: the compile-time y-forward leaves them
+  // unwritten): those of pencil tiles of skip_tx columns outside the truncation (trunc, K2max,
+  // Kimax) and outside the forcing block |k| <= fK (fK < 0: no forcing)
+  int skip_tx, trunc, K2max, Kimax, fK;
 };
 
 // Block maxima m0..m2 (non-negative) folded into umax[0..2], one atomic per value per block:

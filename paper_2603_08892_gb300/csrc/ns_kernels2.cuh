@@ -838,6 +838,29 @@ __global__ void __launch_bounds__(K2Cfg<T, N, V>::NTYI) k2_yinv(SlabArgs<T> a) {
                                                                   reinterpret_cast<cpx<T>*>(smem_raw));
 }
 
+#ifndef NS_FT_SKIP
+#define NS_FT_SKIP 1
+#endif
+// Ft output of the forward y transforms: a mode is stored unless every pencil tile of
+// a.skip_tx columns that holds it lies outside the truncation and the forcing block (the
+// criterion of pencil_tile_truncated with x0 the tile's first column): the pencil passes
+// neither load nor transform such tiles.
+template <typename T, int N, class MP>
+struct FtColOut {
+  cpx<T>* p;
+  int z, x0;
+  const SlabArgs<T>* a;
+  __device__ __forceinline__ void put(int line, int e, cpx<T> v) const {
+    if (a->skip_tx > 0) {
+      const int kx = x0 + line, px = kx - kx % a->skip_tx, ky = kof(e, N);
+      const bool out = a->trunc == 1 ? (px > a->Kimax || abs(ky) > a->Kimax) : px * px + ky * ky > a->K2max;
+      const bool forced = a->fK >= 0 && px <= a->fK && abs(ky) <= a->fK;
+      if (out && !forced) return;
+    }
+    MP::st(&p[((size_t)z * N + e) * (N / 2) + x0 + line], v);
+  }
+};
+
 template <typename T, int N, class MP, int V = 0>
 __device__ __forceinline__ void yfwd_tile(const SlabArgs<T>& a, int tx, int zg, cpx<T>* W) {
   using C = K2Cfg<T, N, V>;
@@ -848,7 +871,7 @@ __device__ __forceinline__ void yfwd_tile(const SlabArgs<T>& a, int tx, int zg, 
   load_twiddles(tws, a.tw, N);
   for (int f = 0; f < 3; ++f) {
     cfft<T, N, 1, C::TY, C::NTY, true, -1, C::RYF>(ScrCol<T, N, MP>{a.scr + f * sstride, zg, x0},
-                                           ScrCol<T, N, MP>{a.Ft + f * fstride, z, x0}, W, tws);
+                                                   FtColOut<T, N, MP>{a.Ft + f * fstride, z, x0, &a}, W, tws);
     __syncthreads();
   }
 }
