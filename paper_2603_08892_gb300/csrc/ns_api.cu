@@ -423,6 +423,7 @@ struct Solver : SolverBase {
       allow(k2.pencil, k2.smP5);
       allow(k2.pencil1, k2.smP1);
       allow(k2.pencil1e, k2.smP1);
+      allow(k2.pencil1re, k2.smP1);
       allow(k2.pencil1r[0], k2.smP1);
       allow(k2.pencil1r[1], k2.smP1);
       allow(k2.pencil2, k2.smP5);
@@ -741,7 +742,7 @@ struct Solver : SolverBase {
     else if (use2 && rog && (vsel & 16))  // the alternative register budget
       k2.pencil1r64[a.mode == MODE_ROG_1 ? 0 : 1]<<<(M / k2.TX) * R, k2.NTP, k2.smP1, st>>>(a);
     else if (use2)
-      (a.nF == 1 && a.nOut == 1   ? (a.epart                  ? k2.pencil1e
+      (a.nF == 1 && a.nOut == 1   ? (a.epart                  ? (a.mode == MODE_ROG_2 ? k2.pencil1re : k2.pencil1e)
                                      : a.mode == MODE_ROG_1 ? k2.pencil1r[0]
                                      : a.mode == MODE_ROG_2 ? k2.pencil1r[1]
                                                             : k2.pencil1)

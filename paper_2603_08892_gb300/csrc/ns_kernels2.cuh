@@ -1185,6 +1185,7 @@ struct K2Entry {
   void (*pencil)(PencilArgs<T>) = nullptr;   // any number of inputs / outputs
   void (*pencil1)(PencilArgs<T>) = nullptr;  // one input, one output
   void (*pencil1e)(PencilArgs<T>) = nullptr; // same, also storing the tile's energy sums
+  void (*pencil1re)(PencilArgs<T>) = nullptr; // the energy-sum variant of the ROG_2 stage
   void (*pencil1r[2])(PencilArgs<T>) = {nullptr, nullptr};  // one in, one out: ROG_1, ROG_2
   void (*pencil2)(PencilArgs<T>) = nullptr;  // two inputs, two outputs
   void (*yinv)(SlabArgs<T>) = nullptr;
@@ -1235,6 +1236,7 @@ K2Entry<T> make_k2_entry() {
 #endif
   e.pencil1r[0] = NS_PENCIL_MODE_VARIANTS ? k2_pencil<T, N, 1, 1, false, MODE_ROG_1> : e.pencil1;
   e.pencil1r[1] = NS_PENCIL_MODE_VARIANTS ? k2_pencil<T, N, 1, 1, false, MODE_ROG_2> : e.pencil1;
+  e.pencil1re = NS_PENCIL_VARIANTS && NS_PENCIL_MODE_VARIANTS ? k2_pencil<T, N, 1, 1, true, MODE_ROG_2> : e.pencil1e;
   e.pencil2 = NS_PENCIL_VARIANTS ? k2_pencil<T, N, 2, 2> : e.pencil;
   e.yinv = k2_yinv<T, N>;
   e.yfwd = k2_yfwd<T, N>;
