@@ -410,6 +410,7 @@ struct Solver : SolverBase {
     CUDA_TRY(cudaFuncSetAttribute(k_yfwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
     CUDA_TRY(cudaFuncSetAttribute(k_xrow<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
     use2 = k2_find(N, &k2);
+    if (const char* e = std::getenv("NS_ZERO_COPY")) zero_copy = std::atoi(e) != 0;
     if (use2) {
       // each kernel may take the opt-in limit less its own static shared memory
       auto allow = [&](auto* f, size_t need) {
@@ -1461,9 +1462,24 @@ struct Solver : SolverBase {
       }
     }
   }
+  // the device address of a page-locked host buffer (written by kernels directly), or null
+  bool zero_copy = true;  // NS_ZERO_COPY=0: always stage and copy
+  double* host_device_view(double* h) {
+    if (!zero_copy) return nullptr;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, h) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    return at.type == cudaMemoryTypeHost && at.devicePointer ? static_cast<double*>(at.devicePointer) : nullptr;
+  }
   void to_host(const T* d, double* h, size_t n) {
     if constexpr (sizeof(T) == sizeof(double)) {
       CUDA_TRY(cudaMemcpyAsync(h, d, n * sizeof(double), cudaMemcpyDeviceToHost, st));
+    } else if (double* hd = host_device_view(h)) {
+      // page-locked destination: the conversion kernel stores into it over the host link
+      k_real_to_double<T><<<8 * nsm, 256, 0, st>>>(d, hd, n);
+      LAUNCH_CHECK();
     } else {
       double* stg = reinterpret_cast<double*>(scr);
       const size_t cap = stage_doubles();
