@@ -1,7 +1,8 @@
 """Element-wise parity of the size-specialised kernels that the benchmark times, at full size.
 
 One step of the compiled instance at each size (256^3 FP32 -- the benchmarked Rogallo step --
-and FP64; 128^3 and 192^3 FP32; RK4 + 2/3 at 384^3 FP32) through the C ABI, compared with
+and FP64; 128^3 and 192^3 FP32; RK4 + 2/3 at 384^3 FP32; the forced split step of the
+512^3 HIT workload) through the C ABI, compared with
 one FP64 oracle step on the whole state (relative L2, Sections 4.1-4.2: the shifted and
 de-shifted term and Eq. Rogallo1981; RK4: the Lawson reading).  The oracle uses threaded
 pocketfft transforms so each full-size step takes seconds.
@@ -19,6 +20,7 @@ import os
 import numpy as np
 import pytest
 
+from oracle import forcing as fo
 from oracle import rng as orng
 from oracle import schemes as sc
 from oracle import spectral as osp
@@ -108,4 +110,28 @@ def test_rk4_step_384_fp32(ns, report):
         got = s.get_state()
     err = rel(got, ref)
     report("rk4_step_broadband_N384_fp32", err, 2e-5)
+    assert err < 2e-5
+
+
+def test_forced_split_step_hit_512_fp32(ns, report):
+    # the forced-turbulence workload: 512^3 RK2 phase-shift random with the constant-rate
+    # forcing on the shell 2 <= |k| <= 3 (the split reading of Sec. 6.1), seeded HIT field,
+    # nu = kmax^(-4/3), CFL 0.4; one step against the FP64 oracle (about 50 GB of host memory)
+    N, kmax = 512, 256.0
+    nu = kmax ** (-4.0 / 3.0)
+    u = inputs.hit_initial(N, 2026)
+    umax = np.abs(u).reshape(3, -1).max(axis=1)
+    dt = 0.4 / float(np.sum(umax / (2 * math.pi / N)))
+    with ns.Solver(N, nu, kmax, scheme=ns.RK2_PS_RANDOM, precision=ns.FP32, seed=2026) as s:
+        s.set_velocity(u)
+        s.set_forcing(2.0, 3.0, 1.0, 0.5, seed=2026)
+        s.step(dt, 1)
+        got = s.get_state()
+    forcing = fo.Forcing(N, 2.0, 3.0, 1.0, 0.5, seed=2026)
+    S0 = osp.set_velocity(u, kmax)
+    del u
+    ref, _ = sc.run(S0, dt, 1, sc.Problem(N, nu, kmax), sc.SCHEME_PS_RANDOM, seed=2026, forcing=forcing)
+    del S0
+    err = rel(got, ref)
+    report("forced_split_step_hit_N512_fp32", err, 2e-5)
     assert err < 2e-5
