@@ -5,7 +5,10 @@
 #include <cstdio>
 #include <cstdlib>
 
+using namespace nsb;
+
 int ns_batch_step_f64(ns_batch* b, const double* dt, int nsteps);
+int ns_batch_max_ctas_f64();
 
 namespace {
 
@@ -64,7 +67,7 @@ int batch_tune(ns_batch* b, const double* dt) {
     if (b->precision == NS_FP32)
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&maxq, k_batch<float>, nt, smem);
     else
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&maxq, k_batch<double>, nt, smem);
+      maxq = ns_batch_max_ctas_f64();  // (the FP64 kernel lives in its own translation unit)
   }
   for (int g : {0, 1, 2, 4, 8}) {  // 0: the grid schedule (one launch per pass and size class)
     for (int q : {0, 1}) {

@@ -37,7 +37,9 @@
 
 using namespace ns;
 
-namespace {
+// (a named namespace: the grid schedule's kernels are compiled in translation units of their
+// own and reached through launch_class_any)
+namespace nsb {
 
 constexpr int kPasses = 9;  // per step
 enum { P_TAB = 0, P_Y1, P_X1, P_F1, P_P1, P_Y2, P_X2, P_F2, P_P2 };
@@ -262,6 +264,7 @@ __global__ void __launch_bounds__(BCfg<T>::NT) k_batch(BatchCtl c, const BatchMe
   }
 }
 
+#ifdef NS_BATCH_GRID_DEFS
 // The grid schedule's kernels, one per kind of pass: tile blockIdx.x of member
 // cls[blockIdx.y] (a member of size N), each with only its own tile body and the block shape
 // of the single-context kernel of that body (the same arithmetic as the persistent kernel's
@@ -303,6 +306,8 @@ __global__ void __launch_bounds__(K2Cfg<T, N>::NTY, 2) k_bgrid_yfwd(const BatchM
                          reinterpret_cast<cpx<T>*>(smem_raw));
 }
 
+#endif  // NS_BATCH_GRID_DEFS
+
 template <typename T, int N>
 void member_items(int* items, int* pro_init) {
   using C = K2Cfg<T, N>;
@@ -314,7 +319,7 @@ void member_items(int* items, int* pro_init) {
   *pro_init = pen;
 }
 
-int size_index(int N) {
+inline int size_index(int N) {
   for (int i = 0; i < kNumSizes; ++i)
     if (kSizes[i] == N) return i;
   return -1;
@@ -332,6 +337,13 @@ void items_for(int N, int* items, int* pro) {
   }
 }
 
+// every pass of nsteps steps (and the prologue) of the nc members cls[0 .. nc) of the size
+// class sz (kSizes[sz]) on stream cs, as grid launches; returns the first launch error.
+// Defined in the grid schedule's translation units (ns_batch_grid_f32.cu, ns_batch_grid_f64.cu).
+template <typename T>
+cudaError_t launch_class_any(int sz, const BatchMem<T>* dm, const int* cls, int nc, int nsteps, cudaStream_t cs);
+
+#ifdef NS_BATCH_GRID_DEFS
 // every pass of nsteps steps (and the prologue) of the nc members cls[0 .. nc) of size N on
 // stream cs; returns the first launch error
 template <typename T, int N>
@@ -383,7 +395,9 @@ cudaError_t launch_class_any(int sz, const BatchMem<T>* dm, const int* cls, int 
   }
 }
 
-uint64_t smix(uint64_t s, uint64_t n) {
+#endif  // NS_BATCH_GRID_DEFS
+
+inline uint64_t smix(uint64_t s, uint64_t n) {
   uint64_t z = s + (n + 1) * 0x9E3779B97F4A7C15ull;
   z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
   z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
@@ -421,11 +435,11 @@ struct ns_batch {
   bool tuned = false;
   // grid schedule (gran 0): member indices grouped by size class, one stream per class
   int* d_cls = nullptr;
-  cudaStream_t cls_st[kNumSizes] = {};
-  cudaEvent_t ev_fork = nullptr, ev_join[kNumSizes] = {};
+  cudaStream_t cls_st[nsb::kNumSizes] = {};
+  cudaEvent_t ev_fork = nullptr, ev_join[nsb::kNumSizes] = {};
 };
 
-namespace {
+namespace nsb {
 
 template <typename T>
 int batch_step_t(ns_batch* b, const double* dt, int nsteps) {
