@@ -581,7 +581,7 @@ def main():
             "schedule": {"kind": "grid" if gran == 0 else "persistent", "tiles_per_ticket": gran,
                          "ctas_per_sm": qsm},
             "launches_per_call": 4 * (2 + 9 * Kb) if gran == 0 else 1,
-            "persistent_ctas": b.grid(),
+            "persistent_ctas": b.grid() if gran != 0 else None,
             "gcells_per_s": world * sum(n ** 3 for n in Ns) * Kb / (msb / 1000.0) / 1e9,
             "model_bytes_per_step": model,
             "frac_hbm": (model / (msb / Kb / 1000.0) / 1e9) / hbm,

@@ -384,7 +384,8 @@ def nonlinear_noalloc(state_ptr, out_ptr, N, kmax, delta, truncation=TRUNC_SPHER
 
 
 class Batch:
-    """Ensemble of independent members of uneven N advanced by one persistent launch."""
+    """Ensemble of independent members of uneven N advanced together (one persistent launch
+    per call, or one grid launch per pass and size class: the schedule the tuner picks)."""
 
     def __init__(self, Ns, nus, kmaxs, seeds=None, scheme=RK2_PS_RANDOM, precision=FP32,
                  stream=None):
