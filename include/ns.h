@@ -249,8 +249,8 @@ int ns_profile_read(ns_ctx* ctx, int kind, double* total_ms, int64_t* timed, int
  *    counter and wait, with a bounded spin, until the member's earlier passes are complete;
  *    an expired wait ends the launch with NS_ERR_TIMEOUT instead of hanging;
  *  - grid (gran 0): every pass of each size class is one ordinary grid launch (tiles x the
- *    class's members) on a stream of its own, the classes overlapping; nothing waits on the
- *    device.
+ *    class's members), the classes one after another on the batch's stream; nothing waits on
+ *    the device.
  * Supported member sizes: N in {16, 32, 48, 64, 96, 128}; spherical truncation. */
 typedef struct ns_batch ns_batch;
 /* count members (1..1024) with sizes N[i], viscosities nu[i], truncation kmax[i] and shift

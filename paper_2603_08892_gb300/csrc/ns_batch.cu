@@ -171,11 +171,6 @@ int ns_batch_destroy(ns_batch* b) {
   cudaFree(b->d_flags);
   cudaFree(b->d_tab);
   cudaFree(b->d_cls);
-  for (int z = 0; z < kNumSizes; ++z) {
-    if (b->cls_st[z]) cudaStreamDestroy(b->cls_st[z]);
-    if (b->ev_join[z]) cudaEventDestroy(b->ev_join[z]);
-  }
-  if (b->ev_fork) cudaEventDestroy(b->ev_fork);
   if (b->own_stream) cudaStreamDestroy(b->st);  // members were given the stream, not its ownership
   delete b;
   return NS_OK;
