@@ -117,6 +117,22 @@ __device__ __forceinline__ void stage_col_tile(cpx<T>* dst, const cpx<T>* src, i
 __host__ __device__ constexpr int radix_cap(int set, int f32_default, bool f32) {
   return set > 0 ? set : (f32 ? f32_default : NS_MAX_RADIX);
 }
+// NS_SLAB_RADIX_RULE=1: the FP32 slab passes of N <= 128 take radix 8 where the radix-16 plan
+// keeps a radix-2 stage that the radix-8 plan avoids (N = 32: 16.2 -> 8.4; N = 96: 16.2.3 ->
+// 8.4.3).  Measured on GB300: 96^3 step 0.110 against 0.123 ms, 32^3 0.058 against 0.060, the
+// 64-member ensemble +4 %; at 512 (16.16.2 -> 8.8.8) it was 14 % slower, so larger N keep 16.
+#ifndef NS_SLAB_RADIX_RULE
+#define NS_SLAB_RADIX_RULE 1
+#endif
+__host__ __device__ constexpr bool plan_has_radix2(int n, int mr) {
+  const CPlan p = cplan(n, mr);
+  for (int i = 0; i < p.nst; ++i)
+    if (p.r[i] == 2) return true;
+  return false;
+}
+__host__ __device__ constexpr int slab_radix(int n) {
+  return NS_SLAB_RADIX_RULE && n <= 128 && plan_has_radix2(n, 16) && !plan_has_radix2(n, 8) ? 8 : 16;
+}
 
 // Unroll factor of the pencil's loops over the transforms of the components: 1 keeps one copy
 // of the transform code per loop (measured 6 % faster than full unrolling at 256^3 FP32: the
@@ -152,9 +168,9 @@ struct K2Cfg {
   static constexpr int MINW = 32 / CS;  // 32-byte global segments
   static constexpr bool F32 = sizeof(T) == 4;
   static constexpr int RZ = radix_cap(NS_RADIX_Z, NS_MAX_RADIX, F32);
-  static constexpr int RYI = radix_cap(NS_RADIX_YI, 16, F32);
-  static constexpr int RYF = radix_cap(NS_RADIX_YF, 16, F32);
-  static constexpr int RXR = radix_cap(NS_RADIX_X, 16, F32);
+  static constexpr int RYI = radix_cap(NS_RADIX_YI, slab_radix(N), F32);
+  static constexpr int RYF = radix_cap(NS_RADIX_YF, slab_radix(N), F32);
+  static constexpr int RXR = radix_cap(NS_RADIX_X, slab_radix(N), F32);
   // pencil: TX columns of N (NS_PZ_LINES / NS_YF_LINES override the pencil / forward-y width)
 #ifndef NS_PZ_LINES
 #define NS_PZ_LINES 0
